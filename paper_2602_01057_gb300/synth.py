@@ -1,0 +1,227 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module draws random numbers and writes down geometry *descriptions*
+(counts, pitches, distances, view angles).  It holds none of the projector's
+arithmetic: no ray set-up, no covariance, no line integral.  Both the CUDA path
+and the FP64 oracle receive exactly these arrays and build everything else on
+their own.
+
+Workloads (sizes of the paper's experiments, section 4.1; constants where the
+paper is silent are this project's readings):
+
+* ``c1``  parallel-beam CT, 1,000 Gaussians with centres U[-1,1]^3, log-scales
+  N(log 0.05, 0.3^2), random unit quaternions, rho ~ U(0,1); 16 views over 180
+  degrees, 64x64 detector of pitch 2/64, rays over t in [-2, 2].
+* ``c2``  cone-beam CT, 50,000 Gaussians fitted to a 12-ellipsoid phantom in
+  [-1,1]^3 (1 unit = 128 mm); 180 views over 360 degrees, 256x256 detector,
+  source-to-origin 1000 mm, source-to-detector 1500 mm, detector pitch
+  chosen so the magnified 256 mm field of view fills the panel.  The cone-beam
+  sparse-view CT data of the paper (TIGRE-simulated volumes) is not available;
+  this phantom stands in for it.
+* ``c3``  PET ring of radius 400 mm, 32 rings, 576 crystals per ring;
+  arc-corrected sinogram of 288 angles x 329 radial bins x 63 planes, 200,000
+  Gaussians fitted to a 20-ellipsoid activity phantom.  Stands in for the
+  STIR/GATE-simulated PET data of the paper.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# 1 world unit = 128 mm for the CT workloads
+CT_MM_PER_UNIT = 128.0
+
+
+def _random_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q.astype(np.float32)
+
+
+def gaussians_uniform(n: int, seed: int, half_box: float = 1.0,
+                      log_sigma: float = math.log(0.05), log_sigma_std: float = 0.3,
+                      rho_range=(0.0, 1.0)) -> dict:
+    """Gaussians with centres U[-half_box, half_box]^3 (the c1 recipe)."""
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(-half_box, half_box, size=(n, 3)).astype(np.float32)
+    ls = rng.normal(log_sigma, log_sigma_std, size=(n, 3)).astype(np.float32)
+    q = _random_quaternions(rng, n)
+    rho = rng.uniform(rho_range[0], rho_range[1], size=n).astype(np.float32)
+    return dict(mu=mu, ls=ls, q=q, rho=rho)
+
+
+def _random_rotations(rng: np.random.Generator, k: int) -> np.ndarray:
+    """Random rotation matrices (QR of Gaussian matrices, sign-fixed)."""
+    out = np.empty((k, 3, 3))
+    for i in range(k):
+        a = rng.normal(size=(3, 3))
+        qm, rm = np.linalg.qr(a)
+        qm = qm * np.sign(np.diag(rm))
+        if np.linalg.det(qm) < 0:
+            qm[:, 0] = -qm[:, 0]
+        out[i] = qm
+    return out
+
+
+def ellipsoid_phantom(k: int, seed: int, semi=(0.05, 0.6), dens=(0.1, 1.0),
+                      centre_box: float = 1.0, semi_axial=None) -> dict:
+    """k random ellipsoids: semi-axes U(semi), random rotation, centre inside the
+    box so the ellipsoid stays inside it, additive density U(dens)."""
+    rng = np.random.default_rng(seed)
+    axes = rng.uniform(semi[0], semi[1], size=(k, 3))
+    if semi_axial is not None:
+        axes[:, 2] = rng.uniform(semi_axial[0], semi_axial[1], size=k)
+    rot = _random_rotations(rng, k)
+    amax = axes.max(axis=1)
+    lim = np.maximum(centre_box - amax, 0.0)
+    centre = rng.uniform(-1.0, 1.0, size=(k, 3)) * lim[:, None]
+    dens_v = rng.uniform(dens[0], dens[1], size=k)
+    return dict(axes=axes, rot=rot, centre=centre, density=dens_v)
+
+
+def _phantom_density(ph: dict, x: np.ndarray) -> np.ndarray:
+    """Additive density of the ellipsoid phantom at points x[n,3]."""
+    dsum = np.zeros(x.shape[0])
+    for a, r, c, dv in zip(ph["axes"], ph["rot"], ph["centre"], ph["density"]):
+        local = (x - c) @ r  # coordinates along the ellipsoid axes
+        inside = np.sum((local / a) ** 2, axis=1) <= 1.0
+        dsum += dv * inside
+    return dsum
+
+
+def phantom_fitted_gaussians(ph: dict, n: int, seed: int, box_lo, box_hi,
+                             log_sigma_std: float = 0.3) -> dict:
+    """Initial Gaussians for a phantom: centres drawn with probability
+    proportional to the phantom density (rejection sampling in the box),
+    isotropic size h = (V_support / n)^(1/3) with log-scale N(log h, 0.3^2) per
+    axis, random rotation, and rho chosen so each Gaussian's mass matches the
+    density at its centre times h^3."""
+    rng = np.random.default_rng(seed)
+    box_lo = np.asarray(box_lo, dtype=np.float64)
+    box_hi = np.asarray(box_hi, dtype=np.float64)
+    vol_box = float(np.prod(box_hi - box_lo))
+    dmax = float(np.sum(ph["density"]))
+    probe = rng.uniform(box_lo, box_hi, size=(200_000, 3))
+    frac = float(np.mean(_phantom_density(ph, probe) > 0))
+    v_support = max(frac * vol_box, 1e-12)
+    h = (v_support / n) ** (1.0 / 3.0)
+    pts = []
+    need = n
+    while need > 0:
+        cand = rng.uniform(box_lo, box_hi, size=(max(4 * need, 1024), 3))
+        dens = _phantom_density(ph, cand)
+        keep = rng.uniform(0.0, dmax, size=cand.shape[0]) < dens
+        sel = cand[keep][:need]
+        pts.append(sel)
+        need -= sel.shape[0]
+    mu = np.concatenate(pts, axis=0)[:n]
+    ls = rng.normal(math.log(h), log_sigma_std, size=(n, 3))
+    q = _random_quaternions(rng, n)
+    dens_mu = _phantom_density(ph, mu)
+    rho = dens_mu * h ** 3 / ((2.0 * math.pi) ** 1.5 * np.exp(ls.sum(axis=1)))
+    return dict(mu=mu.astype(np.float32), ls=ls.astype(np.float32), q=q,
+                rho=rho.astype(np.float32), h=h)
+
+
+# ---------------------------------------------------------------------------
+# geometry descriptions
+# ---------------------------------------------------------------------------
+
+def geom_parallel(n_views: int, n_rows: int, n_cols: int, pitch_u: float, pitch_v: float,
+                  t_a: float, t_b: float, span: float = math.pi, tile=(16, 16)) -> dict:
+    angles = np.array([span * v / n_views for v in range(n_views)], dtype=np.float64)
+    return dict(kind="parallel", n_views=n_views, n_rows=n_rows, n_cols=n_cols,
+                angles=angles, pitch_u=pitch_u, pitch_v=pitch_v, t_a=t_a, t_b=t_b,
+                dso=0.0, dsd=0.0, radius=0.0, n_crystals=0, arc_mode=0,
+                tile_w=tile[0], tile_h=tile[1])
+
+
+def geom_cone(n_views: int, n_rows: int, n_cols: int, pitch_u: float, pitch_v: float,
+              dso: float, dsd: float, span: float = 2.0 * math.pi, tile=(16, 16)) -> dict:
+    angles = np.array([span * v / n_views for v in range(n_views)], dtype=np.float64)
+    return dict(kind="cone", n_views=n_views, n_rows=n_rows, n_cols=n_cols,
+                angles=angles, pitch_u=pitch_u, pitch_v=pitch_v, t_a=0.0, t_b=0.0,
+                dso=dso, dsd=dsd, radius=0.0, n_crystals=0, arc_mode=0,
+                tile_w=tile[0], tile_h=tile[1])
+
+
+def geom_pet(n_angles: int, n_radial: int, n_planes: int, radius: float, n_crystals: int,
+             plane_pitch: float, arc_mode: int = 0, tile=(16, 16)) -> dict:
+    return dict(kind="pet", n_views=n_angles, n_rows=n_planes, n_cols=n_radial,
+                angles=np.zeros(0, dtype=np.float64), pitch_u=0.0, pitch_v=plane_pitch,
+                t_a=0.0, t_b=0.0, dso=0.0, dsd=0.0, radius=radius,
+                n_crystals=n_crystals, arc_mode=arc_mode, tile_w=tile[0], tile_h=tile[1])
+
+
+def geom_c1(tile=(16, 16)) -> dict:
+    return geom_parallel(16, 64, 64, 2.0 / 64, 2.0 / 64, -2.0, 2.0, span=math.pi, tile=tile)
+
+
+def geom_c2(n_views: int = 180, side: int = 256, tile=(16, 16)) -> dict:
+    dso = 1000.0 / CT_MM_PER_UNIT          # 7.8125
+    dsd = 1500.0 / CT_MM_PER_UNIT          # 11.71875
+    # magnified 256 mm field of view fills 256 pixels: 1.5 mm pitch at 256
+    pitch = (1.5 * 256.0 / side) / CT_MM_PER_UNIT
+    return geom_cone(n_views, side, side, pitch, pitch, dso, dsd, span=2.0 * math.pi, tile=tile)
+
+
+def geom_c3(n_angles: int = 288, n_radial: int = 329, n_planes: int = 63, arc_mode: int = 0,
+            tile=(16, 16)) -> dict:
+    # 32 rings at a 4 mm ring pitch: 63 planes (direct + cross) 2 mm apart
+    return geom_pet(n_angles, n_radial, n_planes, radius=400.0, n_crystals=576,
+                    plane_pitch=2.0, arc_mode=arc_mode, tile=tile)
+
+
+def num_rays(g: dict) -> int:
+    return int(g["n_views"]) * int(g["n_rows"]) * int(g["n_cols"])
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def workload_c1(seed: int = 0) -> tuple[dict, dict]:
+    return gaussians_uniform(1000, seed), geom_c1()
+
+
+def workload_c2(seed: int = 0, n: int = 50_000, n_views: int = 180, side: int = 256) -> tuple[dict, dict]:
+    ph = ellipsoid_phantom(12, seed=1000 + seed, semi=(0.05, 0.6), dens=(0.1, 1.0))
+    gs = phantom_fitted_gaussians(ph, n, seed=2000 + seed, box_lo=(-1, -1, -1), box_hi=(1, 1, 1))
+    return gs, geom_c2(n_views=n_views, side=side)
+
+
+def workload_c3(seed: int = 0, n: int = 200_000, n_angles: int = 288, n_radial: int = 329,
+                n_planes: int = 63) -> tuple[dict, dict]:
+    # activity ellipsoids inside a cylinder of radius 250 mm, |z| <= 60 mm
+    rng = np.random.default_rng(3000 + seed)
+    k = 20
+    axes = np.column_stack([rng.uniform(5, 80, k), rng.uniform(5, 80, k), rng.uniform(5, 40, k)])
+    rot = _random_rotations(rng, k)
+    amax = axes.max(axis=1)
+    r_lim = np.maximum(250.0 - amax, 0.0)
+    rad = r_lim * np.sqrt(rng.uniform(0, 1, k))
+    ang = rng.uniform(0, 2 * math.pi, k)
+    z_lim = np.maximum(60.0 - axes[:, 2], 0.0)
+    centre = np.column_stack([rad * np.cos(ang), rad * np.sin(ang), rng.uniform(-1, 1, k) * z_lim])
+    ph = dict(axes=axes, rot=rot, centre=centre, density=rng.uniform(0.1, 1.0, k))
+    gs = phantom_fitted_gaussians(ph, n, seed=4000 + seed, box_lo=(-250, -250, -60),
+                                  box_hi=(250, 250, 60))
+    return gs, geom_c3(n_angles, n_radial, n_planes)
+
+
+def perturbed(gs: dict, seed: int, pos_std: float, ls_std: float = 0.05) -> dict:
+    """A second Gaussian set near gs (same count): the 'measured object'
+    whose projections serve as data when fitting gs."""
+    rng = np.random.default_rng(seed)
+    mu = gs["mu"] + rng.normal(0, pos_std, gs["mu"].shape).astype(np.float32)
+    ls = gs["ls"] + rng.normal(0, ls_std, gs["ls"].shape).astype(np.float32)
+    q = _random_quaternions(rng, gs["q"].shape[0])
+    rho = gs["rho"] * rng.uniform(0.8, 1.2, gs["rho"].shape).astype(np.float32)
+    return dict(mu=mu.astype(np.float32), ls=ls.astype(np.float32), q=q, rho=rho.astype(np.float32))
+
+
+def random_weights(n_rays: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Per-ray adjoint weights (dL/dI) for parity checks of the adjoint."""
+    rng = np.random.default_rng(seed)
+    return (scale * rng.normal(size=n_rays)).astype(np.float32)
