@@ -1,0 +1,210 @@
+/*
+ * rgrt.h -- C ABI of the GB300 analytic Gaussian ray-tracing projector.
+ *
+ * The library projects a set of anisotropic 3D Gaussians along the rays of a
+ * CT (parallel- or cone-beam) or PET (ring, arc-corrected or raw-chord)
+ * geometry and back-propagates a loss to the Gaussian parameters.  It follows
+ * the problem statement of "Radioactive 3D Gaussian Ray Tracing for
+ * Tomographic Reconstruction", section 3:
+ *   Gaussian     G(x) = exp(-1/2 (x-mu)^T Sigma^-1 (x-mu)),
+ *                Sigma = R S S^T R^T                            (Eq. 2)
+ *   ray          r(t) = o + t d                                  (Eq. 3)
+ *   projection   I(r) = sum_i rho_i int G_i(o + t d) dt          (Eq. 4)
+ *   closed form  rho sqrt(2 pi/A) exp(-1/2 (C - B^2/A))          (Eqs. 7-12)
+ * with erf terms where the ray segment is finite, and Gaussians whose
+ * contribution is negligible skipped (section 4.1, implementation details):
+ * a pair counts when C - B^2/A <= 9 (the ray meets the 3-sigma ellipsoid).
+ *
+ * Parameterisation (per Gaussian, FP32):
+ *   mu[3]         centre
+ *   logscale[3]   l, with S = diag(exp(l))
+ *   quat[4]       (w, x, y, z), normalised inside R(q); gradients are taken
+ *                 with respect to the unnormalised q
+ *   rho           density scale (the normalisation of Eq. 2 is absorbed in it)
+ * Arrays are structure-of-arrays, contiguous: mu[n][3], logscale[n][3],
+ * quat[n][4], rho[n].
+ *
+ * Memory: every pointer argument may be host memory (pageable or pinned) or
+ * device memory of the context's device; the library detects which and
+ * copies host data through its own device buffers, stream-ordered.  Device
+ * buffers passed in stay owned by the caller.  The library owns the
+ * Gaussians it copies (RGRT_COPY), their Adam state, and its binning scratch,
+ * all counted against the context's HBM budget.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ * enqueue work on it; project_forward and project_backward read one 8-byte
+ * count back from the device per binning pass (a short synchronisation on
+ * that stream).  Results written to host pointers are complete on return.
+ *
+ * Errors: every call returns RGRT_OK (0) or a negative code; the message of
+ * the last failure on the calling thread is returned by rgrt_last_error().
+ * No call aborts the process or lets a C++ exception cross the ABI.
+ */
+#ifndef RGRT_H
+#define RGRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------- */
+#define RGRT_OK 0
+#define RGRT_E_INVAL -1     /* bad argument: shape, null pointer, non-finite geometry */
+#define RGRT_E_NOMEM -2     /* request exceeds the context's HBM budget, or cudaMalloc failed */
+#define RGRT_E_CAPACITY -3  /* one view's tile lists do not fit the budget */
+#define RGRT_E_CUDA -4      /* a CUDA runtime call failed (message names it) */
+#define RGRT_E_TIMEOUT -5   /* a bounded device-side wait gave up */
+
+/* ---- flags ---------------------------------------------------------- */
+#define RGRT_COPY 0     /* gaussians_create: the library keeps its own device copy */
+#define RGRT_BORROW 1   /* gaussians_create: wrap the caller's device arrays (must stay alive) */
+
+#define RGRT_LOSS_L2 0       /* L = 1/2 sum (I - y)^2 */
+#define RGRT_LOSS_POISSON 1  /* L = sum (k I + e - y log(k I + e)), k = kappa, e = eps */
+
+#define RGRT_GEOM_CT_PARALLEL 0
+#define RGRT_GEOM_CT_CONE 1
+#define RGRT_GEOM_PET_RING 2
+
+typedef struct rgrt_ctx rgrt_ctx;
+typedef struct rgrt_gauss rgrt_gauss;
+typedef struct rgrt_geom rgrt_geom;
+
+/*
+ * Geometry description (section 3 "Inherent limitations": cone/parallel-beam
+ * CT and PET with arc correction; the constants are the caller's).
+ *
+ * CT frame of view k (angle th = angles[k]): e_w = (cos th, sin th, 0) from
+ * source to detector, e_u = (-sin th, cos th, 0), e_v = (0, 0, 1); detector
+ * pixel (row j, col i) at u_i = (i - (n_cols-1)/2) pitch_u,
+ * v_j = (j - (n_rows-1)/2) pitch_v.
+ *   CT_PARALLEL  ray o = u e_u + v e_v, d = e_w, t in [t_a, t_b].
+ *   CT_CONE      source S = -dso e_w, pixel D = S + dsd e_w + u e_u + v e_v;
+ *                the ray runs from S to D.
+ * PET frame of angle k: phi = pi k / n_views, e_u = (cos phi, sin phi, 0),
+ * e_v = (0,0,1), e_w = (sin phi, -cos phi, 0); radial bin i at
+ *   arc_mode 0 (arc-corrected): s_i = (i - c) pi radius / n_crystals
+ *   arc_mode 1 (raw chords):    s_i = radius sin((i - c) pi / n_crystals)
+ * with c = (n_cols-1)/2, plane j at z_j = (j - (n_rows-1)/2) pitch_v; the
+ * line of response o = s e_u + z e_v, d = e_w runs over the chord
+ * t in [-sqrt(radius^2 - s^2), +sqrt(radius^2 - s^2)].
+ * Output layout: CT I[view][row][col]; PET I[plane][angle][radial].
+ * tile_w/tile_h: binning tile in pixels (multiples of 8 and 4; 0 = 16).
+ */
+typedef struct {
+    int32_t kind;        /* RGRT_GEOM_* */
+    int32_t n_views;     /* CT projections / PET sinogram angles */
+    int32_t n_rows;      /* CT detector rows / PET planes */
+    int32_t n_cols;      /* CT detector columns / PET radial bins */
+    const double *angles;/* CT: n_views angles in radians (host memory); PET: unused */
+    double pitch_u, pitch_v;
+    double t_a, t_b;     /* CT_PARALLEL segment */
+    double dso, dsd;     /* CT_CONE source-origin and source-detector distances */
+    double radius;       /* PET ring radius */
+    int32_t n_crystals;  /* PET crystals per ring */
+    int32_t arc_mode;    /* PET: 0 arc-corrected, 1 raw chord positions */
+    int32_t tile_w, tile_h;
+} rgrt_geom_desc;
+
+/* Adam hyper-parameters of loss_step (Kingma & Ba; the paper trains with
+ * Adam, section 4.1, and states no values). */
+typedef struct {
+    float lr_mu, lr_logscale, lr_quat, lr_rho;
+    float beta1, beta2, eps;
+    float kappa, poisson_eps; /* RGRT_LOSS_POISSON only */
+} rgrt_adam;
+
+/* ---- context -------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` whose device allocations stay
+ * within hbm_budget_bytes (0 = 90% of the free memory at creation).
+ * Returns RGRT_E_INVAL for a bad device, RGRT_E_CUDA on a runtime failure. */
+int rgrt_ctx_create(rgrt_ctx **out, int device, size_t hbm_budget_bytes);
+/* Free every buffer of the context (Gaussians and geometries made from it
+ * must be destroyed first). */
+int rgrt_ctx_destroy(rgrt_ctx *ctx);
+
+/* ---- Gaussians (Eq. 2) ---------------------------------------------- */
+
+/* Register n Gaussians.  flags = RGRT_COPY copies the four arrays (host or
+ * device) into library-owned device memory; RGRT_BORROW keeps the caller's
+ * device pointers (n may be 0).  RGRT_E_INVAL for n < 0, a null array with
+ * n > 0, or BORROW of host memory. */
+int gaussians_create(rgrt_ctx *ctx, int64_t n, const float *mu3, const float *logscale3,
+                     const float *quat4, const float *rho, int flags, rgrt_gauss **out);
+int gaussians_destroy(rgrt_gauss *g);
+/* Copy the current parameters out (host or device pointers; null skips). */
+int gaussians_get(rgrt_gauss *g, float *mu3, float *logscale3, float *quat4, float *rho, void *stream);
+/* Overwrite the parameters (host or device pointers; null keeps the old). */
+int gaussians_set(rgrt_gauss *g, const float *mu3, const float *logscale3, const float *quat4,
+                  const float *rho, void *stream);
+int64_t gaussians_count(const rgrt_gauss *g);
+
+/* ---- geometry (Eq. 3, section 3 arc correction) --------------------- */
+
+/* Validate the description and upload its tables (view frames, pixel
+ * coordinates).  RGRT_E_INVAL for non-positive sizes, non-finite or
+ * degenerate constants (dsd <= dso <= 0, radius^2 < s^2 of a bin, ...). */
+int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *desc, rgrt_geom **out);
+int geometry_destroy(rgrt_geom *g);
+int64_t geometry_num_rays(const rgrt_geom *g);
+
+/* ---- projector (Eqs. 4, 11, 12) ------------------------------------- */
+
+/* out_I[geometry_num_rays] = sum over Gaussians of rho sqrt(2 pi/A)
+ * exp(-m/2) Phi, Phi the erf factor of the finite segment.  Overwrites. */
+int project_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out_I,
+                    void *stream);
+
+/* Adjoint of project_forward: given dL/dI[geometry_num_rays], writes dL/dmu,
+ * dL/dlogscale, dL/dquat, dL/drho (overwrite, not accumulate; a null output
+ * is skipped).  The tile lists of the last project_forward of the same
+ * (Gaussians, geometry) are reused when the parameters are unchanged and the
+ * budget allowed keeping them; otherwise they are rebuilt. */
+int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom,
+                     const float *dL_dI, float *g_mu3, float *g_logscale3, float *g_quat4,
+                     float *g_rho, void *stream);
+
+/* One optimisation step: forward, loss and dL/dI against measurements
+ * y[geometry_num_rays], adjoint, and an Adam update of the Gaussians in
+ * place (Adam state kept on the device with the Gaussians).  t = step
+ * number (>= 1) for bias correction.  loss_out (host or device, may be
+ * null) receives the loss as a float. */
+int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
+              const rgrt_adam *hp, int t, float *loss_out, void *stream);
+
+/* ---- diagnostics ---------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rgrt_last_error(void);
+
+/* The FP32 covariance records the cull uses: Sigma packed
+ * (00,01,02,11,12,22), n x 6 floats (host or device). */
+int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *stream);
+
+/* Tile lists of views [v0, v1): n_keys_out = number of (tile, Gaussian)
+ * entries; tile_start[n_tiles + 1] (CSR offsets, tile id = (view - v0) *
+ * tiles_per_view + ty * tiles_x + tx) and gid[cap] (Gaussian ids, ascending
+ * within each tile).  Host or device outputs; RGRT_E_CAPACITY if cap is
+ * smaller than the number of entries (n_keys_out is still set). */
+int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
+                          int v1, int64_t *n_keys_out, uint32_t *tile_start, uint32_t *gid,
+                          int64_t cap, void *stream);
+
+/* Per-kernel timing: when enabled, every kernel launch of the library is
+ * bracketed by CUDA events on its stream.  rgrt_prof_get reports for the
+ * kernel named `name` the number of launches and their summed device time
+ * (ms) since the last reset (it synchronises the recorded events). */
+int rgrt_prof_enable(rgrt_ctx *ctx, int on);
+int rgrt_prof_reset(rgrt_ctx *ctx);
+int rgrt_prof_get(rgrt_ctx *ctx, const char *name, int64_t *launches, double *ms);
+/* Counters of the last forward: pairs evaluated and pairs with m <= 9. */
+int rgrt_stats_get(rgrt_ctx *ctx, int64_t *pairs_evaluated, int64_t *pairs_kept, int64_t *keys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RGRT_H */

@@ -1,0 +1,901 @@
+// C ABI of librgrt: contexts, Gaussians, geometries, and the stream-ordered
+// orchestration of the projector pipeline (records -> cull -> scan -> emit
+// -> radix sort -> tile ranges -> integrate / adjoint -> parameter chain).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rgrt.h"
+#include "rgrt_internal.h"
+
+using namespace rgrt;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(RGRT_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        int r_ = (expr);               \
+        if (r_ != RGRT_OK) return r_;  \
+    } while (0)
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ProfRec {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rgrt_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    // scratch
+    Buf cnt, off, rect, keys, vals, keys_alt, vals_alt, sort_tmp, scan_tmp, ranges, total;
+    Buf stage_in[4], stage_out[4], I, dLdI, y, grad, gflat, partial, stats, loss;
+    unsigned long long *h_total = nullptr;  // pinned
+    // binning cache
+    const rgrt_gauss *bin_g = nullptr;
+    const rgrt_geom *bin_geom = nullptr;
+    unsigned long long bin_version = 0;
+    int bin_v0 = -1, bin_nv = 0;
+    uint32_t bin_keys = 0;
+    bool bin_valid = false;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> pending;
+    std::map<std::string, std::pair<long long, double>> prof_acc;
+    long long last_keys = 0;
+};
+
+struct rgrt_gauss {
+    rgrt_ctx *ctx = nullptr;
+    int64_t n = 0;
+    bool owned = false;
+    float *mu = nullptr, *ls = nullptr, *q = nullptr, *rho = nullptr;
+    void *block = nullptr;     // owned parameter block (COPY)
+    float4 *rec = nullptr, *crec = nullptr;
+    float *adam_m = nullptr, *adam_v = nullptr;
+    unsigned long long version = 1;
+    size_t bytes = 0;
+};
+
+struct rgrt_geom {
+    rgrt_ctx *ctx = nullptr;
+    rgrt_geom_desc desc{};
+    DevGeom dg{};
+    float *d_tables = nullptr;
+    int64_t n_rays = 0;
+    int tiles_per_view = 0;
+    size_t bytes = 0;
+};
+
+namespace {
+
+int dev_alloc(rgrt_ctx *c, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (c->used + bytes > c->budget)
+        return fail(RGRT_E_NOMEM, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu used)",
+                    bytes, c->used, c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(RGRT_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    c->used += bytes;
+    return RGRT_OK;
+}
+
+void dev_free(rgrt_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    if (bytes == 0) bytes = 16;
+    c->used -= bytes;
+}
+
+int ensure(rgrt_ctx *c, Buf &b, size_t bytes)
+{
+    if (b.bytes >= bytes && b.p) return RGRT_OK;
+    size_t want = bytes + bytes / 8 + 256;
+    if (b.p) {
+        cudaFree(b.p);
+        c->used -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    TRY(dev_alloc(c, &b.p, want));
+    b.bytes = want;
+    return RGRT_OK;
+}
+
+void release(rgrt_ctx *c, Buf &b)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        c->used -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of an input array: the pointer itself, or a staged copy
+int stage_input(rgrt_ctx *c, Buf &b, const void *src, size_t bytes, cudaStream_t s, const void **out)
+{
+    if (!src || bytes == 0 || is_device_ptr(src)) {
+        *out = src;
+        return RGRT_OK;
+    }
+    TRY(ensure(c, b, bytes));
+    CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s));
+    *out = b.p;
+    return RGRT_OK;
+}
+
+// device buffer for an output; returns whether a copy-back is needed
+int stage_output(rgrt_ctx *c, Buf &b, void *dst, size_t bytes, void **out, bool *copy_back)
+{
+    *copy_back = false;
+    if (!dst || bytes == 0 || is_device_ptr(dst)) {
+        *out = dst;
+        return RGRT_OK;
+    }
+    TRY(ensure(c, b, bytes));
+    *out = b.p;
+    *copy_back = true;
+    return RGRT_OK;
+}
+
+// ---- profiling ------------------------------------------------------------
+
+struct ProfScope {
+    rgrt_ctx *c;
+    const char *name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(rgrt_ctx *c_, const char *n, cudaStream_t s_) : c(c_), name(n), s(s_)
+    {
+        if (c->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, s);
+    }
+    ~ProfScope()
+    {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            c->pending.push_back(ProfRec{ name, a, b });
+        }
+    }
+};
+
+void prof_harvest(rgrt_ctx *c)
+{
+    for (auto &r : c->pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &e = c->prof_acc[r.name];
+        e.first += 1;
+        e.second += ms;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->pending.clear();
+}
+
+#define PROF(name) ProfScope prof_scope_(ctx, name, s)
+
+// ---- pipeline pieces ------------------------------------------------------
+
+int build_records(rgrt_ctx *ctx, const rgrt_gauss *g, cudaStream_t s)
+{
+    if (g->n == 0) return RGRT_OK;
+    PROF("k_records");
+    CK(launch_records(g->mu, g->ls, g->q, g->rho, g->n, g->rec, g->crec, s));
+    return RGRT_OK;
+}
+
+int ceil_log2(uint64_t x)
+{
+    int b = 0;
+    while ((1ull << b) < x) b++;
+    return b;
+}
+
+// cull + scan + emit + sort + ranges for views [v0, v0 + nv); RGRT_E_CAPACITY
+// if the chunk's keys do not fit the budget (the caller then splits it)
+int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0, int nv,
+              cudaStream_t s, uint32_t *n_keys)
+{
+    const int64_t N = g->n;
+    const int64_t E = (int64_t)nv * N;
+    DevGeom dg = geom->dg;
+    dg.v0 = v0;
+    const uint32_t T = (uint32_t)nv * (uint32_t)geom->tiles_per_view;
+    TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)E));
+    TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)E));
+    TRY(ensure(ctx, ctx->rect, sizeof(uint2) * (size_t)E));
+    TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems(E)));
+    TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
+    TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)T));
+    {
+        PROF("k_cull");
+        CK(launch_cull(dg, nv, g->crec, N, (uint32_t *)ctx->cnt.p, (uint2 *)ctx->rect.p, s));
+    }
+    {
+        PROF("scan");
+        CK(launch_scan((uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p, E,
+                       (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
+    }
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    unsigned long long K = *ctx->h_total;
+    if (K >= 0xffffffffull)
+        return fail(RGRT_E_CAPACITY, "views %d..%d produce %llu tile entries (more than 2^32)", v0,
+                    v0 + nv, K);
+    size_t need = 4 * sizeof(uint32_t) * (size_t)K + sizeof(uint32_t) * sort_tmp_elems((uint32_t)K);
+    size_t have = ctx->keys.bytes + ctx->vals.bytes + ctx->keys_alt.bytes + ctx->vals_alt.bytes +
+                  ctx->sort_tmp.bytes;
+    if (need > have && ctx->used - have + need + need / 8 > ctx->budget)
+        return fail(RGRT_E_CAPACITY, "views %d..%d produce %llu tile entries, over the budget", v0,
+                    v0 + nv, K);
+    TRY(ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)K));
+    TRY(ensure(ctx, ctx->vals, sizeof(uint32_t) * (size_t)K));
+    TRY(ensure(ctx, ctx->keys_alt, sizeof(uint32_t) * (size_t)K));
+    TRY(ensure(ctx, ctx->vals_alt, sizeof(uint32_t) * (size_t)K));
+    TRY(ensure(ctx, ctx->sort_tmp, sizeof(uint32_t) * sort_tmp_elems((uint32_t)K)));
+    uint32_t *keys = (uint32_t *)ctx->keys.p, *vals = (uint32_t *)ctx->vals.p;
+    {
+        PROF("k_emit");
+        CK(launch_emit(dg, nv, N, (uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p,
+                       (uint2 *)ctx->rect.p, keys, vals, (uint32_t)K, s));
+    }
+    {
+        PROF("radix_sort");
+        CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
+                       (uint32_t)K, ceil_log2(T), (uint32_t *)ctx->sort_tmp.p, s));
+    }
+    {
+        PROF("k_ranges");
+        CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T, s));
+        CK(launch_ranges(keys, (uint32_t)K, (uint2 *)ctx->ranges.p, T, s));
+    }
+    *n_keys = (uint32_t)K;
+    ctx->last_keys += (long long)K;
+    ctx->bin_g = g;
+    ctx->bin_geom = geom;
+    ctx->bin_version = g->version;
+    ctx->bin_v0 = v0;
+    ctx->bin_nv = nv;
+    ctx->bin_keys = (uint32_t)K;
+    ctx->bin_valid = true;
+    return RGRT_OK;
+}
+
+// first chunk size: bounded per-(view, Gaussian) scratch
+int initial_chunk(const rgrt_gauss *g, const rgrt_geom *geom)
+{
+    const int64_t max_entries = (int64_t)1 << 27;
+    int64_t nv = g->n > 0 ? max_entries / g->n : geom->desc.n_views;
+    if (nv < 1) nv = 1;
+    if (nv > geom->desc.n_views) nv = geom->desc.n_views;
+    return (int)nv;
+}
+
+// run `body(v0, nv)` over view chunks, binning each first; chunks halve on
+// RGRT_E_CAPACITY.  reuse: keep the cached binning if it covers the chunk.
+template <class F>
+int for_chunks(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cudaStream_t s,
+               bool reuse, F body)
+{
+    int V = geom->desc.n_views;
+    int nv = initial_chunk(g, geom);
+    int v0 = 0;
+    while (v0 < V) {
+        int cur = nv < V - v0 ? nv : V - v0;
+        uint32_t K = 0;
+        bool cached = reuse && ctx->bin_valid && ctx->bin_g == g && ctx->bin_geom == geom &&
+                      ctx->bin_version == g->version && ctx->bin_v0 == v0 && ctx->bin_nv == cur;
+        if (!cached) {
+            int r = bin_views(ctx, g, geom, v0, cur, s, &K);
+            if (r == RGRT_E_CAPACITY && cur > 1) {
+                ctx->bin_valid = false;
+                nv = cur / 2;
+                continue;
+            }
+            if (r != RGRT_OK) {
+                ctx->bin_valid = false;
+                return r;
+            }
+        } else {
+            K = ctx->bin_keys;
+        }
+        TRY(body(v0, cur, K));
+        v0 += cur;
+    }
+    return RGRT_OK;
+}
+
+int check_ctx(rgrt_ctx *c)
+{
+    if (!c) return fail(RGRT_E_INVAL, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(RGRT_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return RGRT_OK;
+}
+
+int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out,
+                cudaStream_t s)
+{
+    if (g->n == 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)geom->n_rays, s));
+        return RGRT_OK;
+    }
+    TRY(build_records(ctx, g, s));
+    TRY(ensure(ctx, ctx->stats, sizeof(Stats)));
+    CK(cudaMemsetAsync(ctx->stats.p, 0, sizeof(Stats), s));
+    ctx->last_keys = 0;
+    return for_chunks(ctx, g, geom, s, false, [&](int v0, int nv, uint32_t K) -> int {
+        (void)K;
+        DevGeom dg = geom->dg;
+        dg.v0 = v0;
+        PROF("k_forward");
+        CK(launch_forward(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
+                          out, (Stats *)ctx->stats.p, s));
+        return RGRT_OK;
+    });
+}
+
+// adjoint into ctx->grad (zeroed first), then the parameter chain into the
+// four (device) outputs
+int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const float *dLdI,
+                 float *gm, float *gl, float *gq, float *gr, cudaStream_t s)
+{
+    const int64_t N = g->n;
+    if (N == 0) return RGRT_OK;
+    TRY(ensure(ctx, ctx->grad, sizeof(float4) * GRAD_F4 * (size_t)N));
+    CK(cudaMemsetAsync(ctx->grad.p, 0, sizeof(float4) * GRAD_F4 * (size_t)N, s));
+    bool reuse = ctx->bin_valid && ctx->bin_g == g && ctx->bin_geom == geom &&
+                 ctx->bin_version == g->version;
+    if (!reuse) TRY(build_records(ctx, g, s));
+    TRY(for_chunks(ctx, g, geom, s, reuse, [&](int v0, int nv, uint32_t K) -> int {
+        (void)K;
+        DevGeom dg = geom->dg;
+        dg.v0 = v0;
+        PROF("k_adjoint");
+        CK(launch_adjoint(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
+                          dLdI, (float4 *)ctx->grad.p, s));
+        return RGRT_OK;
+    }));
+    PROF("k_param_chain");
+    CK(launch_param_chain(g->mu, g->ls, g->q, g->rho, N, (float4 *)ctx->grad.p, gm, gl, gq, gr, s));
+    return RGRT_OK;
+}
+
+int validate_desc(const rgrt_geom_desc *d)
+{
+    if (!d) return fail(RGRT_E_INVAL, "null geometry description");
+    if (d->kind < 0 || d->kind > 2) return fail(RGRT_E_INVAL, "unknown geometry kind %d", d->kind);
+    if (d->n_views <= 0 || d->n_rows <= 0 || d->n_cols <= 0)
+        return fail(RGRT_E_INVAL, "geometry sizes must be positive (%d views, %d x %d)", d->n_views,
+                    d->n_rows, d->n_cols);
+    int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
+    if (tw % 8 || th % 4 || tw * th > 256 || tw * th < 32)
+        return fail(RGRT_E_INVAL, "tile %dx%d: width a multiple of 8, height of 4, 32..256 rays", tw, th);
+    if ((d->n_cols + tw - 1) / tw > 65535 || (d->n_rows + th - 1) / th > 65535)
+        return fail(RGRT_E_INVAL, "too many tiles per detector axis");
+    if ((int64_t)d->n_views * ((d->n_cols + tw - 1) / tw) * ((d->n_rows + th - 1) / th) > (1 << 30))
+        return fail(RGRT_E_INVAL, "too many tiles");
+    if (d->kind != RGRT_GEOM_PET_RING) {
+        if (!d->angles) return fail(RGRT_E_INVAL, "CT geometry needs view angles");
+        for (int v = 0; v < d->n_views; v++)
+            if (!std::isfinite(d->angles[v])) return fail(RGRT_E_INVAL, "non-finite view angle %d", v);
+        if (!(d->pitch_u > 0) || !(d->pitch_v > 0) || !std::isfinite(d->pitch_u) ||
+            !std::isfinite(d->pitch_v))
+            return fail(RGRT_E_INVAL, "detector pitch must be positive and finite");
+    }
+    if (d->kind == RGRT_GEOM_CT_PARALLEL) {
+        if (std::isnan(d->t_a) || std::isnan(d->t_b) || !(d->t_a < d->t_b))
+            return fail(RGRT_E_INVAL, "parallel-beam segment needs t_a < t_b");
+    }
+    if (d->kind == RGRT_GEOM_CT_CONE) {
+        if (!(d->dso > 0) || !(d->dsd > d->dso) || !std::isfinite(d->dsd))
+            return fail(RGRT_E_INVAL, "cone beam needs 0 < dso < dsd (finite)");
+    }
+    if (d->kind == RGRT_GEOM_PET_RING) {
+        if (!(d->radius > 0) || !std::isfinite(d->radius) || d->n_crystals <= 0)
+            return fail(RGRT_E_INVAL, "PET ring needs radius > 0 and crystals > 0");
+        if (!(d->pitch_v > 0) || !std::isfinite(d->pitch_v))
+            return fail(RGRT_E_INVAL, "PET plane spacing must be positive");
+        if (d->arc_mode != 0 && d->arc_mode != 1) return fail(RGRT_E_INVAL, "arc_mode must be 0 or 1");
+        double c = 0.5 * (double)(d->n_cols - 1);
+        double smax = d->arc_mode == 0 ? c * (M_PI * d->radius / d->n_crystals) : d->radius;
+        if (d->arc_mode == 1 && c * M_PI / d->n_crystals >= M_PI / 2)
+            return fail(RGRT_E_INVAL, "raw radial bins reach beyond the ring");
+        if (d->arc_mode == 0 && !(smax < d->radius))
+            return fail(RGRT_E_INVAL, "radial bins reach beyond the ring");
+    }
+    return RGRT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported API
+// ===========================================================================
+
+extern "C" {
+
+const char *rgrt_last_error(void) { return g_err.c_str(); }
+
+int rgrt_ctx_create(rgrt_ctx **out, int device, size_t budget)
+{
+    if (!out) return fail(RGRT_E_INVAL, "null output");
+    *out = nullptr;
+    int nd = 0;
+    cudaError_t e = cudaGetDeviceCount(&nd);
+    if (e != cudaSuccess) return fail(RGRT_E_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= nd) return fail(RGRT_E_INVAL, "device %d of %d", device, nd);
+    CK(cudaSetDevice(device));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    rgrt_ctx *c = new (std::nothrow) rgrt_ctx();
+    if (!c) return fail(RGRT_E_NOMEM, "host allocation failed");
+    c->device = device;
+    c->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+    e = cudaMallocHost((void **)&c->h_total, sizeof(unsigned long long) * 2);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(RGRT_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return RGRT_OK;
+}
+
+int rgrt_ctx_destroy(rgrt_ctx *c)
+{
+    if (!c) return RGRT_OK;
+    cudaSetDevice(c->device);
+    prof_harvest(c);
+    Buf *bufs[] = { &c->cnt, &c->off, &c->rect, &c->keys, &c->vals, &c->keys_alt, &c->vals_alt,
+                    &c->sort_tmp, &c->scan_tmp, &c->ranges, &c->total, &c->I, &c->dLdI, &c->y,
+                    &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss };
+    for (Buf *b : bufs) release(c, *b);
+    for (auto &b : c->stage_in) release(c, b);
+    for (auto &b : c->stage_out) release(c, b);
+    if (c->h_total) cudaFreeHost(c->h_total);
+    delete c;
+    return RGRT_OK;
+}
+
+int gaussians_create(rgrt_ctx *ctx, int64_t n, const float *mu3, const float *ls3, const float *q4,
+                     const float *rho, int flags, rgrt_gauss **out)
+{
+    TRY(check_ctx(ctx));
+    if (!out) return fail(RGRT_E_INVAL, "null output");
+    *out = nullptr;
+    if (n < 0 || n > (int64_t)0x7fffffff) return fail(RGRT_E_INVAL, "Gaussian count %lld", (long long)n);
+    if (n > 0 && (!mu3 || !ls3 || !q4 || !rho)) return fail(RGRT_E_INVAL, "null parameter array");
+    if (flags != RGRT_COPY && flags != RGRT_BORROW) return fail(RGRT_E_INVAL, "flags %d", flags);
+    if (flags == RGRT_BORROW && n > 0 &&
+        !(is_device_ptr(mu3) && is_device_ptr(ls3) && is_device_ptr(q4) && is_device_ptr(rho)))
+        return fail(RGRT_E_INVAL, "RGRT_BORROW needs device arrays");
+    rgrt_gauss *g = new (std::nothrow) rgrt_gauss();
+    if (!g) return fail(RGRT_E_NOMEM, "host allocation failed");
+    g->ctx = ctx;
+    g->n = n;
+    g->owned = flags == RGRT_COPY;
+    size_t recb = sizeof(float4) * (REC_F4 + CREC_F4) * (size_t)(n > 0 ? n : 1);
+    size_t parb = g->owned ? sizeof(float) * 11 * (size_t)n : 0;
+    g->bytes = recb + parb;
+    void *blk = nullptr;
+    int r = dev_alloc(ctx, &blk, g->bytes);
+    if (r != RGRT_OK) {
+        delete g;
+        return r;
+    }
+    g->block = blk;
+    g->rec = (float4 *)blk;
+    g->crec = g->rec + REC_F4 * (size_t)(n > 0 ? n : 1);
+    if (g->owned) {
+        float *p = (float *)(g->crec + CREC_F4 * (size_t)(n > 0 ? n : 1));
+        g->mu = p;
+        g->ls = p + 3 * n;
+        g->q = p + 6 * n;
+        g->rho = p + 10 * n;
+        if (n > 0) {
+            cudaMemcpy(g->mu, mu3, sizeof(float) * 3 * n, cudaMemcpyDefault);
+            cudaMemcpy(g->ls, ls3, sizeof(float) * 3 * n, cudaMemcpyDefault);
+            cudaMemcpy(g->q, q4, sizeof(float) * 4 * n, cudaMemcpyDefault);
+            cudaError_t e = cudaMemcpy(g->rho, rho, sizeof(float) * n, cudaMemcpyDefault);
+            if (e != cudaSuccess) {
+                dev_free(ctx, blk, g->bytes);
+                delete g;
+                return fail(RGRT_E_CUDA, "copying parameters: %s", cudaGetErrorString(e));
+            }
+        }
+    } else {
+        g->mu = const_cast<float *>(mu3);
+        g->ls = const_cast<float *>(ls3);
+        g->q = const_cast<float *>(q4);
+        g->rho = const_cast<float *>(rho);
+    }
+    *out = g;
+    return RGRT_OK;
+}
+
+int gaussians_destroy(rgrt_gauss *g)
+{
+    if (!g) return RGRT_OK;
+    rgrt_ctx *c = g->ctx;
+    cudaSetDevice(c->device);
+    if (c->bin_g == g) c->bin_valid = false;
+    dev_free(c, g->block, g->bytes);
+    if (g->adam_m) dev_free(c, g->adam_m, sizeof(float) * 22 * (size_t)g->n);
+    delete g;
+    return RGRT_OK;
+}
+
+int64_t gaussians_count(const rgrt_gauss *g) { return g ? g->n : -1; }
+
+int gaussians_get(rgrt_gauss *g, float *mu3, float *ls3, float *q4, float *rho, void *stream)
+{
+    if (!g) return fail(RGRT_E_INVAL, "null Gaussians");
+    TRY(check_ctx(g->ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t n = (size_t)g->n;
+    if (n == 0) return RGRT_OK;
+    if (mu3) CK(cudaMemcpyAsync(mu3, g->mu, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+    if (ls3) CK(cudaMemcpyAsync(ls3, g->ls, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+    if (q4) CK(cudaMemcpyAsync(q4, g->q, sizeof(float) * 4 * n, cudaMemcpyDefault, s));
+    if (rho) CK(cudaMemcpyAsync(rho, g->rho, sizeof(float) * n, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return RGRT_OK;
+}
+
+int gaussians_set(rgrt_gauss *g, const float *mu3, const float *ls3, const float *q4,
+                  const float *rho, void *stream)
+{
+    if (!g) return fail(RGRT_E_INVAL, "null Gaussians");
+    TRY(check_ctx(g->ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t n = (size_t)g->n;
+    if (n > 0) {
+        if (mu3 && mu3 != g->mu) CK(cudaMemcpyAsync(g->mu, mu3, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+        if (ls3 && ls3 != g->ls) CK(cudaMemcpyAsync(g->ls, ls3, sizeof(float) * 3 * n, cudaMemcpyDefault, s));
+        if (q4 && q4 != g->q) CK(cudaMemcpyAsync(g->q, q4, sizeof(float) * 4 * n, cudaMemcpyDefault, s));
+        if (rho && rho != g->rho) CK(cudaMemcpyAsync(g->rho, rho, sizeof(float) * n, cudaMemcpyDefault, s));
+    }
+    g->version++;
+    return RGRT_OK;
+}
+
+int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *d, rgrt_geom **out)
+{
+    TRY(check_ctx(ctx));
+    if (!out) return fail(RGRT_E_INVAL, "null output");
+    *out = nullptr;
+    TRY(validate_desc(d));
+    rgrt_geom *g = new (std::nothrow) rgrt_geom();
+    if (!g) return fail(RGRT_E_NOMEM, "host allocation failed");
+    g->ctx = ctx;
+    g->desc = *d;
+    g->desc.angles = nullptr;
+    const int V = d->n_views, H = d->n_rows, W = d->n_cols;
+    const int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
+    g->desc.tile_w = tw;
+    g->desc.tile_h = th;
+    // host tables: the binary32 rounding of the binary64 geometry
+    std::vector<float> tab((size_t)9 * V + W + H);
+    const double PI = 3.14159265358979323846;
+    for (int v = 0; v < V; v++) {
+        double eu[3], ev[3], ew[3];
+        if (d->kind == RGRT_GEOM_PET_RING) {
+            double phi = (PI * (double)v) / (double)V;
+            double c = cos(phi), s = sin(phi);
+            eu[0] = c; eu[1] = s; eu[2] = 0.0;
+            ew[0] = s; ew[1] = -c; ew[2] = 0.0;
+        } else {
+            double th_ = d->angles[v];
+            double c = cos(th_), s = sin(th_);
+            ew[0] = c; ew[1] = s; ew[2] = 0.0;
+            eu[0] = -s; eu[1] = c; eu[2] = 0.0;
+        }
+        ev[0] = 0.0; ev[1] = 0.0; ev[2] = 1.0;
+        for (int k = 0; k < 3; k++) {
+            tab[9 * v + k] = (float)eu[k];
+            tab[9 * v + 3 + k] = (float)ev[k];
+            tab[9 * v + 6 + k] = (float)ew[k];
+        }
+    }
+    float *ut = tab.data() + 9 * (size_t)V, *vt = ut + W;
+    for (int i = 0; i < W; i++) {
+        double k = (double)i - 0.5 * (double)(W - 1);
+        double u;
+        if (d->kind == RGRT_GEOM_PET_RING)
+            u = d->arc_mode == 0 ? k * ((PI * d->radius) / (double)d->n_crystals)
+                                 : d->radius * sin((k * PI) / (double)d->n_crystals);
+        else
+            u = k * d->pitch_u;
+        ut[i] = (float)u;
+    }
+    for (int j = 0; j < H; j++) vt[j] = (float)(((double)j - 0.5 * (double)(H - 1)) * d->pitch_v);
+    g->bytes = sizeof(float) * tab.size();
+    int r = dev_alloc(ctx, (void **)&g->d_tables, g->bytes);
+    if (r != RGRT_OK) {
+        delete g;
+        return r;
+    }
+    cudaError_t e = cudaMemcpy(g->d_tables, tab.data(), g->bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dev_free(ctx, g->d_tables, g->bytes);
+        delete g;
+        return fail(RGRT_E_CUDA, "uploading geometry tables: %s", cudaGetErrorString(e));
+    }
+    DevGeom &dg = g->dg;
+    dg.kind = d->kind == RGRT_GEOM_CT_CONE ? 1 : 0;
+    dg.pet = d->kind == RGRT_GEOM_PET_RING;
+    dg.n_views = V; dg.n_rows = H; dg.n_cols = W;
+    dg.tile_w = tw; dg.tile_h = th;
+    dg.tiles_x = (W + tw - 1) / tw;
+    dg.tiles_y = (H + th - 1) / th;
+    dg.v0 = 0;
+    if (dg.pet) { dg.stride_view = W; dg.stride_row = (long long)V * W; }
+    else { dg.stride_view = (long long)H * W; dg.stride_row = W; }
+    dg.dso = (float)d->dso;
+    dg.dsd = (float)d->dsd;
+    dg.t_a = (float)d->t_a;
+    dg.t_b = (float)d->t_b;
+    dg.radius2 = (float)(d->radius * d->radius);
+    dg.frames = g->d_tables;
+    dg.utab = g->d_tables + 9 * (size_t)V;
+    dg.vtab = dg.utab + W;
+    g->tiles_per_view = dg.tiles_x * dg.tiles_y;
+    g->n_rays = (int64_t)V * H * W;
+    *out = g;
+    return RGRT_OK;
+}
+
+int geometry_destroy(rgrt_geom *g)
+{
+    if (!g) return RGRT_OK;
+    rgrt_ctx *c = g->ctx;
+    cudaSetDevice(c->device);
+    if (c->bin_geom == g) c->bin_valid = false;
+    dev_free(c, g->d_tables, g->bytes);
+    delete g;
+    return RGRT_OK;
+}
+
+int64_t geometry_num_rays(const rgrt_geom *g) { return g ? g->n_rays : -1; }
+
+int project_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out_I,
+                    void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !geom || !out_I) return fail(RGRT_E_INVAL, "null argument");
+    if (g->ctx != ctx || geom->ctx != ctx) return fail(RGRT_E_INVAL, "objects of another context");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dout;
+    bool back;
+    size_t ob = sizeof(float) * (size_t)geom->n_rays;
+    TRY(stage_output(ctx, ctx->stage_out[0], out_I, ob, &dout, &back));
+    TRY(run_forward(ctx, g, geom, (float *)dout, s));
+    if (back) {
+        CK(cudaMemcpyAsync(out_I, dout, ob, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RGRT_OK;
+}
+
+int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const float *dL_dI,
+                     float *g_mu3, float *g_ls3, float *g_q4, float *g_rho, void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !geom || !dL_dI) return fail(RGRT_E_INVAL, "null argument");
+    if (g->ctx != ctx || geom->ctx != ctx) return fail(RGRT_E_INVAL, "objects of another context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *dw;
+    TRY(stage_input(ctx, ctx->stage_in[0], dL_dI, sizeof(float) * (size_t)geom->n_rays, s, &dw));
+    size_t n = (size_t)g->n;
+    float *outs[4] = { g_mu3, g_ls3, g_q4, g_rho };
+    const size_t sz[4] = { 3 * n, 3 * n, 4 * n, n };
+    void *dev[4];
+    bool back[4];
+    for (int k = 0; k < 4; k++)
+        TRY(stage_output(ctx, ctx->stage_out[k], outs[k], sizeof(float) * sz[k], &dev[k], &back[k]));
+    TRY(run_backward(ctx, g, geom, (const float *)dw, (float *)dev[0], (float *)dev[1],
+                     (float *)dev[2], (float *)dev[3], s));
+    bool any = false;
+    for (int k = 0; k < 4; k++)
+        if (back[k]) {
+            CK(cudaMemcpyAsync(outs[k], dev[k], sizeof(float) * sz[k], cudaMemcpyDeviceToHost, s));
+            any = true;
+        }
+    if (any) CK(cudaStreamSynchronize(s));
+    return RGRT_OK;
+}
+
+int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
+              const rgrt_adam *hp, int t, float *loss_out, void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !geom || !y || !hp) return fail(RGRT_E_INVAL, "null argument");
+    if (g->ctx != ctx || geom->ctx != ctx) return fail(RGRT_E_INVAL, "objects of another context");
+    if (loss != RGRT_LOSS_L2 && loss != RGRT_LOSS_POISSON) return fail(RGRT_E_INVAL, "loss %d", loss);
+    if (t < 1) return fail(RGRT_E_INVAL, "Adam step t must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t R = geom->n_rays, N = g->n;
+    const void *dy;
+    TRY(stage_input(ctx, ctx->stage_in[0], y, sizeof(float) * (size_t)R, s, &dy));
+    TRY(ensure(ctx, ctx->I, sizeof(float) * (size_t)R));
+    TRY(ensure(ctx, ctx->dLdI, sizeof(float) * (size_t)R));
+    int nblk = loss_blocks(R);
+    TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)nblk));
+    TRY(ensure(ctx, ctx->loss, sizeof(float) * 4));
+    TRY(run_forward(ctx, g, geom, (float *)ctx->I.p, s));
+    {
+        PROF("k_loss");
+        CK(launch_loss(loss, (float *)ctx->I.p, (const float *)dy, R, hp->kappa, hp->poisson_eps,
+                       (float *)ctx->dLdI.p, (double *)ctx->partial.p, nblk, (float *)ctx->loss.p, s));
+    }
+    if (N > 0) {
+        TRY(ensure(ctx, ctx->gflat, sizeof(float) * 11 * (size_t)N));
+        float *gf = (float *)ctx->gflat.p;
+        TRY(run_backward(ctx, g, geom, (float *)ctx->dLdI.p, gf, gf + 3 * N, gf + 6 * N, gf + 10 * N, s));
+        if (!g->adam_m) {
+            void *p = nullptr;
+            TRY(dev_alloc(ctx, &p, sizeof(float) * 22 * (size_t)N));
+            CK(cudaMemsetAsync(p, 0, sizeof(float) * 22 * (size_t)N, s));
+            g->adam_m = (float *)p;
+            g->adam_v = g->adam_m + 11 * N;
+        }
+        float bc1 = (float)(1.0 - pow((double)hp->beta1, (double)t));
+        float bc2 = (float)(1.0 - pow((double)hp->beta2, (double)t));
+        float *ps[4] = { g->mu, g->ls, g->q, g->rho };
+        const int64_t off[4] = { 0, 3 * N, 6 * N, 10 * N }, len[4] = { 3 * N, 3 * N, 4 * N, N };
+        const float lr[4] = { hp->lr_mu, hp->lr_logscale, hp->lr_quat, hp->lr_rho };
+        PROF("k_adam");
+        for (int k = 0; k < 4; k++)
+            CK(launch_adam(ps[k], gf + off[k], g->adam_m + off[k], g->adam_v + off[k], len[k], lr[k],
+                           hp->beta1, hp->beta2, hp->eps, bc1, bc2, s));
+        g->version++;
+    }
+    if (loss_out) CK(cudaMemcpyAsync(loss_out, ctx->loss.p, sizeof(float), cudaMemcpyDefault, s));
+    if (loss_out && !is_device_ptr(loss_out)) CK(cudaStreamSynchronize(s));
+    return RGRT_OK;
+}
+
+int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !sigma6) return fail(RGRT_E_INVAL, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(build_records(ctx, g, s));
+    std::vector<float4> h((size_t)CREC_F4 * g->n);
+    if (g->n > 0)
+        CK(cudaMemcpyAsync(h.data(), g->crec, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<float> o((size_t)6 * g->n);
+    for (int64_t k = 0; k < g->n; k++) {
+        float4 a = h[CREC_F4 * k + 1], b = h[CREC_F4 * k + 2];
+        float v[6] = { a.x, a.y, a.z, a.w, b.x, b.y };
+        memcpy(&o[6 * k], v, sizeof(v));
+    }
+    if (!o.empty()) CK(cudaMemcpy(sigma6, o.data(), sizeof(float) * o.size(), cudaMemcpyDefault));
+    return RGRT_OK;
+}
+
+int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0, int v1,
+                          int64_t *n_keys_out, uint32_t *tile_start, uint32_t *gid, int64_t cap,
+                          void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !geom || !n_keys_out || !tile_start) return fail(RGRT_E_INVAL, "null argument");
+    if (v0 < 0 || v1 > geom->desc.n_views || v0 >= v1) return fail(RGRT_E_INVAL, "view range");
+    cudaStream_t s = (cudaStream_t)stream;
+    int nv = v1 - v0;
+    uint32_t T = (uint32_t)nv * (uint32_t)geom->tiles_per_view;
+    std::vector<uint32_t> start(T + 1, 0);
+    uint32_t K = 0;
+    if (g->n > 0) {
+        TRY(build_records(ctx, g, s));
+        TRY(bin_views(ctx, g, geom, v0, nv, s, &K));
+        std::vector<uint2> rg(T);
+        CK(cudaMemcpyAsync(rg.data(), ctx->ranges.p, sizeof(uint2) * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint32_t pos = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            start[t] = pos;
+            if (rg[t].y > rg[t].x) {
+                if (rg[t].x != pos) return fail(RGRT_E_CUDA, "tile ranges are not contiguous");
+                pos = rg[t].y;
+            }
+        }
+        start[T] = pos;
+        if (pos != K) return fail(RGRT_E_CUDA, "tile ranges cover %u of %u entries", pos, K);
+    }
+    *n_keys_out = K;
+    CK(cudaMemcpy(tile_start, start.data(), sizeof(uint32_t) * (T + 1), cudaMemcpyDefault));
+    if ((int64_t)K > cap) return fail(RGRT_E_CAPACITY, "%u entries, capacity %lld", K, (long long)cap);
+    if (K > 0 && gid) CK(cudaMemcpy(gid, ctx->vals.p, sizeof(uint32_t) * K, cudaMemcpyDefault));
+    return RGRT_OK;
+}
+
+int rgrt_prof_enable(rgrt_ctx *ctx, int on)
+{
+    if (!ctx) return fail(RGRT_E_INVAL, "null context");
+    ctx->prof = on != 0;
+    return RGRT_OK;
+}
+
+int rgrt_prof_reset(rgrt_ctx *ctx)
+{
+    if (!ctx) return fail(RGRT_E_INVAL, "null context");
+    prof_harvest(ctx);
+    ctx->prof_acc.clear();
+    return RGRT_OK;
+}
+
+int rgrt_prof_get(rgrt_ctx *ctx, const char *name, int64_t *launches, double *ms)
+{
+    if (!ctx || !name) return fail(RGRT_E_INVAL, "null argument");
+    prof_harvest(ctx);
+    auto it = ctx->prof_acc.find(name);
+    if (launches) *launches = it == ctx->prof_acc.end() ? 0 : it->second.first;
+    if (ms) *ms = it == ctx->prof_acc.end() ? 0.0 : it->second.second;
+    return RGRT_OK;
+}
+
+int rgrt_stats_get(rgrt_ctx *ctx, int64_t *pairs_evaluated, int64_t *pairs_kept, int64_t *keys)
+{
+    TRY(check_ctx(ctx));
+    Stats st{ 0, 0 };
+    if (ctx->stats.p) CK(cudaMemcpy(&st, ctx->stats.p, sizeof(Stats), cudaMemcpyDeviceToHost));
+    if (pairs_evaluated) *pairs_evaluated = (int64_t)st.pairs_eval;
+    if (pairs_kept) *pairs_kept = (int64_t)st.pairs_kept;
+    if (keys) *keys = ctx->last_keys;
+    return RGRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// Binning (a2, second half): exclusive scan of per-(view, Gaussian) tile
+// counts, emission of (tile, Gaussian) keys, a stable LSD radix sort on the
+// tile bits, and per-tile ranges.  Keys are emitted in (view, Gaussian) order
+// and the sort is stable, so each tile's list ends up in ascending Gaussian
+// order: the lists are canonical and the per-ray sums deterministic.
+#include "rgrt_internal.h"
+
+namespace rgrt {
+namespace {
+
+constexpr int SCAN_BS = 256;
+constexpr int SCAN_IPT = 16;
+constexpr int SCAN_TILE = SCAN_BS * SCAN_IPT;
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sh)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n, unsigned long long *part)
+{
+    __shared__ unsigned long long sh[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; i++) {
+        int64_t x = base + (int64_t)i * SCAN_BS + threadIdx.x;
+        if (x < n) s += in[x];
+    }
+    s = block_sum_u64(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// single block: exclusive scan of part[0..nb) in place, total to *total
+__global__ void k_scan_top(unsigned long long *part, int64_t nb, unsigned long long *total)
+{
+    __shared__ unsigned long long sh[32];
+    __shared__ unsigned long long carry_sh;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_sh = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        int64_t x = base + threadIdx.x;
+        unsigned long long v = x < nb ? part[x] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) sh[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            unsigned long long s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
+            unsigned long long si = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) si += t;
+            }
+            if (lane < (int)(blockDim.x >> 5)) sh[lane] = si - s;
+        }
+        __syncthreads();
+        unsigned long long carry = carry_sh;
+        unsigned long long excl = carry + sh[w] + inc - v;
+        if (x < nb) part[x] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_sh = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry_sh;
+}
+
+__global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                            const unsigned long long *__restrict__ part)
+{
+    __shared__ uint32_t sm[SCAN_TILE];
+    __shared__ uint32_t wsum[SCAN_BS / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; i++) {
+        int64_t x = base + (int64_t)i * SCAN_BS + t;
+        sm[i * SCAN_BS + t] = x < n ? in[x] : 0u;
+    }
+    __syncthreads();
+    uint32_t loc[SCAN_IPT];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_IPT; j++) { loc[j] = sm[t * SCAN_IPT + j]; s += loc[j]; }
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = lane < SCAN_BS / 32 ? wsum[lane] : 0u;
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += u;
+        }
+        if (lane < SCAN_BS / 32) wsum[lane] = vi - v;
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)part[blockIdx.x] + wsum[w] + inc - s;
+#pragma unroll
+    for (int j = 0; j < SCAN_IPT; j++) { sm[t * SCAN_IPT + j] = run; run += loc[j]; }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; i++) {
+        int64_t x = base + (int64_t)i * SCAN_BS + t;
+        if (x < n) out[x] = sm[i * SCAN_BS + t];
+    }
+}
+
+// one thread per (view of the chunk, Gaussian): write its tiles' keys
+__global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict__ cnt,
+                       const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
+                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t cap)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nv * n) return;
+    uint32_t c = cnt[idx];
+    if (c == 0) return;
+    if ((uint64_t)off[idx] + c > cap) return;  // never taken when the scan is consistent
+    int vl = (int)(idx / n);
+    uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
+    uint2 r = rect[idx];
+    uint32_t tx0 = r.x & 0xffffu, tx1 = r.x >> 16, ty0 = r.y & 0xffffu, ty1 = r.y >> 16;
+    uint32_t o = off[idx];
+    uint32_t tbase = (uint32_t)vl * (uint32_t)(g.tiles_x * g.tiles_y);
+    for (uint32_t ty = ty0; ty <= ty1; ty++)
+        for (uint32_t tx = tx0; tx <= tx1; tx++) {
+            keys[o] = tbase + ty * (uint32_t)g.tiles_x + tx;
+            vals[o] = k;
+            o++;
+        }
+}
+
+constexpr int SORT_BS = 256;     // one thread per digit value
+constexpr int SORT_ROUNDS = 8;
+constexpr int SORT_TILE = SORT_BS * SORT_ROUNDS;
+
+__global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int shift,
+                            uint32_t *__restrict__ hist, uint32_t nb)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t base = blockIdx.x * SORT_TILE;
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; r++) {
+        uint32_t i = base + r * SORT_BS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// stable scatter: rank of a key = keys with the same digit in earlier rounds
+// of this block + in earlier warps of this round + in lower lanes of its warp
+__global__ void k_sort_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                               uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals, uint32_t n,
+                               int shift, const uint32_t *__restrict__ offs, uint32_t nb)
+{
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wc[SORT_BS / 32][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    run[t] = offs[(size_t)t * nb + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t base = blockIdx.x * SORT_TILE;
+    for (int r = 0; r < SORT_ROUNDS; r++) {
+#pragma unroll
+        for (int ww = 0; ww < SORT_BS / 32; ww++) wc[ww][t] = 0;
+        __syncthreads();
+        uint32_t i = base + r * SORT_BS + t;
+        bool valid = i < n;
+        uint32_t key = valid ? keys[i] : 0u;
+        uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wc[w][d] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = run[t];
+#pragma unroll
+        for (int ww = 0; ww < SORT_BS / 32; ww++) {
+            uint32_t c = wc[ww][t];
+            wc[ww][t] = acc;
+            acc += c;
+        }
+        run[t] = acc;
+        __syncthreads();
+        if (valid) {
+            uint32_t dst = wc[w][d] + rank;
+            if (dst >= n) dst = i;  // never taken when the histogram scan is consistent
+            okeys[dst] = key;
+            ovals[dst] = vals[i];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n, uint2 *__restrict__ ranges,
+                         uint32_t n_tiles)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = keys[i];
+    if (k >= n_tiles) return;  // never taken: emitted tile ids are < n_tiles
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+}
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t n)
+{
+    return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1;
+}
+
+cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total,
+                        unsigned long long *tmp, cudaStream_t s)
+{
+    if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, n, tmp);
+    k_scan_top<<<1, 1024, 0, s>>>(tmp, nb, total);
+    k_scan_down<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, out, n, tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
+                        const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
+                        uint32_t cap, cudaStream_t s)
+{
+    int64_t tot = (int64_t)nv * n;
+    if (tot <= 0) return cudaSuccess;
+    k_emit<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap);
+    return cudaGetLastError();
+}
+
+size_t sort_tmp_elems(uint32_t n)
+{
+    size_t nb = ((size_t)n + SORT_TILE - 1) / SORT_TILE;
+    return 2 * 256 * nb + 2 * (nb * 256 / SCAN_TILE + 2) + 8;
+}
+
+cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    uint32_t nb = (n + SORT_TILE - 1) / SORT_TILE;
+    size_t hn = (size_t)256 * nb;
+    uint32_t *hist = tmp;
+    uint32_t *offs = tmp + hn;
+    // the scan's 64-bit scratch sits 8-byte aligned after the two u32 arrays
+    unsigned long long *stmp = (unsigned long long *)(tmp + ((2 * hn + 1) & ~(size_t)1));
+    unsigned long long *stot = stmp + scan_tmp_elems((int64_t)hn);
+    uint32_t *src_k = keys, *src_v = vals, *dst_k = keys_alt, *dst_v = vals_alt;
+    int passes = (bits + 7) / 8;
+    if (passes < 1) passes = 1;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        k_sort_hist<<<nb, SORT_BS, 0, s>>>(src_k, n, shift, hist, nb);
+        cudaError_t e = launch_scan(hist, offs, (int64_t)hn, stot, stmp, s);
+        if (e != cudaSuccess) return e;
+        k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, offs, nb);
+        uint32_t *tk = src_k, *tv = src_v;
+        src_k = dst_k; src_v = dst_v; dst_k = tk; dst_v = tv;
+    }
+    if (src_k != keys) {  // odd pass count: bring the result home
+        cudaMemcpyAsync(keys, src_k, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
+                          cudaStream_t s)
+{
+    if (n_keys == 0) return cudaSuccess;
+    k_ranges<<<(n_keys + 255) / 256, 256, 0, s>>>(keys, n_keys, ranges, n_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace rgrt

@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA translation units of librgrt.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rgrt {
+
+// Geometry as the kernels see it.  kind: 0 = parallel rays (CT parallel and
+// PET), 1 = cone beam.  pet != 0 selects the PET chord segment and the
+// [plane][angle][radial] output layout.
+struct DevGeom {
+    int kind, pet;
+    int n_views, n_rows, n_cols;
+    int tile_w, tile_h, tiles_x, tiles_y;
+    int v0;                       // first view of the current chunk
+    long long stride_view, stride_row;
+    float dso, dsd, t_a, t_b, radius2;
+    const float *frames;          // n_views x 9 : e_u, e_v, e_w
+    const float *utab;            // n_cols pixel u coordinates
+    const float *vtab;            // n_rows pixel v coordinates
+};
+
+// Per-Gaussian records built once per parameter version.
+//   rec  : 5 float4 = (mu, rho), (P00 P01 P02 P11), (P12 P22 S00 S01),
+//          (S02 S11 S12 S22), (sigma_max, 0, 0, 0);  P = Sigma^-1, S = Sigma/det Sigma
+//   crec : 3 float4 = (mu, 0), (Sig00 Sig01 Sig02 Sig11), (Sig12 Sig22 0 0)
+//          -- the FP32 culling record, bit-exact by specification.
+constexpr int REC_F4 = 5;
+constexpr int CREC_F4 = 3;
+
+// Gradient accumulator per Gaussian: 4 float4 =
+//   (dmu, drho), (GP00 GP01 GP02 GP11), (GP12 GP22 GS00 GS01), (GS02 GS11 GS12 GS22)
+// GP, GS: symmetric-matrix gradients w.r.t. P and S (entry (a,b) == (b,a)).
+constexpr int GRAD_F4 = 4;
+
+// culling constant K^2 (K = 3.0104, a margin over the 3-sigma pair cut)
+constexpr float CULL_K2 = 9.0625f;
+// pair cut-off: m <= 9
+constexpr float PAIR_CUT2 = 9.0f;
+
+struct Stats {
+    unsigned long long pairs_eval, pairs_kept;
+};
+
+// ---- launchers (each returns cudaGetLastError of its launch) -------------
+cudaError_t launch_records(const float *mu, const float *ls, const float *q, const float *rho,
+                           int64_t n, float4 *rec, float4 *crec, cudaStream_t s);
+cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n, uint32_t *cnt,
+                        uint2 *rect, cudaStream_t s);
+cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
+                        const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
+                        uint32_t cap, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
+                          cudaStream_t s);
+
+// exclusive scan of n u32 values; writes out[0..n) and the 64-bit total to
+// *total (device).  tmp must hold scan_tmp_elems(n) u64.
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned long long *total,
+                        unsigned long long *tmp, cudaStream_t s);
+
+// stable LSD radix sort of (keys, vals) by the low `bits` key bits; results
+// end in (keys, vals) (alt buffers are scratch).  tmp must hold
+// sort_tmp_elems(n) u32.
+size_t sort_tmp_elems(uint32_t n);
+cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s);
+
+cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
+                           const uint32_t *gids, const uint2 *ranges, float *out, Stats *stats,
+                           cudaStream_t s);
+cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
+                           const uint32_t *gids, const uint2 *ranges, const float *dLdI,
+                           float4 *grad, cudaStream_t s);
+cudaError_t launch_param_chain(const float *mu, const float *ls, const float *q, const float *rho,
+                               int64_t n, const float4 *grad, float *g_mu, float *g_ls,
+                               float *g_q, float *g_rho, cudaStream_t s);
+cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, float kappa,
+                        float eps, float *dLdI, double *partial, int nblk, float *loss_out,
+                        cudaStream_t s);
+int loss_blocks(int64_t n);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr,
+                        float beta1, float beta2, float eps, float bc1, float bc2, cudaStream_t s);
+
+}  // namespace rgrt

@@ -1,0 +1,306 @@
+"""GPU parity of the CUDA projector against the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the method's targets): projections within 1e-5
+relative L2 of the oracle, gradients within 1e-4 relative L2, culling
+records and tile lists bit-exact.  For projections the reference is the
+oracle's admissible interval [I_lo, I_hi] (pairs whose m is within 1e-4*9 of
+the 3-sigma cut may go either way in FP32), i.e. the error is the distance
+of the GPU result from that interval.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_01057_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def rg(torch):
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    return rgrt
+
+
+@pytest.fixture(scope="module")
+def ctx(rg):
+    c = rg.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(torch, G):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in G.items()}
+
+
+def fwd_err(I_gpu, ref):
+    I = np.asarray(I_gpu, np.float64)
+    clip = np.clip(I, ref["I_lo"], ref["I_hi"])
+    den = np.linalg.norm(clip)
+    return np.linalg.norm(I - clip) / (den if den > 0 else 1.0)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def gpu_forward(torch, rg, ctx, G, gd):
+    geom = rg.Geometry(ctx, gd)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    out = torch.empty(geom.n_rays, device="cuda", dtype=torch.float32)
+    rg.project_forward(ctx, gs, geom, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), gs, geom
+
+
+def gpu_backward(torch, rg, ctx, gs, geom, w):
+    n = gs.n
+    wd = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    outs = [torch.empty(s, device="cuda") for s in ((n, 3), (n, 3), (n, 4), (n,))]
+    rg.project_backward(ctx, gs, geom, wd, *outs)
+    torch.cuda.synchronize()
+    return dict(zip(("mu", "ls", "q", "rho"), (o.cpu().numpy() for o in outs)))
+
+
+# ------------------------------------------------------------------ cases
+
+def case(name):
+    if name == "c1":
+        return synth.workload_c1(0)
+    if name == "parallel_ragged":
+        return (synth.gaussians_uniform(400, 11, log_sigma=math.log(0.08)),
+                synth.geom_parallel(5, 37, 53, 0.04, 0.04, -2.0, 2.0))
+    if name == "parallel_infinite":
+        return (synth.gaussians_uniform(300, 12, half_box=0.7, log_sigma=math.log(0.08)),
+                synth.geom_parallel(4, 40, 48, 0.04, 0.04, -math.inf, math.inf))
+    if name == "parallel_short_segment":
+        # segment [-0.3, 0.4] cuts through the Gaussians: erf terms matter
+        return (synth.gaussians_uniform(300, 13, half_box=0.7, log_sigma=math.log(0.1)),
+                synth.geom_parallel(4, 40, 48, 0.04, 0.04, -0.3, 0.4))
+    if name == "cone_small":
+        G, _ = synth.workload_c2(0, n=3000, n_views=12, side=64)
+        return G, synth.geom_c2(n_views=12, side=64)
+    if name == "cone_near_source":
+        # detector close behind the volume: segments end inside Gaussians
+        return (synth.gaussians_uniform(400, 14, log_sigma=math.log(0.08)),
+                synth.geom_cone(6, 48, 40, 0.06, 0.06, 1.6, 2.4))
+    if name == "pet_arc":
+        G, _ = synth.workload_c3(0, n=4000, n_angles=24, n_radial=329, n_planes=63)
+        return G, synth.geom_c3(24, 329, 63, arc_mode=0)
+    if name == "pet_raw":
+        G, _ = synth.workload_c3(1, n=4000, n_angles=24, n_radial=329, n_planes=63)
+        return G, synth.geom_c3(24, 329, 63, arc_mode=1)
+    if name == "tile8x4":
+        G, gd = synth.workload_c1(1)
+        gd = dict(gd, tile_w=8, tile_h=4)
+        return G, gd
+    if name == "tile32x8":
+        G, gd = synth.workload_c1(2)
+        gd = dict(gd, tile_w=32, tile_h=8)
+        return G, gd
+    raise KeyError(name)
+
+
+FWD_CASES = ["c1", "parallel_ragged", "parallel_infinite", "parallel_short_segment", "cone_small",
+             "cone_near_source", "pet_arc", "pet_raw", "tile8x4", "tile32x8"]
+
+
+def test_records_bit_exact(rg, ctx, torch, oracle):
+    G = synth.gaussians_uniform(5000, 3, log_sigma=math.log(0.05), log_sigma_std=1.0)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    got = rg.debug_records(ctx, gs)
+    ref = oracle.records_fp32(G["ls"], G["q"])
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("name", ["c1", "parallel_ragged", "cone_small", "cone_near_source",
+                                  "pet_arc", "pet_raw", "tile8x4"])
+def test_tile_lists_bit_exact(rg, ctx, torch, oracle, name):
+    G, gd = case(name)
+    geom = rg.Geometry(ctx, gd)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    start, gid = rg.debug_tile_lists(ctx, gs, geom)
+    rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"])
+    assert gid.size == rgid.size and gid.size > 0
+    assert np.array_equal(start, rstart)
+    assert np.array_equal(gid, rgid)
+
+
+@pytest.mark.parametrize("name", FWD_CASES)
+def test_forward_parity(rg, ctx, torch, oracle, name):
+    G, gd = case(name)
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    ref = oracle.forward(gd, G)
+    assert ref["pairs"] > 1000
+    err = fwd_err(I, ref)
+    assert err < FWD_TOL, f"{name}: forward rel-L2 {err:.3e}"
+    st = ctx.stats()
+    assert st["pairs_kept"] >= 0.999 * ref["pairs"] - 10
+
+
+@pytest.mark.parametrize("name", ["c1", "parallel_ragged", "parallel_short_segment", "cone_small",
+                                  "cone_near_source", "pet_arc", "tile8x4"])
+def test_backward_parity(rg, ctx, torch, oracle, name):
+    G, gd = case(name)
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    w = synth.random_weights(geom.n_rays, 5)
+    got = gpu_backward(torch, rg, ctx, gs, geom, w)
+    ref = oracle.backward(gd, G, w)
+    for k in ("mu", "ls", "q", "rho"):
+        e = rel_l2(got[k], ref[k])
+        assert e < GRAD_TOL, f"{name}: grad {k} rel-L2 {e:.3e}"
+
+
+def test_host_pointers_match_device(rg, ctx, torch):
+    G, gd = case("parallel_ragged")
+    I_dev, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    gh = rg.Gaussians(ctx, G["mu"], G["ls"], G["q"], G["rho"])    # host arrays, copied
+    I_host = np.zeros(geom.n_rays, np.float32)
+    rg.project_forward(ctx, gh, geom, I_host)
+    assert np.array_equal(I_host, I_dev)
+    w = synth.random_weights(geom.n_rays, 9)
+    gd_dev = gpu_backward(torch, rg, ctx, gs, geom, w)
+    outs = [np.zeros(s, np.float32) for s in ((gh.n, 3), (gh.n, 3), (gh.n, 4), (gh.n,))]
+    rg.project_backward(ctx, gh, geom, w.astype(np.float32), *outs)
+    for k, o in zip(("mu", "ls", "q", "rho"), outs):
+        assert rel_l2(o, gd_dev[k]) < 1e-6
+
+
+def test_autograd_function_matches_c_abi(rg, ctx, torch):
+    G, gd = case("cone_small")
+    geom = rg.Geometry(ctx, gd)
+    t = _dev(torch, G)
+    leaves = [t[k].clone().requires_grad_() for k in ("mu", "ls", "q", "rho")]
+    I = rg.gaussian_project(*leaves, geom)
+    w = torch.from_numpy(synth.random_weights(geom.n_rays, 2)).cuda()
+    (I * w).sum().backward()
+    gs = rg.Gaussians(ctx, t["mu"], t["ls"], t["q"], t["rho"])
+    ref = gpu_backward(torch, rg, ctx, gs, geom, w.cpu().numpy())
+    for leaf, k in zip(leaves, ("mu", "ls", "q", "rho")):
+        assert rel_l2(leaf.grad.cpu().numpy(), ref[k]) < 1e-5
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_no_gaussians(rg, ctx, torch):
+    gd = synth.geom_c1()
+    geom = rg.Geometry(ctx, gd)
+    z = np.zeros((0, 3), np.float32)
+    gs = rg.Gaussians(ctx, z, z, np.zeros((0, 4), np.float32), np.zeros(0, np.float32))
+    out = torch.full((geom.n_rays,), 7.0, device="cuda")
+    rg.project_forward(ctx, gs, geom, out)
+    assert float(out.abs().max()) == 0.0
+
+
+def test_gaussians_outside_detector(rg, ctx, torch, oracle):
+    G = synth.gaussians_uniform(200, 21, half_box=0.5, log_sigma=math.log(0.05))
+    G["mu"][:, 2] += 5.0     # far above the detector rows
+    gd = synth.geom_c1()
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    assert float(np.abs(I).max()) == 0.0
+    w = synth.random_weights(geom.n_rays, 1)
+    g = gpu_backward(torch, rg, ctx, gs, geom, w)
+    assert all(float(np.abs(v).max()) == 0.0 for v in g.values())
+
+
+def test_huge_gaussian_covers_detector(rg, ctx, torch, oracle):
+    G = synth.gaussians_uniform(3, 22, half_box=0.2, log_sigma=math.log(0.9), log_sigma_std=0.05)
+    gd = synth.geom_parallel(3, 40, 40, 0.05, 0.05, -6.0, 6.0)
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    ref = oracle.forward(gd, G)
+    assert fwd_err(I, ref) < FWD_TOL
+
+
+def test_degenerate_quaternion_and_flat_gaussian(rg, ctx, torch, oracle):
+    G = synth.gaussians_uniform(50, 23, half_box=0.6, log_sigma=math.log(0.08))
+    G["q"][:5] = 0.0                     # zero quaternion: identity rotation
+    G["ls"][5:10, 2] = math.log(0.004)   # nearly flat pancakes
+    gd = synth.geom_parallel(6, 48, 48, 0.04, 0.04, -2.0, 2.0)
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    ref = oracle.forward(gd, G)
+    assert fwd_err(I, ref) < FWD_TOL
+
+
+def test_invalid_geometry_rejected(rg, ctx):
+    bad = synth.geom_cone(4, 16, 16, 0.1, 0.1, 5.0, 4.0)   # detector before the origin
+    with pytest.raises(rg.RgrtError):
+        rg.Geometry(ctx, bad)
+    bad = dict(synth.geom_c1(), tile_w=12)
+    with pytest.raises(rg.RgrtError):
+        rg.Geometry(ctx, bad)
+    bad = synth.geom_pet(8, 400, 5, 100.0, 64, 2.0)       # bins beyond the ring
+    with pytest.raises(rg.RgrtError):
+        rg.Geometry(ctx, bad)
+
+
+# ------------------------------------------------------------------ full sizes, sampled
+
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_full_size_sampled_parity(rg, ctx, torch, oracle, cfg):
+    """At the benchmark sizes: sampled rays against the oracle's brute force,
+    sampled Gaussians' gradients against the oracle's adjoint."""
+    G, gd = synth.workload_c2(0) if cfg == "c2" else synth.workload_c3(0)
+    I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)
+    rng = np.random.default_rng(0)
+    nz = np.nonzero(I)[0]
+    idx = np.concatenate([rng.choice(nz, 300, replace=False), rng.choice(I.size, 100, replace=False)])
+    ref = oracle.forward_rays(gd, G, idx)
+    err = fwd_err(I[idx], ref)
+    assert err < FWD_TOL, f"{cfg}: sampled forward rel-L2 {err:.3e}"
+    w = synth.random_weights(geom.n_rays, 4)
+    got = gpu_backward(torch, rg, ctx, gs, geom, w)
+    sel = rng.choice(G["mu"].shape[0], 24, replace=False)
+    gref = oracle.backward(gd, G, w, sel=sel)
+    for k in ("mu", "ls", "q", "rho"):
+        e = rel_l2(got[k][sel], gref[k][sel])
+        assert e < GRAD_TOL, f"{cfg}: sampled grad {k} rel-L2 {e:.3e}"
+
+
+# ------------------------------------------------------------------ loss_step
+
+@pytest.mark.parametrize("loss", ["l2", "poisson"])
+def test_loss_step_matches_oracle(rg, ctx, torch, oracle, loss):
+    G, gd = case("cone_small")
+    ref_fwd = oracle.forward(gd, G)
+    rng = np.random.default_rng(3)
+    if loss == "l2":
+        y = (ref_fwd["I"] * rng.uniform(0.8, 1.2, ref_fwd["I"].size)).astype(np.float32)
+        kappa, eps = 1.0, 0.0
+        L_ref, dLdI = oracle.loss_l2(ref_fwd["I"], y)
+        kind = rg.RGRT_LOSS_L2
+    else:
+        kappa = 50.0
+        eps = 1e-3
+        y = rng.poisson(kappa * ref_fwd["I"] + eps).astype(np.float32)
+        L_ref, dLdI = oracle.loss_poisson(ref_fwd["I"], y, kappa, eps)
+        kind = rg.RGRT_LOSS_POISSON
+    hp = rg.adam_params(kappa=kappa, poisson_eps=eps)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    geom = rg.Geometry(ctx, gd)
+    loss_out = np.zeros(1, np.float32)
+    rg.loss_step(ctx, gs, geom, y, kind, hp, 1, loss_out)
+    assert float(loss_out[0]) == pytest.approx(L_ref, rel=1e-5)
+    g = oracle.backward(gd, G, dLdI)
+    new = gs.numpy()
+    lrs = dict(mu=hp.lr_mu, ls=hp.lr_logscale, q=hp.lr_quat, rho=hp.lr_rho)
+    for k in ("mu", "ls", "q", "rho"):
+        p_ref, _, _ = oracle.adam(G[k].astype(np.float64), g[k], 0.0, 0.0, 1, lrs[k])
+        strong = np.abs(g[k]) > 1e-2 * np.abs(g[k]).max()   # well-determined update signs
+        d_got = (new[k].astype(np.float64) - G[k])[strong]
+        d_ref = (p_ref - G[k])[strong]
+        assert rel_l2(d_got, d_ref) < 1e-3, k
