@@ -1,0 +1,390 @@
+"""Benchmark: rays/s of one full optimisation step (forward projection, L2
+loss, adjoint, parameter chain, Adam) of the analytic Gaussian ray-tracing
+projector on the cone-beam CT workload (50,000 Gaussians fitted to a
+12-ellipsoid phantom, 180 views x 256 x 256 detector).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Under torchrun each rank runs its own independent
+scan (weak scaling, no collective on the data path); the reported time is the
+maximum over ranks.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload (its rays/s extrapolates linearly in the
+number of rays).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2602_01057_gb300 import synth  # noqa: E402
+
+METRIC = "rays/s fwd+bwd"
+UNIT = "rays/s"
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# algorithmic FP32 work per kept pair (m <= 9), FMA counted as 2 FLOP: the
+# per-pair arithmetic of the recentred closed form (Eqs. 7-11), forward and
+# adjoint; see the kernel notes for the count.
+FLOP_PER_PAIR_FWD = 78
+FLOP_PER_PAIR_ADJ = 180
+WORKLOADS = {
+    "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
+          "180 views over 360 deg, 256x256 detector, source-origin 1000 mm, source-detector 1500 mm",
+    "c3": "PET fwd+bwd (Poisson NLL + Adam): 200,000 Gaussians, ring radius 400 mm, 576 crystals, "
+          "arc-corrected 288 angles x 329 radial x 63 planes",
+    "c1": "parallel-beam CT fwd+bwd (L2 + Adam): 1,000 Gaussians, 16 views x 64x64",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
+    ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU sample (0 = auto)")
+    return ap.parse_args()
+
+
+def _params(G):
+    return {k: G[k] for k in ("mu", "ls", "q", "rho")}
+
+
+def workload(name, seed):
+    G, true, gd, loss = _workload(name, seed)
+    return _params(G), _params(true), gd, loss
+
+
+def _workload(name, seed):
+    if name == "c2":
+        G, gd = synth.workload_c2(seed)
+        true = synth.perturbed(G, seed + 101, pos_std=0.01)
+        return G, true, gd, "l2"
+    if name == "c3":
+        G, gd = synth.workload_c3(seed)
+        true = synth.perturbed(G, seed + 101, pos_std=1.0)
+        return G, true, gd, "poisson"
+    G, gd = synth.workload_c1(seed)
+    true = synth.perturbed(G, seed + 101, pos_std=0.01)
+    return G, true, gd, "l2"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(G, gd, loss, n_views):
+    """Oracle fwd + loss + bwd on the first n_views views: (seconds, rays)."""
+    from oracle import oracle
+    sub = dict(gd)
+    sub["n_views"] = n_views
+    if gd["kind"] != "pet":
+        sub["angles"] = gd["angles"][:n_views]
+    rays = synth.num_rays(sub)
+    y = np.zeros(rays)
+    t0 = time.perf_counter()
+    f = oracle.forward(sub, G)
+    if loss == "l2":
+        _, w = oracle.loss_l2(f["I"], y)
+    else:
+        _, w = oracle.loss_poisson(f["I"], y + 1.0, 1.0, 1e-9)
+    oracle.backward(sub, G, w)
+    return time.perf_counter() - t0, rays
+
+
+def cpu_baseline(G, gd, loss, n_views):
+    from oracle import oracle
+    sec, rays = oracle_sample(G, gd, loss, n_views)
+    return dict(value=rays / sec, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+                sample=f"FP64 oracle fwd+loss+bwd on {n_views} of {gd['n_views']} views "
+                       f"({rays} rays, all Gaussians); {sec:.1f} s")
+
+
+def auto_views(name):
+    return {"c2": 4, "c3": 4, "c1": 16}[name]
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    G, _, gd, loss = workload(args.workload, 0)
+    nv = args.cpu_views or auto_views(args.workload)
+    if args.warmup > 0:
+        oracle_sample(G, gd, loss, 1)
+    times, rays = [], 0
+    for _ in range(args.steps):
+        s, rays = oracle_sample(G, gd, loss, nv)
+        times.append(s)
+    from oracle import oracle
+    tot = sum(times)
+    value = rays * args.steps / tot
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config=dict(workload=WORKLOADS[args.workload],
+                            sample=f"{nv} of {gd['n_views']} views per step"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+                                  sample=f"FP64 oracle fwd+loss+bwd, {nv} of {gd['n_views']} "
+                                         f"views ({rays} rays) per step"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm),
+                    reasons=sorted(reasons))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    dev = torch.device("cuda", local)
+    G, Gt, gd, loss = workload(args.workload, rank)
+    R = synth.num_rays(gd)
+    ctx = rgrt.Context(local)
+    geom = rgrt.Geometry(ctx, gd)
+    # measured data: projections of the perturbed ("true") Gaussians
+    tt = {k: torch.from_numpy(v).to(dev) for k, v in Gt.items()}
+    gtrue = rgrt.Gaussians(ctx, tt["mu"], tt["ls"], tt["q"], tt["rho"])
+    ytrue = torch.empty(R, device=dev)
+    rgrt.project_forward(ctx, gtrue, geom, ytrue)
+    gtrue.close()
+    if loss == "poisson":
+        kappa = 1e8 / float(ytrue.sum())
+        gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+        y = torch.poisson(kappa * ytrue, generator=gen)
+        eps = 1e-9 * float((kappa * ytrue).max())
+        hp = rgrt.adam_params(kappa=kappa, poisson_eps=eps)
+        lkind = rgrt.RGRT_LOSS_POISSON
+    else:
+        y = ytrue
+        hp = rgrt.adam_params()
+        lkind = rgrt.RGRT_LOSS_L2
+    t0 = {k: torch.from_numpy(v).to(dev) for k, v in G.items()}
+    gs = rgrt.Gaussians(ctx, t0["mu"], t0["ls"], t0["q"], t0["rho"])
+    loss_dev = torch.zeros(1, device=dev)
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    step = 0
+    for _ in range(args.warmup):
+        step += 1
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, loss_dev)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    # timed region
+    ctx.prof_enable(True)
+    ctx.prof_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = rgrt.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(k & 0xff)      # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step += 1
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, loss_dev)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    launches = rgrt.launch_count() - launches0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max = max_over_ranks(ms, world)
+    st = ctx.stats()
+    kernels = {}
+    for name in ("k_records", "k_cull", "scan", "k_emit", "radix_sort", "k_ranges", "k_forward",
+                 "k_loss", "k_adjoint", "k_param_chain", "k_adam"):
+        n, t = ctx.prof_get(name)
+        kernels[name] = dict(launches=n, ms=t)
+    ctx.prof_enable(False)
+    value = R * args.steps * world / (ms_max / 1e3)
+    pairs = st["pairs_kept"]
+    # roofline of the dominant kernel (FP32 ALU bound)
+    dom = max(("k_forward", "k_adjoint"), key=lambda k: kernels[k]["ms"])
+    per = kernels[dom]["ms"] / max(kernels[dom]["launches"], 1)
+    flop = pairs * (FLOP_PER_PAIR_ADJ if dom == "k_adjoint" else FLOP_PER_PAIR_FWD)
+    achieved = flop / (per / 1e3) / 1e12
+    peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                traffic=None, kernel=dom, kernel_ms=per,
+                note="FP32 FLOP of the kept pairs (m <= 9) / kernel time; peak = 152 SMs x 128 "
+                     "FP32 lanes x 2 (FMA) x 2070 MHz")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOADS[args.workload], rays_per_step=R,
+                            gaussians=int(G["mu"].shape[0]),
+                            l2=("flushed between timed steps (256 MiB write outside the events)"
+                                if flush is not None else "not flushed"),
+                            parallelism=f"{world} independent scans (one per GPU)"),
+                pairs_per_s=pairs * world / (ms_max / 1e3 / args.steps),
+                pairs_kept_per_step=pairs, pairs_evaluated_per_step=st["pairs_evaluated"],
+                keys_per_step=st["keys"], kernels=kernels, roofline=roof,
+                gpu_launches=launches, wall_s=wall)
+    if clk:
+        line["clocks"] = clk
+    # end to end: host parameters in, step, host loss + parameters out
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        nv = args.cpu_views or auto_views(args.workload)
+        line["cpu_baseline"] = cpu_baseline(G, gd, loss, nv)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    del st0
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world):
+    """Same step through the C ABI with host buffers: parameters and
+    measurements copied in from pinned host memory, loss and updated
+    parameters read back, every step."""
+    import torch
+    n = G["mu"].shape[0]
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in G.items()}
+    yh = y.cpu().pin_memory()
+    out = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+    lh = torch.zeros(1).pin_memory()
+    gs = rgrt.Gaussians(ctx, host["mu"], host["ls"], host["q"], host["rho"])
+    steps = max(3, args.steps // 2)
+    step = 0
+    for _ in range(2):
+        step += 1
+        gs.set(host["mu"], host["ls"], host["q"], host["rho"])
+        rgrt.loss_step(ctx, gs, geom, yh, lkind, hp, step, lh)
+        gs.get(out["mu"], out["ls"], out["q"], out["rho"])
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step += 1
+        gs.set(host["mu"], host["ls"], host["q"], host["rho"])
+        rgrt.loss_step(ctx, gs, geom, yh, lkind, hp, step, lh)
+        gs.get(out["mu"], out["ls"], out["q"], out["rho"])
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    gs.close()
+    h2d = 4 * 11 * n + 4 * R
+    d2h = 4 + 4 * 11 * n
+    return dict(value=R * steps * world / dt, unit=UNIT, h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=d2h, steps=steps)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -181,6 +181,9 @@ int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *
 /* Message of the last failed call on this thread ("" if none). */
 const char *rgrt_last_error(void);
 
+/* Number of CUDA kernels the library has launched in this process. */
+int64_t rgrt_launch_count(void);
+
 /* The FP32 covariance records the cull uses: Sigma packed
  * (00,01,02,11,12,22), n x 6 floats (host or device). */
 int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *stream);

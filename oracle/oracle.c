@@ -553,10 +553,16 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
  * adjoint: dL/d(mu, l, q, rho) = sum over pairs with m <= cut2 of
  * dLdI[ray] * d(contribution)/d(parameter).  sel (length nsel) restricts the
  * Gaussians evaluated (others are left untouched); sel == NULL means all.
+ * Pairs with |m - cut2| <= band may be kept or dropped by an FP32
+ * evaluation; when lohi != NULL it receives, per Gaussian, the bounds
+ * lo[11] = main + sum of the negative parts of the band pairs' gradients and
+ * hi[11] = main + sum of their positive parts (order mu[3], l[3], q[4], rho),
+ * which bracket every admissible choice.
  */
 void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, const float *q,
-                 const float *rho, double cut2, const double *dLdI, int64_t nsel, const int64_t *sel,
-                 int brute, int nthreads, double *g_mu, double *g_ls, double *g_q, double *g_rho)
+                 const float *rho, double cut2, double band, const double *dLdI, int64_t nsel,
+                 const int64_t *sel, int brute, int nthreads, double *g_mu, double *g_ls,
+                 double *g_q, double *g_rho, double *lohi)
 {
     og_set_threads(nthreads);
     double *ut, *vt;
@@ -569,25 +575,49 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
         og_cov(ls + 3 * k, q + 4 * k, Sig, P);
         double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
         double gm[3] = { 0, 0, 0 }, gP[3][3] = { { 0 } }, grho = 0.0, gl[3], gq[4];
+        double bnom[11] = { 0 }, bneg[11] = { 0 }, bpos[11] = { 0 };
         for (int v = 0; v < g->n_views; v++) {
             int i0 = 0, i1 = g->n_cols - 1, j0 = 0, j1 = g->n_rows - 1;
-            if (!brute) og_bbox(g, v, m3, Sig, og_box_k2(cut2, 0.0), ut, vt, &i0, &i1, &j0, &j1);
+            if (!brute) og_bbox(g, v, m3, Sig, og_box_k2(cut2, band), ut, vt, &i0, &i1, &j0, &j1);
             for (int j = j0; j <= j1; j++)
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
                     og_ray(g, v, j, i, o, d, &ta, &tb);
                     og_pairval r;
                     og_eval(o, d, ta, tb, m3, P, rho[k], &r);
-                    if (!(r.m <= cut2)) continue;
+                    if (!(r.m <= cut2 + band)) continue;
                     double w = dLdI[og_index(g, v, j, i)];
                     if (w == 0.0) continue;
-                    og_pair_grad(o, d, ta, tb, m3, P, rho[k], w, &r, gm, gP, &grho);
+                    if (r.m <= cut2 - band) {
+                        og_pair_grad(o, d, ta, tb, m3, P, rho[k], w, &r, gm, gP, &grho);
+                        continue;
+                    }
+                    /* ambiguous pair: its own full parameter gradient */
+                    double bm[3] = { 0, 0, 0 }, bP[3][3] = { { 0 } }, br = 0.0, bl[3], bq[4], b[11];
+                    og_pair_grad(o, d, ta, tb, m3, P, rho[k], w, &r, bm, bP, &br);
+                    og_chain(ls + 3 * k, q + 4 * k, bP, bl, bq);
+                    for (int c = 0; c < 3; c++) { b[c] = bm[c]; b[3 + c] = bl[c]; }
+                    for (int c = 0; c < 4; c++) b[6 + c] = bq[c];
+                    b[10] = br;
+                    for (int c = 0; c < 11; c++) {
+                        if (r.m <= cut2) bnom[c] += b[c];
+                        if (b[c] < 0) bneg[c] += b[c]; else bpos[c] += b[c];
+                    }
                 }
         }
         og_chain(ls + 3 * k, q + 4 * k, gP, gl, gq);
-        for (int c = 0; c < 3; c++) { g_mu[3 * k + c] = gm[c]; g_ls[3 * k + c] = gl[c]; }
-        for (int c = 0; c < 4; c++) g_q[4 * k + c] = gq[c];
-        g_rho[k] = grho;
+        double mainv[11];
+        for (int c = 0; c < 3; c++) { mainv[c] = gm[c]; mainv[3 + c] = gl[c]; }
+        for (int c = 0; c < 4; c++) mainv[6 + c] = gq[c];
+        mainv[10] = grho;
+        for (int c = 0; c < 3; c++) { g_mu[3 * k + c] = mainv[c] + bnom[c]; g_ls[3 * k + c] = mainv[3 + c] + bnom[3 + c]; }
+        for (int c = 0; c < 4; c++) g_q[4 * k + c] = mainv[6 + c] + bnom[6 + c];
+        g_rho[k] = mainv[10] + bnom[10];
+        if (lohi)
+            for (int c = 0; c < 11; c++) {
+                lohi[22 * k + c] = mainv[c] + bneg[c];
+                lohi[22 * k + 11 + c] = mainv[c] + bpos[c];
+            }
     }
     free(ut); free(vt);
 }

@@ -191,25 +191,31 @@ def forward_rays(geom, G, idx, cut2=CUT2, band=BAND, nthreads=0):
     return dict(I=I, I_lo=Ilo, I_hi=Ihi)
 
 
-def backward(geom, G, dLdI, sel=None, cut2=CUT2, brute=False, nthreads=0):
-    """FP64 adjoint: dict(mu, ls, q, rho) of dL/dparameter.  ``sel`` restricts
-    the Gaussians evaluated (rows of the others are NaN)."""
+def backward(geom, G, dLdI, sel=None, cut2=CUT2, band=BAND, brute=False, nthreads=0):
+    """FP64 adjoint: dict(mu, ls, q, rho) of dL/dparameter (pairs with m <= cut2),
+    plus 'lo' and 'hi' dicts bracketing every admissible choice for pairs
+    within ``band`` of the cut.  ``sel`` restricts the Gaussians evaluated
+    (rows of the others are NaN)."""
     g = _geom(geom)
     n, mu, ls, q, rho = _gauss(G)
     w = _f64(dLdI).reshape(-1)
     assert w.size == g.n_rays
     gm = np.full((n, 3), np.nan); gl = np.full((n, 3), np.nan)
     gq = np.full((n, 4), np.nan); gr = np.full(n, np.nan)
+    lohi = np.full((n, 22), np.nan)
     if sel is None:
         nsel, selp = n, None
     else:
         sel_a = np.ascontiguousarray(sel, dtype=np.int64)
         nsel, selp = sel_a.size, _p(sel_a)
     lib().or_backward(g.ref, ctypes.c_int64(n), _p(mu), _p(ls), _p(q), _p(rho),
-                      ctypes.c_double(cut2), _p(w), ctypes.c_int64(nsel), selp,
-                      ctypes.c_int(int(brute)), ctypes.c_int(nthreads),
-                      _p(gm), _p(gl), _p(gq), _p(gr))
-    return dict(mu=gm, ls=gl, q=gq, rho=gr)
+                      ctypes.c_double(cut2), ctypes.c_double(band), _p(w), ctypes.c_int64(nsel),
+                      selp, ctypes.c_int(int(brute)), ctypes.c_int(nthreads),
+                      _p(gm), _p(gl), _p(gq), _p(gr), _p(lohi))
+
+    def split(a):
+        return dict(mu=a[:, 0:3], ls=a[:, 3:6], q=a[:, 6:10], rho=a[:, 10])
+    return dict(mu=gm, ls=gl, q=gq, rho=gr, lo=split(lohi[:, :11]), hi=split(lohi[:, 11:]))
 
 
 # ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <new>
 #include <string>
@@ -16,6 +17,12 @@
 #include "rgrt_internal.h"
 
 using namespace rgrt;
+
+namespace {
+std::atomic<long long> g_launches{ 0 };
+}
+
+void rgrt::count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
@@ -467,6 +474,8 @@ int validate_desc(const rgrt_geom_desc *d)
 extern "C" {
 
 const char *rgrt_last_error(void) { return g_err.c_str(); }
+
+int64_t rgrt_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int rgrt_ctx_create(rgrt_ctx **out, int device, size_t budget)
 {

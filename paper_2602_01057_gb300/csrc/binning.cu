@@ -242,6 +242,7 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
     k_scan_reduce<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, n, tmp);
     k_scan_top<<<1, 1024, 0, s>>>(tmp, nb, total);
     k_scan_down<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, out, n, tmp);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -252,6 +253,7 @@ cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt
     int64_t tot = (int64_t)nv * n;
     if (tot <= 0) return cudaSuccess;
     k_emit<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -281,6 +283,7 @@ cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint
         cudaError_t e = launch_scan(hist, offs, (int64_t)hn, stot, stmp, s);
         if (e != cudaSuccess) return e;
         k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, offs, nb);
+        count_launches(2);
         uint32_t *tk = src_k, *tv = src_v;
         src_k = dst_k; src_v = dst_v; dst_k = tk; dst_v = tv;
     }
@@ -296,6 +299,7 @@ cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, 
 {
     if (n_keys == 0) return cudaSuccess;
     k_ranges<<<(n_keys + 255) / 256, 256, 0, s>>>(keys, n_keys, ranges, n_tiles);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,7 @@ cudaError_t launch_param_chain(const float *mu, const float *ls, const float *q,
     if (n <= 0) return cudaSuccess;
     k_param_chain<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mu, ls, q, rho, n, grad, g_mu, g_ls,
                                                                g_q, g_rho);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -159,6 +160,7 @@ cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, flo
 {
     k_loss<<<nblk, LOSS_BS, 0, s>>>(kind, I, y, n, kappa, eps, dLdI, partial);
     k_loss_final<<<1, 32, 0, s>>>(partial, nblk, loss_out);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -167,6 +169,7 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
 {
     if (n <= 0) return cudaSuccess;
     k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, lr, beta1, beta2, eps, bc1, bc2);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -198,13 +198,22 @@ __device__ __forceinline__ int tr_reduce(float *v, int lane)
     tr_stage<N3, 4>(v, lane);
     tr_stage<N4, 2>(v, lane);
     tr_stage<N5, 1>(v, lane);
-    int idx = 0;
-    if (N1 > 1 && (lane & 16)) idx += H1;
-    if (N2 > 1 && (lane & 8)) idx += H2;
-    if (N3 > 1 && (lane & 4)) idx += H3;
-    if (N4 > 1 && (lane & 2)) idx += H4;
-    // lanes whose path ran through padding hold zeros; odd lanes duplicate
-    return (lane & 1) ? N : idx;
+    // walk the splits backwards: the lane's element sits at position p of
+    // each stage's array; it is a padding zero if p ever falls outside it
+    int p = 0;
+    bool ok = true;
+    if (N4 > 1 && (lane & 2)) { p += H4; ok &= p < N4; }
+    if (N3 > 1 && (lane & 4)) { p += H3; ok &= p < N3; }
+    if (N2 > 1 && (lane & 8)) { p += H2; ok &= p < N2; }
+    if (N1 > 1 && (lane & 16)) { p += H1; ok &= p < N1; }
+    // a plain butterfly stage (one value left) leaves both partners with the
+    // same sum: only the partner with a clear bit owns it
+    if (N1 == 1) ok &= !(lane & 16);
+    if (N2 == 1) ok &= !(lane & 8);
+    if (N3 == 1) ok &= !(lane & 4);
+    if (N4 == 1) ok &= !(lane & 2);
+    ok &= !(lane & 1);
+    return ok ? p : N;
 }
 
 struct TileCtx {
@@ -430,6 +439,7 @@ cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const fl
         k_forward<true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
     else
         k_forward<false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -444,6 +454,7 @@ cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const fl
         k_adjoint<true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
     else
         k_adjoint<false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
+    count_launches(1);
     return cudaGetLastError();
 }
 

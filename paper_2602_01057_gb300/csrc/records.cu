@@ -196,6 +196,7 @@ cudaError_t launch_records(const float *mu, const float *ls, const float *q, con
     if (n <= 0) return cudaSuccess;
     int bs = 256;
     k_records<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(mu, ls, q, rho, n, rec, crec);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -206,6 +207,7 @@ cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n,
     if (tot <= 0) return cudaSuccess;
     int bs = 256;
     k_cull<<<(unsigned)((tot + bs - 1) / bs), bs, 0, s>>>(g, nv, crec, n, cnt, rect);
+    count_launches(1);
     return cudaGetLastError();
 }
 

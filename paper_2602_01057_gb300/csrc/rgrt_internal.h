@@ -42,6 +42,9 @@ struct Stats {
     unsigned long long pairs_eval, pairs_kept;
 };
 
+// number of kernels the library has launched (all contexts, all threads)
+void count_launches(int k);
+
 // ---- launchers (each returns cudaGetLastError of its launch) -------------
 cudaError_t launch_records(const float *mu, const float *ls, const float *q, const float *rho,
                            int64_t n, float4 *rec, float4 *crec, cudaStream_t s);

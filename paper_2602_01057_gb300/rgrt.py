@@ -66,6 +66,7 @@ _EXPORTS = {
     "loss_step": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
                   ctypes.c_int),
     "rgrt_last_error": ([], ctypes.c_char_p),
+    "rgrt_launch_count": ([], ctypes.c_int64),
     "rgrt_debug_records": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "rgrt_debug_tile_lists": ([_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int64), _VP, _VP, ctypes.c_int64, _VP],
@@ -107,6 +108,11 @@ def _check(rc):
     if rc != RGRT_OK:
         raise RgrtError(rc, lib().rgrt_last_error().decode())
     return rc
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().rgrt_launch_count())
 
 
 def last_error() -> str:

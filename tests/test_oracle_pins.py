@@ -310,8 +310,11 @@ def test_fast_equals_brute(oracle, kind):
     w = synth.random_weights(a["I"].size, 5)
     ga = oracle.backward(g, G, w)
     gb = oracle.backward(g, G, w, brute=True)
-    for key in ga:
+    for key in ("mu", "ls", "q", "rho"):
         np.testing.assert_array_equal(ga[key], gb[key])
+        np.testing.assert_array_equal(ga["lo"][key], gb["lo"][key])
+        np.testing.assert_array_equal(ga["hi"][key], gb["hi"][key])
+        assert np.all(ga["lo"][key] <= ga[key]) and np.all(ga[key] <= ga["hi"][key])
 
 
 def test_sampled_rays_equal_full(oracle):
