@@ -92,14 +92,21 @@ def dist_env():
     return world, rank, local
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """Maximum of a per-rank scalar over all ranks (identity for one rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_value(rays_per_step, steps, world, ms_max):
+    """Whole-job rays/s: every rank projects its own scan of rays_per_step rays
+    per step; the job takes as long as the slowest rank."""
+    return rays_per_step * steps * world / (ms_max / 1e3)
 
 
 def barrier(world):
@@ -266,11 +273,13 @@ def run_ours(args):
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     step = 0
-    for _ in range(args.warmup):
+    for wi in range(args.warmup):
         step += 1
+        ctx.stats_enable(wi == args.warmup - 1)    # pair counts from the last warm-up step
         rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, loss_dev)
     torch.cuda.synchronize()
-    st0 = ctx.stats()
+    st = ctx.stats()
+    ctx.stats_enable(False)
     # timed region
     ctx.prof_enable(True)
     ctx.prof_reset()
@@ -296,14 +305,13 @@ def run_ours(args):
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_max = max_over_ranks(ms, world)
-    st = ctx.stats()
     kernels = {}
     for name in ("k_records", "k_cull", "scan", "k_emit", "radix_sort", "k_ranges", "k_forward",
                  "k_loss", "k_adjoint", "k_param_chain", "k_adam"):
         n, t = ctx.prof_get(name)
         kernels[name] = dict(launches=n, ms=t)
     ctx.prof_enable(False)
-    value = R * args.steps * world / (ms_max / 1e3)
+    value = weak_value(R, args.steps, world, ms_max)
     pairs = st["pairs_kept"]
     # roofline of the dominant kernel (FP32 ALU bound)
     dom = max(("k_forward", "k_adjoint"), key=lambda k: kernels[k]["ms"])
@@ -337,7 +345,6 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(G, gd, loss, nv)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    del st0
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

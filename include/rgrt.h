@@ -204,7 +204,11 @@ int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *g
 int rgrt_prof_enable(rgrt_ctx *ctx, int on);
 int rgrt_prof_reset(rgrt_ctx *ctx);
 int rgrt_prof_get(rgrt_ctx *ctx, const char *name, int64_t *launches, double *ms);
-/* Counters of the last forward: pairs evaluated and pairs with m <= 9. */
+/* Pair counters (off by default: they cost a few instructions per pair).
+ * When enabled, each project_forward counts the (ray, Gaussian) pairs it
+ * evaluated and those with m <= 9; rgrt_stats_get returns the counts of the
+ * last forward and its number of (tile, Gaussian) entries. */
+int rgrt_stats_enable(rgrt_ctx *ctx, int on);
 int rgrt_stats_get(rgrt_ctx *ctx, int64_t *pairs_evaluated, int64_t *pairs_kept, int64_t *keys);
 
 #ifdef __cplusplus

@@ -82,6 +82,7 @@ struct rgrt_ctx {
     bool bin_valid = false;
     // profiling
     bool prof = false;
+    bool stats_on = false;
     std::vector<ProfRec> pending;
     std::map<std::string, std::pair<long long, double>> prof_acc;
     long long last_keys = 0;
@@ -379,8 +380,12 @@ int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float
         return RGRT_OK;
     }
     TRY(build_records(ctx, g, s));
-    TRY(ensure(ctx, ctx->stats, sizeof(Stats)));
-    CK(cudaMemsetAsync(ctx->stats.p, 0, sizeof(Stats), s));
+    Stats *st = nullptr;
+    if (ctx->stats_on) {
+        TRY(ensure(ctx, ctx->stats, sizeof(Stats)));
+        CK(cudaMemsetAsync(ctx->stats.p, 0, sizeof(Stats), s));
+        st = (Stats *)ctx->stats.p;
+    }
     ctx->last_keys = 0;
     return for_chunks(ctx, g, geom, s, false, [&](int v0, int nv, uint32_t K) -> int {
         (void)K;
@@ -388,7 +393,7 @@ int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float
         dg.v0 = v0;
         PROF("k_forward");
         CK(launch_forward(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
-                          out, (Stats *)ctx->stats.p, s));
+                          out, st, s));
         return RGRT_OK;
     });
 }
@@ -893,6 +898,13 @@ int rgrt_prof_get(rgrt_ctx *ctx, const char *name, int64_t *launches, double *ms
     auto it = ctx->prof_acc.find(name);
     if (launches) *launches = it == ctx->prof_acc.end() ? 0 : it->second.first;
     if (ms) *ms = it == ctx->prof_acc.end() ? 0.0 : it->second.second;
+    return RGRT_OK;
+}
+
+int rgrt_stats_enable(rgrt_ctx *ctx, int on)
+{
+    if (!ctx) return fail(RGRT_E_INVAL, "null context");
+    ctx->stats_on = on != 0;
     return RGRT_OK;
 }
 

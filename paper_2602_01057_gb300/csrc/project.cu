@@ -3,16 +3,33 @@
 // One CTA per detector tile of tile_w x tile_h rays, one ray per thread,
 // warps laid out as 8 x 4 ray blocks.  The tile's Gaussian list (ascending
 // ids) is walked in chunks: the CTA gathers each chunk's records into shared
-// memory together with the Gaussian's detector bounding box for this view;
-// a warp skips a Gaussian whose box misses its 8 x 4 block (a warp-uniform
-// branch), otherwise every lane evaluates its pair:
-//   delta = o - mu, recentred on the foot of the perpendicular from mu
-//   A = d^T P d, B = d^T P delta, C = delta^T P delta        (Eq. 7)
-//   m = C - B^2/A                                             (Eq. 9)
-//   f = rho sqrt(2 pi / A) exp(-m/2) Phi                      (Eqs. 10-11)
-//   Phi = 1/2 [erf(w_b) - erf(w_a)], w = (A t + B)/sqrt(2A)  (finite segment)
-// and the pair counts when m <= 9 (3-sigma cut).  FP32 throughout, FP32
-// accumulation per ray.
+// memory, turning every Gaussian into its view-space form for this view (see
+// below) together with its detector bounding box.  A warp skips a Gaussian
+// whose box misses its 8 x 4 block (a warp-uniform branch); otherwise every
+// lane evaluates its pair and the pair counts when m <= 9 (3-sigma cut).
+// FP32 throughout, FP32 accumulation per ray.
+//
+// The closed form (Eqs. 7-11) for a ray and one Gaussian is
+//   rho sqrt(2 pi / A) exp(-m/2),  A = d^T P d,  m = C - B^2/A,
+// with unit d.  Two exact rewritings make the per-pair work small:
+//  * m does not depend on the length of d, and
+//      A C - B^2 = (d x delta)^T cof(P) (d x delta),  cof(P) = Sigma / det Sigma,
+//    so m = Q / A with Q = c^T S c, c = d x delta, S = Sigma / det Sigma.
+//  * In the frame (e_u, e_v, e_w) of a view every ray is fixed by its
+//    detector coordinates (u, v).  For parallel rays (CT parallel beam, PET)
+//    d = e_w: A = P'_ww is a per-(Gaussian, view) constant and
+//    c = du e_v - dv e_u with (du, dv) = (u - mu_u, v - mu_v), so Q is a 2x2
+//    quadratic form.  For cone-beam rays from the source S, d~ = (u, v, dsd)
+//    and delta = S - mu is the same for every ray of the view; writing
+//    d~ = d~0 + (du, dv, 0) with d~0 the ray through mu, c = du g_u + dv g_v
+//    (g_u = e_u x delta, g_v = e_v x delta) and A(du, dv) = d~^T P' d~ are
+//    both quadratic in (du, dv), and the integral along the physical ray is
+//    |d~| rho sqrt(2 pi / A) exp(-Q/(2A)).
+// Both forms avoid the cancellation of C - B^2/A entirely.  Segment ends
+// (erf terms) only matter for a Gaussian whose 3-sigma ball lies within
+// 5.66 sigma of a segment end (then |w| < 4 is possible); such Gaussians take
+// the general path below, in world coordinates, with the ray re-based at the
+// foot of the perpendicular from mu.
 #include "rgrt_internal.h"
 
 namespace rgrt {
@@ -24,15 +41,27 @@ constexpr float INV_SQRTPI = 0.564189583547756287f;
 constexpr float SQRT_HALF = 0.707106781186547524f;
 constexpr float SKIP_K2 = 9.2f;   // skip boxes: a little wider than the 3-sigma cut
 constexpr float W_SAT = 4.0f;     // |w| >= 4: erf(w) == +-1 in binary32
-constexpr int FWD_CH = 128;
-constexpr int ADJ_CH = 64;
-constexpr int NG = 10;            // adjoint components per pair: dmu[3], G_P[6], drho
+constexpr float SAT_BALL = 8.66f; // (3 + 4 sqrt 2) sigma_max
+constexpr int CH = 256;             // records per chunk (one per thread in the prep)
+constexpr float NEG_HALF_LOG2E = -0.721347520444481703f;   // -log2(e)/2
+constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
+constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
+constexpr int NG = 10;            // general path: dmu[3], G_P[6], drho
+constexpr int NV_CONE = 12;       // view-space moments, cone beam
+constexpr int NV_PAR = 7;         // view-space moments, parallel rays
+constexpr int NSLOT = 12;
 
-struct SRec {
-    float4 a;   // mu, rho
-    float4 b;   // P00 P01 P02 P11
-    float4 c;   // P12 P22, gid (bits), 0
-    float4 bb;  // u_lo, u_hi, v_lo, v_hi of the (skip) detector box
+// a Gaussian in the view of the current tile (shared memory)
+// The Q coefficients carry the factor -log2(e)/2 (and, for parallel rays, 1/A)
+// so that arg = Q/A * (-log2(e)/2) feeds ex2 directly; m = -2 ln2 arg.
+struct VRec {
+    float4 c0;  // u0, v0, k M_uu, 2 k M_uv               (k = -log2(e)/2, x 1/A for parallel rays)
+    float4 c1;  // k M_vv, A0 (cone) | 1/A (parallel), 2 a_u (cone) | 1/sqrt(A) (parallel), 2 a_v
+    float4 c2;  // P'_uu, 2 P'_uv, P'_vv, alpha = rho sqrt(2 pi) (cone) | alpha/sqrt(A) (parallel)
+    float4 bb;  // u_lo, u_hi, v_lo, v_hi of the detector box (skip test)
+    float4 g0;  // mu, rho                      (general path)
+    float4 g1;  // P00 P01 P02 P11              (general path)
+    float4 g2;  // P12 P22, gid bits, 1 = view-space path / 0 = general path
 };
 
 struct Ray {
@@ -61,42 +90,95 @@ __device__ __forceinline__ bool cone_interval(float K2, float dsd, float ae, flo
     return true;
 }
 
-// gather one record and its detector box for view frame F
+// symmetric X (packed 00 01 02 11 12 22) in the view frame E = [e_u e_v e_w]:
+// out = (X'_uu, X'_uv, X'_uw, X'_vv, X'_vw, X'_ww)
+__device__ __forceinline__ void to_frame(const float *X, const float *eu, const float *ev,
+                                         const float *ew, float *out)
+{
+    out[0] = quad_form(X, eu, eu);
+    out[1] = quad_form(X, eu, ev);
+    out[2] = quad_form(X, eu, ew);
+    out[3] = quad_form(X, ev, ev);
+    out[4] = quad_form(X, ev, ew);
+    out[5] = quad_form(X, ew, ew);
+}
+
+// gather one record and turn it into its view-space form for frame F
 template <bool CONE>
 __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, uint32_t gid,
                                             const float4 *__restrict__ rec,
-                                            const float4 *__restrict__ crec, SRec &out)
+                                            const float4 *__restrict__ crec, VRec &out)
 {
-    float4 r0 = __ldg(rec + REC_F4 * (size_t)gid);
-    float4 r1 = __ldg(rec + REC_F4 * (size_t)gid + 1);
-    float4 r2 = __ldg(rec + REC_F4 * (size_t)gid + 2);
-    float4 c1 = __ldg(crec + CREC_F4 * (size_t)gid + 1);
-    float4 c2 = __ldg(crec + CREC_F4 * (size_t)gid + 2);
-    float Sg[6] = { c1.x, c1.y, c1.z, c1.w, c2.x, c2.y };
-    float m[3] = { r0.x, r0.y, r0.z };
-    float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
-    float mu_u = m[0] * eu[0] + m[1] * eu[1] + m[2] * eu[2];
-    float mu_v = m[0] * ev[0] + m[1] * ev[1] + m[2] * ev[2];
+    const float4 *r = rec + REC_F4 * (size_t)gid;
+    float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
+    float4 k1 = __ldg(crec + CREC_F4 * (size_t)gid + 1), k2 = __ldg(crec + CREC_F4 * (size_t)gid + 2);
+    const float Sg[6] = { k1.x, k1.y, k1.z, k1.w, k2.x, k2.y };
+    const float P[6] = { r1.x, r1.y, r1.z, r1.w, r2.x, r2.y };
+    const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
+    const float m[3] = { r0.x, r0.y, r0.z };
+    const float rho = r0.w, smax = r4.x;
+    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
+    const float mu_u = m[0] * eu[0] + m[1] * eu[1] + m[2] * eu[2];
+    const float mu_v = m[0] * ev[0] + m[1] * ev[1] + m[2] * ev[2];
+    const float mu_w = m[0] * ew[0] + m[1] * ew[1] + m[2] * ew[2];
+    float Pf[6], Sf[6];
+    to_frame(P, eu, ev, ew, Pf);
+    to_frame(Sh, eu, ev, ew, Sf);
     float ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
+    bool sat;
     if (CONE) {
-        float aw = m[0] * ew[0] + m[1] * ew[1] + m[2] * ew[2] + g.dso;
+        const float D = mu_w + g.dso;           // depth of mu from the source
         float suu = quad_form(Sg, eu, eu), svv = quad_form(Sg, ev, ev), sww = quad_form(Sg, ew, ew);
         float suw = quad_form(Sg, eu, ew), svw = quad_form(Sg, ev, ew);
         float lo, hi;
-        if (cone_interval(SKIP_K2, g.dsd, mu_u, aw, suu, suw, sww, lo, hi)) { ulo = lo; uhi = hi; }
-        if (cone_interval(SKIP_K2, g.dsd, mu_v, aw, svv, svw, sww, lo, hi)) { vlo = lo; vhi = hi; }
+        if (cone_interval(SKIP_K2, g.dsd, mu_u, D, suu, suw, sww, lo, hi)) { ulo = lo; uhi = hi; }
+        if (cone_interval(SKIP_K2, g.dsd, mu_v, D, svv, svw, sww, lo, hi)) { vlo = lo; vhi = hi; }
+        const float iD = 1.0f / D;
+        const float u0 = g.dsd * mu_u * iD, v0 = g.dsd * mu_v * iD;
+        // A(du, dv) = d~^T P' d~, d~ = (u0 + du, v0 + dv, dsd)
+        const float au = Pf[0] * u0 + Pf[1] * v0 + Pf[2] * g.dsd;
+        const float av = Pf[1] * u0 + Pf[3] * v0 + Pf[4] * g.dsd;
+        const float aw = Pf[2] * u0 + Pf[4] * v0 + Pf[5] * g.dsd;
+        const float A0 = au * u0 + av * v0 + aw * g.dsd;
+        // g_u = e_u x delta = (0, D, -mu_v), g_v = e_v x delta = (-D, 0, mu_u)
+        const float guv = D, guw = -mu_v, gvu = -D, gvw = mu_u;
+        const float cu1 = Sf[3] * guv + Sf[4] * guw, cu2 = Sf[4] * guv + Sf[5] * guw;  // (S' g_u)_{v,w}
+        const float cv0 = Sf[0] * gvu + Sf[2] * gvw, cv1 = Sf[1] * gvu + Sf[4] * gvw,
+                    cv2 = Sf[2] * gvu + Sf[5] * gvw;                                  // S' g_v
+        const float Muu = guv * cu1 + guw * cu2;
+        const float Muv = guv * cv1 + guw * cv2;
+        const float Mvv = gvu * cv0 + gvw * cv2;
+        const float k = NEG_HALF_LOG2E;
+        out.c0 = make_float4(u0, v0, k * Muu, 2.0f * k * Muv);
+        out.c1 = make_float4(k * Mvv, A0, 2.0f * au, 2.0f * av);
+        out.c2 = make_float4(Pf[0], 2.0f * Pf[1], Pf[3], rho * SQRT2PI);
+        // both segment ends (source, detector plane) beyond the 8.66-sigma ball
+        sat = D >= SAT_BALL * smax && (g.dsd - D) >= SAT_BALL * smax;
     } else {
         float hu = sqrtf(SKIP_K2 * quad_form(Sg, eu, eu));
         float hv = sqrtf(SKIP_K2 * quad_form(Sg, ev, ev));
         ulo = mu_u - hu; uhi = mu_u + hu; vlo = mu_v - hv; vhi = mu_v + hv;
+        const float iA = 1.0f / Pf[5];
+        const float rA = sqrtf(iA);
+        // c = du e_v - dv e_u: M_uu = S'_vv, M_uv = -S'_uv, M_vv = S'_uu
+        const float k = NEG_HALF_LOG2E * iA;
+        out.c0 = make_float4(mu_u, mu_v, k * Sf[3], -2.0f * k * Sf[1]);
+        out.c1 = make_float4(k * Sf[0], iA, rA, 0.0f);
+        out.c2 = make_float4(0.0f, 0.0f, 0.0f, rho * SQRT2PI * rA);
+        if (g.pet) {
+            float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
+            sat = rxy + SAT_BALL * smax <= sqrtf(g.radius2);
+        } else {
+            sat = mu_w - SAT_BALL * smax >= g.t_a && mu_w + SAT_BALL * smax <= g.t_b;
+        }
     }
-    out.a = r0;
-    out.b = r1;
-    out.c = make_float4(r2.x, r2.y, __uint_as_float(gid), 0.0f);
     out.bb = make_float4(ulo, uhi, vlo, vhi);
+    out.g0 = r0;
+    out.g1 = r1;
+    out.g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), sat ? 1.0f : 0.0f);
 }
 
-// ray of detector pixel (u, v) in view frame F (FP32; see ray set-up notes)
+// ray of detector pixel (u, v) in view frame F (FP32), for the general path
 template <bool CONE>
 __device__ __forceinline__ Ray make_ray(const DevGeom &g, const float *F, float u, float v)
 {
@@ -143,13 +225,15 @@ struct PairGeo {
     float A, B, C, rA, iA, m;
 };
 
-__device__ __forceinline__ void pair_geo(const Ray &r, const SRec &s, PairGeo &q)
+// general path: A, B, C, m of Eq. 7/9 with delta re-based at the foot of the
+// perpendicular from mu (B small, no cancellation in C - B^2/A)
+__device__ __forceinline__ void pair_geo(const Ray &r, const VRec &s, PairGeo &q)
 {
-    float ex = r.ox - s.a.x, ey = r.oy - s.a.y, ez = r.oz - s.a.z;
+    float ex = r.ox - s.g0.x, ey = r.oy - s.g0.y, ez = r.oz - s.g0.z;
     float tau = r.dx * ex + r.dy * ey + r.dz * ez;
     q.px = ex - tau * r.dx; q.py = ey - tau * r.dy; q.pz = ez - tau * r.dz;
     q.ta = r.ta + tau; q.tb = r.tb + tau;
-    const float P00 = s.b.x, P01 = s.b.y, P02 = s.b.z, P11 = s.b.w, P12 = s.c.x, P22 = s.c.y;
+    const float P00 = s.g1.x, P01 = s.g1.y, P02 = s.g1.z, P11 = s.g1.w, P12 = s.g2.x, P22 = s.g2.y;
     q.Pdx = P00 * r.dx + P01 * r.dy + P02 * r.dz;
     q.Pdy = P01 * r.dx + P11 * r.dy + P12 * r.dz;
     q.Pdz = P02 * r.dx + P12 * r.dy + P22 * r.dz;
@@ -250,177 +334,457 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g)
     return c;
 }
 
-__device__ __forceinline__ bool box_hits(const TileCtx &c, const float4 &bb)
+// general-path value: K = rho sqrt(2pi/A) e^{-m/2}; returns K Phi
+__device__ __forceinline__ float general_value(const PairGeo &q, float rho)
 {
-    return !(bb.y < c.wu_lo || bb.x > c.wu_hi || bb.w < c.wv_lo || bb.z > c.wv_hi);
+    const float E = __expf(-0.5f * q.m);
+    const float K = rho * SQRT2PI * q.rA * E;
+    const float sc = q.rA * SQRT_HALF;
+    const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
+    float phi = 1.0f;
+    if (!(wa <= -W_SAT && wb >= W_SAT)) phi = 0.5f * (erff(wb) - erff(wa));
+    return K * phi;
 }
 
-template <bool CONE>
-__global__ void __launch_bounds__(256) k_forward(DevGeom g, const float4 *__restrict__ rec,
-                                                 const float4 *__restrict__ crec,
-                                                 const uint32_t *__restrict__ gids,
-                                                 const uint2 *__restrict__ ranges,
-                                                 float *__restrict__ out, Stats *stats)
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    __shared__ SRec srec[FWD_CH];
-    __shared__ float Fs[9];
-    TileCtx c = tile_ctx(g);
-    if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
-    __syncthreads();
-    float F[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) F[i] = Fs[i];
-    float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
-    float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
-    Ray ray = make_ray<CONE>(g, F, u, v);
-    uint2 rg = ranges[blockIdx.x];
-    float acc = 0.0f;
-    unsigned long long n_eval = 0, n_kept = 0;
-    const int nthr = blockDim.x;
-    for (uint32_t base = rg.x; base < rg.y; base += FWD_CH) {
-        int cnt = min((uint32_t)FWD_CH, rg.y - base);
-        for (int i = threadIdx.x; i < cnt; i += nthr)
-            prep_record<CONE>(g, F, __ldg(gids + base + i), rec, crec, srec[i]);
-        __syncthreads();
-        for (int j = 0; j < cnt; j++) {
-            float4 bb = srec[j].bb;
-            if (!box_hits(c, bb)) continue;
-            SRec s;
-            s.a = srec[j].a; s.b = srec[j].b; s.c = srec[j].c;
-            PairGeo q;
-            pair_geo(ray, s, q);
-            float E = __expf(-0.5f * q.m);
-            float K = s.a.w * SQRT2PI * q.rA * E;
-            float sc = q.rA * SQRT_HALF;
-            float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
-            float phi = 1.0f;
-            if (!(wa <= -W_SAT && wb >= W_SAT)) phi = 0.5f * (erff(wb) - erff(wa));
-            bool keep = c.valid && q.m <= PAIR_CUT2;
-            acc += keep ? K * phi : 0.0f;
-            n_eval += c.valid;
-            n_kept += keep;
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Per chunk: every thread turns one record into its view-space form and tests
+// its detector box against the 8 x 4 ray block of every warp of the tile
+// (bit w of msk); then each warp compacts, in record order, the records that
+// touch its block into a list of view-space records and a list of general ones.
+struct ChunkLists {
+    uint8_t vs[8][CH];
+    uint8_t gen[8][CH];
+};
+
+template <bool CONE>
+__device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
+                                           uint32_t base, int cnt, const float4 *rec,
+                                           const float4 *crec, VRec *sv, const float4 *wbox,
+                                           int nw, uint32_t *msk)
+{
+    const int i = threadIdx.x;
+    if (i < cnt) {
+        prep_record<CONE>(g, F, __ldg(gids + base + i), rec, crec, sv[i]);
+        const float4 bb = sv[i].bb;
+        uint32_t m = 0;
+        for (int w = 0; w < nw; w++) {
+            const float4 wb = wbox[w];
+            const bool hit = !(bb.y < wb.x || bb.x > wb.y || bb.w < wb.z || bb.z > wb.w);
+            m |= (uint32_t)hit << w;
         }
-        __syncthreads();
-    }
-    if (c.valid) out[c.out_idx] = acc;
-    if (stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
-            n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&stats->pairs_eval, n_eval);
-            atomicAdd(&stats->pairs_kept, n_kept);
-        }
+        if (sv[i].g2.w != 0.0f) m |= 0x100u;
+        msk[i] = m;
     }
 }
 
-template <bool CONE>
-__global__ void __launch_bounds__(256) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
-                                                 const float4 *__restrict__ crec,
-                                                 const uint32_t *__restrict__ gids,
-                                                 const uint2 *__restrict__ ranges,
-                                                 const float *__restrict__ dLdI,
-                                                 float4 *__restrict__ grad)
+// warp-private compaction; returns the list lengths in nvs, ngen
+__device__ __forceinline__ void build_lists(int cnt, const uint32_t *msk, ChunkLists &L, int w,
+                                            int lane, int &nvs, int &ngen)
 {
-    __shared__ SRec srec[ADJ_CH];
-    __shared__ float part[ADJ_CH][8][NG];   // per record, per warp, per component
+    const uint32_t lt = (1u << lane) - 1u;
+    nvs = 0;
+    ngen = 0;
+    for (int b = 0; b < cnt; b += 32) {
+        const int i = b + lane;
+        const uint32_t m = i < cnt ? msk[i] : 0u;
+        const bool in = (m >> w) & 1u;
+        const bool vs = (m & 0x100u) != 0u;
+        const uint32_t bv = __ballot_sync(0xffffffffu, in && vs);
+        const uint32_t bg = __ballot_sync(0xffffffffu, in && !vs);
+        if (in && vs) L.vs[w][nvs + __popc(bv & lt)] = (uint8_t)i;
+        if (in && !vs) L.gen[w][ngen + __popc(bg & lt)] = (uint8_t)i;
+        nvs += __popc(bv);
+        ngen += __popc(bg);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void warp_box(const TileCtx &c, float4 *wbox)
+{
+    if ((threadIdx.x & 31) == 0) wbox[threadIdx.x >> 5] = make_float4(c.wu_lo, c.wu_hi, c.wv_lo, c.wv_hi);
+}
+
+// view-space value of one pair (without the |d~| factor of cone beam);
+// returns arg = -m log2(e)/2
+template <bool CONE>
+__device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float &arg)
+{
+    const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
+    const float du = u - c0.x, dv = v - c0.y;
+    const float q = du * (c0.z * du + c0.w * dv) + c1.x * dv * dv;
+    if (CONE) {
+        const float A = c1.y + du * (c1.z + c2.x * du + c2.y * dv) + dv * (c1.w + c2.z * dv);
+        const float rA = rsqrt_approx(A);
+        arg = q * (rA * rA);
+        return c2.w * rA * ex2_approx(arg);
+    }
+    arg = q;
+    return c2.w * ex2_approx(arg);
+}
+
+template <bool CONE, bool STATS>
+__global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__restrict__ rec,
+                                                    const float4 *__restrict__ crec,
+                                                    const uint32_t *__restrict__ gids,
+                                                    const uint2 *__restrict__ ranges,
+                                                    float *__restrict__ out, Stats *stats)
+{
+    __shared__ VRec sv[CH];
+    __shared__ ChunkLists lists;
+    __shared__ uint32_t msk[CH];
+    __shared__ float4 wbox[8];
     __shared__ float Fs[9];
-    TileCtx c = tile_ctx(g);
+    const TileCtx c = tile_ctx(g);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
+    warp_box(c, wbox);
     __syncthreads();
     float F[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) F[i] = Fs[i];
-    float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
-    float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
-    Ray ray = make_ray<CONE>(g, F, u, v);
-    float gw = c.valid ? __ldg(dLdI + c.out_idx) : 0.0f;
-    uint2 rg = ranges[blockIdx.x];
-    const int nthr = blockDim.x;
-    for (uint32_t base = rg.x; base < rg.y; base += ADJ_CH) {
-        int cnt = min((uint32_t)ADJ_CH, rg.y - base);
-        for (int i = threadIdx.x; i < cnt; i += nthr)
-            prep_record<CONE>(g, F, __ldg(gids + base + i), rec, crec, srec[i]);
+    const float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
+    const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
+    const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd) : 1.0f;
+    const uint2 rg = ranges[blockIdx.x];
+    float acc_vs = 0.0f, acc_gen = 0.0f;
+    unsigned n_eval = 0, n_kept = 0;
+    for (uint32_t base = rg.x; base < rg.y; base += CH) {
+        const int cnt = min((uint32_t)CH, rg.y - base);
+        prep_chunk<CONE>(g, F, gids, base, cnt, rec, crec, sv, wbox, nw, msk);
         __syncthreads();
-        for (int j = 0; j < cnt; j++) {
-            float4 bb = srec[j].bb;
-            if (!box_hits(c, bb)) {
-                if (lane < NG) part[j][w][lane] = 0.0f;
-                continue;
+        int nvs, ngen;
+        build_lists(cnt, msk, lists, w, lane, nvs, ngen);
+        int k = 0;
+        for (; k + 1 < nvs; k += 2) {
+            const int j0 = lists.vs[w][k], j1 = lists.vs[w][k + 1];
+            float a0, a1;
+            const float v0 = vs_value<CONE>(sv[j0], u, v, a0);
+            const float v1 = vs_value<CONE>(sv[j1], u, v, a1);
+            acc_vs += a0 >= CUT_ARG ? v0 : 0.0f;
+            acc_vs += a1 >= CUT_ARG ? v1 : 0.0f;
+            if (STATS) n_kept += (a0 >= CUT_ARG) + (a1 >= CUT_ARG);
+        }
+        if (k < nvs) {
+            float a0;
+            const float v0 = vs_value<CONE>(sv[lists.vs[w][k]], u, v, a0);
+            acc_vs += a0 >= CUT_ARG ? v0 : 0.0f;
+            if (STATS) n_kept += a0 >= CUT_ARG;
+        }
+        if (ngen > 0) {
+            const Ray ray = make_ray<CONE>(g, F, u, v);
+            for (int k2 = 0; k2 < ngen; k2++) {
+                const VRec &r = sv[lists.gen[w][k2]];
+                PairGeo q;
+                pair_geo(ray, r, q);
+                const float val = general_value(q, r.g0.w);
+                acc_gen += q.m <= PAIR_CUT2 ? val : 0.0f;
+                if (STATS) n_kept += q.m <= PAIR_CUT2;
             }
-            SRec s;
-            s.a = srec[j].a; s.b = srec[j].b; s.c = srec[j].c;
-            PairGeo q;
-            pair_geo(ray, s, q);
-            float val[NG];
-            bool keep = c.valid && q.m <= PAIR_CUT2 && gw != 0.0f;
-            if (keep) {
-                float E = __expf(-0.5f * q.m);
-                float K = s.a.w * SQRT2PI * q.rA * E;
-                float sc = q.rA * SQRT_HALF;
-                float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
-                float phi = 1.0f, dPhiB = 0.0f, dPhiA = 0.0f;
-                if (!(wa <= -W_SAT && wb >= W_SAT)) {
-                    phi = 0.5f * (erff(wb) - erff(wa));
-                    float ea = __expf(-wa * wa), eb = __expf(-wb * wb);
-                    dPhiB = (eb - ea) * q.rA * INV_SQRT2PI;
-                    float tA = 2.0f * q.A;
-                    float r32 = rsqrtf(tA) / tA;  // (2A)^-3/2
-                    dPhiA = (eb * (q.A * q.tb - q.B) - ea * (q.A * q.ta - q.B)) * INV_SQRTPI * r32;
-                }
-                float f = K * phi;
-                float fC = -0.5f * f;
-                float fB = f * q.B * q.iA + K * dPhiB;
-                float fA = -0.5f * f * q.iA * (1.0f + q.B * q.B * q.iA) + K * dPhiA;
-                // gradient w.r.t. the recentred delta: fB P d + 2 fC P delta
-                float gx = fB * q.Pdx + 2.0f * fC * q.Ppx;
-                float gy = fB * q.Pdy + 2.0f * fC * q.Ppy;
-                float gz = fB * q.Pdz + 2.0f * fC * q.Ppz;
-                float dg = ray.dx * gx + ray.dy * gy + ray.dz * gz;
-                float st = K * q.A * dPhiB;  // d f / d(segment shift)
-                // d mu = -(I - d d^T) grad - d * st
-                val[0] = gw * (-(gx - ray.dx * dg) - ray.dx * st);
-                val[1] = gw * (-(gy - ray.dy * dg) - ray.dy * st);
-                val[2] = gw * (-(gz - ray.dz * dg) - ray.dz * st);
-                // symmetric gradient w.r.t. P: fA d d^T + fB sym(d p^T) + fC p p^T
-                float hB = 0.5f * fB;
-                val[3] = gw * (fA * ray.dx * ray.dx + 2.0f * hB * ray.dx * q.px + fC * q.px * q.px);
-                val[4] = gw * (fA * ray.dx * ray.dy + hB * (ray.dx * q.py + q.px * ray.dy) + fC * q.px * q.py);
-                val[5] = gw * (fA * ray.dx * ray.dz + hB * (ray.dx * q.pz + q.px * ray.dz) + fC * q.px * q.pz);
-                val[6] = gw * (fA * ray.dy * ray.dy + 2.0f * hB * ray.dy * q.py + fC * q.py * q.py);
-                val[7] = gw * (fA * ray.dy * ray.dz + hB * (ray.dy * q.pz + q.py * ray.dz) + fC * q.py * q.pz);
-                val[8] = gw * (fA * ray.dz * ray.dz + 2.0f * hB * ray.dz * q.pz + fC * q.pz * q.pz);
-                val[9] = gw * (SQRT2PI * q.rA * E * phi);
+        }
+        if (STATS) n_eval += nvs + ngen;
+        __syncthreads();
+    }
+    if (c.valid) out[c.out_idx] = acc_gen + L * acc_vs;
+    if (STATS) {
+        unsigned long long e = c.valid ? n_eval : 0, kk = c.valid ? n_kept : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            kk += __shfl_xor_sync(0xffffffffu, kk, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&stats->pairs_eval, e);
+            atomicAdd(&stats->pairs_kept, kk);
+        }
+    }
+}
+
+// symmetric 3x3 (packed 00 01 02 11 12 22) back to world: G = E G' E^T
+__device__ __forceinline__ void from_frame(const float *Gf, const float *eu, const float *ev,
+                                           const float *ew, float *G)
+{
+    const float *E[3] = { eu, ev, ew };
+    const float M[3][3] = { { Gf[0], Gf[1], Gf[2] }, { Gf[1], Gf[3], Gf[4] }, { Gf[2], Gf[4], Gf[5] } };
+    const int ia[6] = { 0, 0, 0, 1, 1, 2 }, ib[6] = { 0, 1, 2, 1, 2, 2 };
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) s += E[i][ia[e]] * M[i][j] * E[j][ib[e]];
+        G[e] = s;
+    }
+}
+
+__device__ __forceinline__ void cross_acc(const float *a, const float *b, float s, float *o)
+{
+    o[0] += s * (a[1] * b[2] - a[2] * b[1]);
+    o[1] += s * (a[2] * b[0] - a[0] * b[2]);
+    o[2] += s * (a[0] * b[1] - a[1] * b[0]);
+}
+
+// Gradient w.r.t. (mu, rho, G_P, G_S) of one Gaussian from its view-space
+// moments s[] summed over the tile's rays:
+//   cone:  s = [SQ_u, SQ_v, SQ_uu, SQ_uv, SQ_vv, SA, SA_u, SA_v, SA_uu, SA_uv, SA_vv, Sw]
+//   par.:  s = [SQ_u, SQ_v, SQ_uu, SQ_uv, SQ_vv, SA, Sw]
+// where SQ_x = sum (dL/dQ / alpha) x, SA_x = sum (dL/dA / alpha) x (x a
+// monomial in du, dv), Sw = sum dL/dI |d~| A^-1/2 e^{-m/2} and
+// alpha = rho sqrt(2 pi).  With c = du g_u + dv g_v and d~ = d~0 + (du, dv, 0):
+//   dL/dS'  = sum dL/dQ c c^T
+//   dL/dP'  = sum dL/dA d~ d~^T
+//   dL/dmu' = -2 sum dL/dQ (S' c) x d~      (Q = c^T S' c, c = d~ x (S - mu'))
+//   dL/drho = sqrt(2 pi) Sw
+// out16 = (dmu[3], drho, G_P[6], G_S[6]) in world coordinates.
+template <bool CONE>
+__device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, const float4 *rec,
+                                           uint32_t gid, const float *s, float *out16)
+{
+    const float4 *r = rec + REC_F4 * (size_t)gid;
+    const float4 r0 = __ldg(r), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
+    const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
+    const float m[3] = { r0.x, r0.y, r0.z };
+    const float alpha = r0.w * SQRT2PI;
+    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
+    float Sf[6];
+    to_frame(Sh, eu, ev, ew, Sf);
+    const float mu_u = m[0] * eu[0] + m[1] * eu[1] + m[2] * eu[2];
+    const float mu_v = m[0] * ev[0] + m[1] * ev[1] + m[2] * ev[2];
+    const float mu_w = m[0] * ew[0] + m[1] * ew[1] + m[2] * ew[2];
+    const float SQu = alpha * s[0], SQv = alpha * s[1], SQuu = alpha * s[2], SQuv = alpha * s[3],
+                SQvv = alpha * s[4];
+    float gu[3], gv[3], d0[3], GPf[6], GSf[6];
+    float Sw;
+    if (CONE) {
+        const float D = mu_w + g.dso;
+        const float u0 = g.dsd * mu_u / D, v0 = g.dsd * mu_v / D;
+        gu[0] = 0.0f; gu[1] = D; gu[2] = -mu_v;
+        gv[0] = -D; gv[1] = 0.0f; gv[2] = mu_u;
+        d0[0] = u0; d0[1] = v0; d0[2] = g.dsd;
+        const float SA = alpha * s[5], SAu = alpha * s[6], SAv = alpha * s[7], SAuu = alpha * s[8],
+                    SAuv = alpha * s[9], SAvv = alpha * s[10];
+        Sw = s[11];
+        // dL/dP' = SA d0 d0^T + (d0 m^T + m d0^T) + N,  m = (SAu, SAv, 0)
+        GPf[0] = SA * d0[0] * d0[0] + 2.0f * d0[0] * SAu + SAuu;
+        GPf[1] = SA * d0[0] * d0[1] + d0[0] * SAv + SAu * d0[1] + SAuv;
+        GPf[2] = SA * d0[0] * d0[2] + SAu * d0[2];
+        GPf[3] = SA * d0[1] * d0[1] + 2.0f * d0[1] * SAv + SAvv;
+        GPf[4] = SA * d0[1] * d0[2] + SAv * d0[2];
+        GPf[5] = SA * d0[2] * d0[2];
+    } else {
+        // c = du e_v - dv e_u: "g_u" = e_v, "g_v" = -e_u (frame coordinates), d~ = e_w
+        gu[0] = 0.0f; gu[1] = 1.0f; gu[2] = 0.0f;
+        gv[0] = -1.0f; gv[1] = 0.0f; gv[2] = 0.0f;
+        d0[0] = 0.0f; d0[1] = 0.0f; d0[2] = 1.0f;
+        Sw = s[6];
+        GPf[0] = GPf[1] = GPf[2] = GPf[3] = GPf[4] = 0.0f;
+        GPf[5] = alpha * s[5];
+    }
+    float cu[3], cv[3];   // S' g_u, S' g_v
+    cu[0] = Sf[0] * gu[0] + Sf[1] * gu[1] + Sf[2] * gu[2];
+    cu[1] = Sf[1] * gu[0] + Sf[3] * gu[1] + Sf[4] * gu[2];
+    cu[2] = Sf[2] * gu[0] + Sf[4] * gu[1] + Sf[5] * gu[2];
+    cv[0] = Sf[0] * gv[0] + Sf[1] * gv[1] + Sf[2] * gv[2];
+    cv[1] = Sf[1] * gv[0] + Sf[3] * gv[1] + Sf[4] * gv[2];
+    cv[2] = Sf[2] * gv[0] + Sf[4] * gv[1] + Sf[5] * gv[2];
+    {
+        const int ia[6] = { 0, 0, 0, 1, 1, 2 }, ib[6] = { 0, 1, 2, 1, 2, 2 };
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            const int a = ia[e], b = ib[e];
+            GSf[e] = SQuu * gu[a] * gu[b] + SQuv * (gu[a] * gv[b] + gv[a] * gu[b]) + SQvv * gv[a] * gv[b];
+        }
+    }
+    // T = sum dL/dQ (S'c) x d~ = cu x d0 SQu + cv x d0 SQv
+    //     + cu x e_u SQuu + (cu x e_v + cv x e_u) SQuv + cv x e_v SQvv
+    // (the last three only for the cone: parallel rays keep d~ = e_w)
+    float T[3] = { 0.0f, 0.0f, 0.0f };
+    cross_acc(cu, d0, SQu, T);
+    cross_acc(cv, d0, SQv, T);
+    if (CONE) {
+        const float eU[3] = { 1.0f, 0.0f, 0.0f }, eV[3] = { 0.0f, 1.0f, 0.0f };
+        cross_acc(cu, eU, SQuu, T);
+        cross_acc(cu, eV, SQuv, T);
+        cross_acc(cv, eU, SQuv, T);
+        cross_acc(cv, eV, SQvv, T);
+    }
+    const float dmuf[3] = { -2.0f * T[0], -2.0f * T[1], -2.0f * T[2] };
+    out16[0] = dmuf[0] * eu[0] + dmuf[1] * ev[0] + dmuf[2] * ew[0];
+    out16[1] = dmuf[0] * eu[1] + dmuf[1] * ev[1] + dmuf[2] * ew[1];
+    out16[2] = dmuf[0] * eu[2] + dmuf[1] * ev[2] + dmuf[2] * ew[2];
+    out16[3] = SQRT2PI * Sw;
+    from_frame(GPf, eu, ev, ew, out16 + 4);
+    from_frame(GSf, eu, ev, ew, out16 + 10);
+}
+
+// general-path gradient of one pair: dmu[3], G_P[6], drho (times dL/dI)
+__device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, float rho, float gw,
+                                             float *val)
+{
+    const float E = __expf(-0.5f * q.m);
+    const float K = rho * SQRT2PI * q.rA * E;
+    const float sc = q.rA * SQRT_HALF;
+    const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
+    float phi = 1.0f, dPhiB = 0.0f, dPhiA = 0.0f;
+    if (!(wa <= -W_SAT && wb >= W_SAT)) {
+        phi = 0.5f * (erff(wb) - erff(wa));
+        const float ea = __expf(-wa * wa), eb = __expf(-wb * wb);
+        dPhiB = (eb - ea) * q.rA * INV_SQRT2PI;
+        const float tA = 2.0f * q.A;
+        const float r32 = rsqrtf(tA) / tA;  // (2A)^-3/2
+        dPhiA = (eb * (q.A * q.tb - q.B) - ea * (q.A * q.ta - q.B)) * INV_SQRTPI * r32;
+    }
+    const float f = K * phi;
+    const float fC = -0.5f * f;
+    const float fB = f * q.B * q.iA + K * dPhiB;
+    const float fA = -0.5f * f * q.iA * (1.0f + q.B * q.B * q.iA) + K * dPhiA;
+    // gradient w.r.t. the recentred delta: fB P d + 2 fC P delta
+    const float gx = fB * q.Pdx + 2.0f * fC * q.Ppx;
+    const float gy = fB * q.Pdy + 2.0f * fC * q.Ppy;
+    const float gz = fB * q.Pdz + 2.0f * fC * q.Ppz;
+    const float dg = ray.dx * gx + ray.dy * gy + ray.dz * gz;
+    const float st = K * q.A * dPhiB;  // d f / d(segment shift)
+    // d mu = -(I - d d^T) grad - d * st
+    val[0] = gw * (-(gx - ray.dx * dg) - ray.dx * st);
+    val[1] = gw * (-(gy - ray.dy * dg) - ray.dy * st);
+    val[2] = gw * (-(gz - ray.dz * dg) - ray.dz * st);
+    // symmetric gradient w.r.t. P: fA d d^T + fB sym(d p^T) + fC p p^T
+    const float hB = 0.5f * fB;
+    val[3] = gw * (fA * ray.dx * ray.dx + 2.0f * hB * ray.dx * q.px + fC * q.px * q.px);
+    val[4] = gw * (fA * ray.dx * ray.dy + hB * (ray.dx * q.py + q.px * ray.dy) + fC * q.px * q.py);
+    val[5] = gw * (fA * ray.dx * ray.dz + hB * (ray.dx * q.pz + q.px * ray.dz) + fC * q.px * q.pz);
+    val[6] = gw * (fA * ray.dy * ray.dy + 2.0f * hB * ray.dy * q.py + fC * q.py * q.py);
+    val[7] = gw * (fA * ray.dy * ray.dz + hB * (ray.dy * q.pz + q.py * ray.dz) + fC * q.py * q.pz);
+    val[8] = gw * (fA * ray.dz * ray.dz + 2.0f * hB * ray.dz * q.pz + fC * q.pz * q.pz);
+    val[9] = gw * (SQRT2PI * q.rA * E * phi);
+}
+
+template <bool CONE>
+__global__ void __launch_bounds__(256, 3) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
+                                                    const float4 *__restrict__ crec,
+                                                    const uint32_t *__restrict__ gids,
+                                                    const uint2 *__restrict__ ranges,
+                                                    const float *__restrict__ dLdI,
+                                                    float4 *__restrict__ grad)
+{
+    __shared__ VRec sv[CH];
+    __shared__ ChunkLists lists;
+    __shared__ uint32_t msk[CH];
+    __shared__ float part[CH][NSLOT];   // per record: moments summed over the tile's warps
+    __shared__ float4 wbox[8];
+    __shared__ float Fs[9];
+    const TileCtx c = tile_ctx(g);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
+    warp_box(c, wbox);
+    __syncthreads();
+    float F[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) F[i] = Fs[i];
+    const float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
+    const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
+    const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd) : 1.0f;
+    const float gw = c.valid ? __ldg(dLdI + c.out_idx) : 0.0f;
+    const float gL = gw * L;
+    const uint2 rg = ranges[blockIdx.x];
+    for (uint32_t base = rg.x; base < rg.y; base += CH) {
+        const int cnt = min((uint32_t)CH, rg.y - base);
+        prep_chunk<CONE>(g, F, gids, base, cnt, rec, crec, sv, wbox, nw, msk);
+        if (threadIdx.x < cnt) {
+#pragma unroll
+            for (int k = 0; k < NSLOT; k++) part[threadIdx.x][k] = 0.0f;
+        }
+        __syncthreads();
+        int nvs, ngen;
+        build_lists(cnt, msk, lists, w, lane, nvs, ngen);
+        for (int k = 0; k < nvs; k++) {
+            // view-space path: moments of dL/dQ and dL/dA over the rays
+            const int j = lists.vs[w][k];
+            const float4 c0 = sv[j].c0, c1 = sv[j].c1, c2 = sv[j].c2;
+            const float du = u - c0.x, dv = v - c0.y;
+            const float du2 = du * du, dudv = du * dv, dv2 = dv * dv;
+            const float q = c0.z * du2 + c0.w * dudv + c1.x * dv2;
+            float rA, iA;
+            if (CONE) {
+                const float A = c1.y + c1.z * du + c1.w * dv + c2.x * du2 + c2.y * dudv + c2.z * dv2;
+                rA = rsqrt_approx(A);
+                iA = rA * rA;
             } else {
-#pragma unroll
-                for (int k = 0; k < NG; k++) val[k] = 0.0f;
+                iA = c1.y;
+                rA = c1.z;
             }
-            int idx = tr_reduce<NG>(val, lane);
-            if (idx < NG) part[j][w][idx] = val[0];
+            const float arg = CONE ? q * iA : q;
+            const float m = arg * M_PER_ARG;
+            // wv = dL/dI |d~| A^-1/2 e^{-m/2}; dL/dQ = -alpha wv/(2A), dL/dA = alpha wv (m-1)/(2A)
+            const float wv = arg >= CUT_ARG ? gL * rA * ex2_approx(arg) : 0.0f;
+            const float h = 0.5f * wv * iA;
+            const float gQ = -h, gA = h * (m - 1.0f);
+            if (CONE) {
+                float val[NV_CONE] = { gQ * du, gQ * dv, gQ * du2, gQ * dudv, gQ * dv2, gA,
+                                       gA * du, gA * dv, gA * du2, gA * dudv, gA * dv2, wv };
+                const int idx = tr_reduce<NV_CONE>(val, lane);
+                if (idx < NV_CONE) atomicAdd(&part[j][idx], val[0]);
+            } else {
+                float val[NV_PAR] = { gQ * du, gQ * dv, gQ * du2, gQ * dudv, gQ * dv2, gA, wv };
+                const int idx = tr_reduce<NV_PAR>(val, lane);
+                if (idx < NV_PAR) atomicAdd(&part[j][idx], val[0]);
+            }
         }
-        __syncthreads();
-        // sum over warps, then one set of vector atomics per Gaussian
-        for (int e = threadIdx.x; e < cnt * NG; e += nthr) {
-            int j = e / NG, k = e - j * NG;
-            float s = 0.0f;
-            for (int ww = 0; ww < nw; ww++) s += part[j][ww][k];
-            part[j][0][k] = s;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += nthr) {
-            const float *p = part[j][0];
-            bool any = false;
+        if (ngen > 0) {
+            const Ray ray = make_ray<CONE>(g, F, u, v);
+            for (int k = 0; k < ngen; k++) {
+                const int j = lists.gen[w][k];
+                PairGeo q;
+                pair_geo(ray, sv[j], q);
+                float val[NG];
+                if (q.m <= PAIR_CUT2 && gw != 0.0f) {
+                    general_grad(ray, q, sv[j].g0.w, gw, val);
+                } else {
 #pragma unroll
-            for (int k = 0; k < NG; k++) any |= p[k] != 0.0f;
-            if (!any) continue;
-            uint32_t gid = __float_as_uint(srec[j].c.z);
-            float4 *gp = grad + GRAD_F4 * (size_t)gid;
-            atomicAdd(gp, make_float4(p[0], p[1], p[2], p[9]));
-            atomicAdd(gp + 1, make_float4(p[3], p[4], p[5], p[6]));
-            atomicAdd(reinterpret_cast<float2 *>(gp + 2), make_float2(p[7], p[8]));
+                    for (int kk = 0; kk < NG; kk++) val[kk] = 0.0f;
+                }
+                const int idx = tr_reduce<NG>(val, lane);
+                if (idx < NG) atomicAdd(&part[j][idx], val[0]);
+            }
+        }
+        __syncthreads();
+        // one set of vector atomics per Gaussian of the chunk
+        const int j = threadIdx.x;
+        if (j < cnt && (msk[j] & 0xffu) != 0u) {
+            const float *p = part[j];
+            const bool vs = (msk[j] & 0x100u) != 0u;
+            const int nk = vs ? (CONE ? NV_CONE : NV_PAR) : NG;
+            bool any = false;
+            for (int k = 0; k < nk; k++) any |= p[k] != 0.0f;
+            if (any) {
+                const uint32_t gid = __float_as_uint(sv[j].g2.z);
+                float4 *gp = grad + GRAD_F4 * (size_t)gid;
+                if (vs) {
+                    float o[16];
+                    view_chain<CONE>(g, F, rec, gid, p, o);
+                    atomicAdd(gp, make_float4(o[0], o[1], o[2], o[3]));
+                    atomicAdd(gp + 1, make_float4(o[4], o[5], o[6], o[7]));
+                    atomicAdd(gp + 2, make_float4(o[8], o[9], o[10], o[11]));
+                    atomicAdd(gp + 3, make_float4(o[12], o[13], o[14], o[15]));
+                } else {
+                    atomicAdd(gp, make_float4(p[0], p[1], p[2], p[9]));
+                    atomicAdd(gp + 1, make_float4(p[3], p[4], p[5], p[6]));
+                    atomicAdd(reinterpret_cast<float2 *>(gp + 2), make_float2(p[7], p[8]));
+                }
+            }
         }
         __syncthreads();
     }
@@ -435,10 +799,13 @@ cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const fl
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
     int bs = g.tile_w * g.tile_h;
-    if (g.kind == 1)
-        k_forward<true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
-    else
-        k_forward<false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+    if (g.kind == 1) {
+        if (stats) k_forward<true, true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+        else k_forward<true, false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+    } else {
+        if (stats) k_forward<false, true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+        else k_forward<false, false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -75,6 +75,7 @@ _EXPORTS = {
     "rgrt_prof_reset": ([_VP], ctypes.c_int),
     "rgrt_prof_get": ([_VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "rgrt_stats_enable": ([_VP, ctypes.c_int], ctypes.c_int),
     "rgrt_stats_get": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
 }
@@ -181,6 +182,9 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().rgrt_prof_get(self.h, name.encode(), ctypes.byref(n), ctypes.byref(ms)))
         return int(n.value), float(ms.value)
+
+    def stats_enable(self, on=True):
+        _check(lib().rgrt_stats_enable(self.h, int(on)))
 
     def stats(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -38,6 +38,7 @@ def rg(torch):
 @pytest.fixture(scope="module")
 def ctx(rg):
     c = rg.Context(0)
+    c.stats_enable(True)
     yield c
     c.close()
 
