@@ -375,8 +375,7 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
                                            const float4 *crec, VRec *sv, const float4 *wbox,
                                            int nw, uint32_t *msk)
 {
-    const int i = threadIdx.x;
-    if (i < cnt) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         prep_record<CONE>(g, F, __ldg(gids + base + i), rec, crec, sv[i]);
         const float4 bb = sv[i].bb;
         uint32_t m = 0;
@@ -703,9 +702,9 @@ __global__ void __launch_bounds__(256, 3) k_adjoint(DevGeom g, const float4 *__r
     for (uint32_t base = rg.x; base < rg.y; base += CH) {
         const int cnt = min((uint32_t)CH, rg.y - base);
         prep_chunk<CONE>(g, F, gids, base, cnt, rec, crec, sv, wbox, nw, msk);
-        if (threadIdx.x < cnt) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
 #pragma unroll
-            for (int k = 0; k < NSLOT; k++) part[threadIdx.x][k] = 0.0f;
+            for (int k = 0; k < NSLOT; k++) part[i][k] = 0.0f;
         }
         __syncthreads();
         int nvs, ngen;
@@ -762,8 +761,8 @@ __global__ void __launch_bounds__(256, 3) k_adjoint(DevGeom g, const float4 *__r
         }
         __syncthreads();
         // one set of vector atomics per Gaussian of the chunk
-        const int j = threadIdx.x;
-        if (j < cnt && (msk[j] & 0xffu) != 0u) {
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            if ((msk[j] & 0xffu) == 0u) continue;
             const float *p = part[j];
             const bool vs = (msk[j] & 0x100u) != 0u;
             const int nk = vs ? (CONE ? NV_CONE : NV_PAR) : NG;
