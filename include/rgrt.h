@@ -176,6 +176,33 @@ int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom,
 int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
               const rgrt_adam *hp, int t, float *loss_out, void *stream);
 
+/* ---- allocation-free forward projection ----------------------------- */
+
+/* Maximum scratch, in bytes, of project_forward_noalloc (one static device
+ * array per GPU that loads the library, held until the process exits). */
+#define RGRT_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* project_forward without any memory allocation, for callers that must not
+ * allocate device memory where they project (device memory owned by another
+ * allocator, latency budgets that exclude cudaMalloc/cudaFree and the device
+ * synchronisation they may cause, or fully reserved devices).  The paper has
+ * no counterpart: this is an interface convenience.
+ * All intermediate buffers come from a static device array of
+ * RGRT_NOALLOC_SCRATCH_BYTES; no context is needed.  Arguments as for
+ * gaussians_create + geometry_set + project_forward, but every array (mu3,
+ * logscale3, quat4, rho, out_I) must be device memory of the current device;
+ * desc->angles stays host memory.  Limits: at most 1024 views of 1024 x 1024
+ * pixels, and the whole pipeline must fit the scratch (C1-sized problems of
+ * a few thousand Gaussians fit easily); otherwise RGRT_E_CAPACITY with a
+ * message stating the bytes needed.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and must come before any
+ * stream capture on that device.  Calls share the array: calls whose GPU work
+ * overlaps (unordered streams, several host threads) race.  Reads one 8-byte
+ * count back from the device (a synchronisation of `stream`). */
+int project_forward_noalloc(const rgrt_geom_desc *desc, int64_t n, const float *mu3,
+                            const float *logscale3, const float *quat4, const float *rho,
+                            float *out_I, void *stream);
+
 /* ---- diagnostics ---------------------------------------------------- */
 
 /* Message of the last failed call on this thread ("" if none). */

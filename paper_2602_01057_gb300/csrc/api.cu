@@ -472,6 +472,10 @@ int validate_desc(const rgrt_geom_desc *d)
 
 }  // namespace
 
+// validation and error reporting shared with the allocation-free entry point
+int rgrt::validate_geometry(const rgrt_geom_desc *d) { return validate_desc(d); }
+int rgrt::report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 // ===========================================================================
 // exported API
 // ===========================================================================

@@ -1,0 +1,239 @@
+// project_forward_noalloc: the forward projection with no memory allocation.
+//
+// Some callers cannot allocate device memory at the moment they project:
+// applications whose device memory belongs to another allocator (a framework
+// memory pool that must not be bypassed with cudaMalloc), code on a latency
+// budget that cannot afford cudaMalloc/cudaFree (both may synchronise the
+// whole device), or processes that have already reserved all device memory.
+// For them this entry point runs the same pipeline as project_forward (records,
+// cull, scan, emit, radix sort, tile ranges, integration) with every
+// intermediate buffer carved out of one statically declared device array of
+// RGRT_NOALLOC_SCRATCH_BYTES.  The array exists on every GPU that loads the
+// library, for the life of the process.
+//
+// Host code cannot use the array's name as a device address (on the host it
+// is only a stand-in symbol); the address is fetched with cudaGetSymbolAddress
+// once per device, with that device current, by the first call made on the
+// device -- so that first call must come before any stream capture.  All calls
+// share the array: calls whose GPU work overlaps (unordered streams, several
+// host threads) race and corrupt each other's results.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/rgrt.h"
+#include "rgrt_internal.h"
+
+using namespace rgrt;
+
+namespace {
+
+constexpr size_t SCRATCH_BYTES = (size_t)RGRT_NOALLOC_SCRATCH_BYTES;
+constexpr int MAX_DEVICES = 64;
+constexpr int MAX_VIEWS = 1024, MAX_SIDE = 1024;
+
+static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
+
+std::mutex g_mu;
+void *g_base[MAX_DEVICES];
+
+// device address of g_scratch on the current device (looked up once)
+int scratch_base(int dev, void **out)
+{
+    if (dev < 0 || dev >= MAX_DEVICES) return report_error(RGRT_E_INVAL, "device id out of range");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            char msg[200];
+            snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the static scratch: %s",
+                     cudaGetErrorString(e));
+            return report_error(RGRT_E_CUDA, msg);
+        }
+        g_base[dev] = p;
+    }
+    *out = g_base[dev];
+    return RGRT_OK;
+}
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// bump allocator over the scratch array (256-byte aligned pieces)
+struct Carver {
+    unsigned char *base;
+    size_t used = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        used = off + sizeof(T) * (count ? count : 1);
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+int ceil_log2_u(uint64_t x)
+{
+    int b = 0;
+    while ((1ull << b) < x) b++;
+    return b;
+}
+
+#define NA_CK(expr)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            char m_[256];                                                              \
+            snprintf(m_, sizeof(m_), "%s: %s", #expr, cudaGetErrorString(e_));         \
+            return report_error(RGRT_E_CUDA, m_);                                      \
+        }                                                                              \
+    } while (0)
+
+}  // namespace
+
+extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const float *mu3,
+                                       const float *logscale3, const float *quat4,
+                                       const float *rho, float *out_I, void *stream)
+{
+    if (!d || !out_I) return report_error(RGRT_E_INVAL, "null argument");
+    if (n < 0 || n > (int64_t)0x7fffffff) return report_error(RGRT_E_INVAL, "Gaussian count");
+    if (n > 0 && (!mu3 || !logscale3 || !quat4 || !rho))
+        return report_error(RGRT_E_INVAL, "null parameter array");
+    int rc = validate_geometry(d);
+    if (rc != RGRT_OK) return rc;
+    const int V = d->n_views, H = d->n_rows, W = d->n_cols;
+    if (V > MAX_VIEWS || H > MAX_SIDE || W > MAX_SIDE)
+        return report_error(RGRT_E_CAPACITY,
+                            "project_forward_noalloc handles at most 1024 views of 1024 x 1024 pixels");
+    if (!on_device(out_I) || (n > 0 && !(on_device(mu3) && on_device(logscale3) && on_device(quat4) &&
+                                         on_device(rho))))
+        return report_error(RGRT_E_INVAL, "project_forward_noalloc takes device arrays only");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t R = (int64_t)V * H * W;
+    if (n == 0) {
+        NA_CK(cudaMemsetAsync(out_I, 0, sizeof(float) * (size_t)R, s));
+        return RGRT_OK;
+    }
+    int dev = 0;
+    NA_CK(cudaGetDevice(&dev));
+    void *base = nullptr;
+    rc = scratch_base(dev, &base);
+    if (rc != RGRT_OK) return rc;
+
+    // geometry tables (the same binary32 values geometry_set uploads)
+    float tab[9 * MAX_VIEWS + 2 * MAX_SIDE];
+    const double PI = 3.14159265358979323846;
+    for (int v = 0; v < V; v++) {
+        double eu[3], ev[3] = { 0.0, 0.0, 1.0 }, ew[3];
+        if (d->kind == RGRT_GEOM_PET_RING) {
+            double phi = (PI * (double)v) / (double)V;
+            double c = cos(phi), sn = sin(phi);
+            eu[0] = c; eu[1] = sn; eu[2] = 0.0;
+            ew[0] = sn; ew[1] = -c; ew[2] = 0.0;
+        } else {
+            double th = d->angles[v];
+            double c = cos(th), sn = sin(th);
+            ew[0] = c; ew[1] = sn; ew[2] = 0.0;
+            eu[0] = -sn; eu[1] = c; eu[2] = 0.0;
+        }
+        for (int k = 0; k < 3; k++) {
+            tab[9 * v + k] = (float)eu[k];
+            tab[9 * v + 3 + k] = (float)ev[k];
+            tab[9 * v + 6 + k] = (float)ew[k];
+        }
+    }
+    float *ut = tab + 9 * V, *vt = ut + W;
+    for (int i = 0; i < W; i++) {
+        double k = (double)i - 0.5 * (double)(W - 1);
+        double u;
+        if (d->kind == RGRT_GEOM_PET_RING)
+            u = d->arc_mode == 0 ? k * ((PI * d->radius) / (double)d->n_crystals)
+                                 : d->radius * sin((k * PI) / (double)d->n_crystals);
+        else
+            u = k * d->pitch_u;
+        ut[i] = (float)u;
+    }
+    for (int j = 0; j < H; j++) vt[j] = (float)(((double)j - 0.5 * (double)(H - 1)) * d->pitch_v);
+
+    const int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
+    DevGeom dg{};
+    dg.kind = d->kind == RGRT_GEOM_CT_CONE ? 1 : 0;
+    dg.pet = d->kind == RGRT_GEOM_PET_RING;
+    dg.n_views = V; dg.n_rows = H; dg.n_cols = W;
+    dg.tile_w = tw; dg.tile_h = th;
+    dg.tiles_x = (W + tw - 1) / tw;
+    dg.tiles_y = (H + th - 1) / th;
+    dg.v0 = 0;
+    if (dg.pet) { dg.stride_view = W; dg.stride_row = (long long)V * W; }
+    else { dg.stride_view = (long long)H * W; dg.stride_row = W; }
+    dg.dso = (float)d->dso;
+    dg.dsd = (float)d->dsd;
+    dg.t_a = (float)d->t_a;
+    dg.t_b = (float)d->t_b;
+    dg.radius2 = (float)(d->radius * d->radius);
+
+    // carve the fixed-size part of the scratch
+    Carver cv{ (unsigned char *)base };
+    const size_t ntab = (size_t)9 * V + W + H;
+    float *d_tab = cv.take<float>(ntab);
+    float4 *rec = cv.take<float4>((size_t)REC_F4 * n);
+    float4 *crec = cv.take<float4>((size_t)CREC_F4 * n);
+    const int64_t E = (int64_t)V * n;
+    const uint32_t T = (uint32_t)V * (uint32_t)(dg.tiles_x * dg.tiles_y);
+    uint32_t *cnt = cv.take<uint32_t>((size_t)E);
+    uint32_t *off = cv.take<uint32_t>((size_t)E);
+    uint2 *rect = cv.take<uint2>((size_t)E);
+    unsigned long long *stmp = cv.take<unsigned long long>(scan_tmp_elems(E));
+    unsigned long long *total = cv.take<unsigned long long>(2);
+    uint2 *ranges = cv.take<uint2>(T);
+    if (cv.used > SCRATCH_BYTES) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "project_forward_noalloc: %lld Gaussians x %d views need %zu bytes before binning, "
+                 "over the %zu-byte static scratch",
+                 (long long)n, V, cv.used, SCRATCH_BYTES);
+        return report_error(RGRT_E_CAPACITY, msg);
+    }
+    dg.frames = d_tab;
+    dg.utab = d_tab + 9 * (size_t)V;
+    dg.vtab = dg.utab + W;
+
+    NA_CK(cudaMemcpyAsync(d_tab, tab, sizeof(float) * ntab, cudaMemcpyHostToDevice, s));
+    NA_CK(launch_records(mu3, logscale3, quat4, rho, n, rec, crec, s));
+    NA_CK(launch_cull(dg, V, crec, n, cnt, rect, s));
+    NA_CK(launch_scan(cnt, off, E, total, stmp, s));
+    unsigned long long K = 0;
+    NA_CK(cudaMemcpyAsync(&K, total, sizeof(K), cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaStreamSynchronize(s));
+    // carve the part that depends on the number of (tile, Gaussian) entries
+    uint32_t *keys = cv.take<uint32_t>(K);
+    uint32_t *vals = cv.take<uint32_t>(K);
+    uint32_t *keys_alt = cv.take<uint32_t>(K);
+    uint32_t *vals_alt = cv.take<uint32_t>(K);
+    uint32_t *sort_tmp = cv.take<uint32_t>(K < 0xffffffffull ? sort_tmp_elems((uint32_t)K) : 1);
+    if (K >= 0xffffffffull || cv.used > SCRATCH_BYTES) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "project_forward_noalloc: %llu tile entries need %zu bytes, over the %zu-byte "
+                 "static scratch",
+                 K, cv.used, SCRATCH_BYTES);
+        return report_error(RGRT_E_CAPACITY, msg);
+    }
+    NA_CK(launch_emit(dg, V, n, cnt, off, rect, keys, vals, (uint32_t)K, s));
+    NA_CK(launch_sort(keys, vals, keys_alt, vals_alt, (uint32_t)K, ceil_log2_u(T), sort_tmp, s));
+    // tiles without entries keep the zero range: clear before filling
+    NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)T, s));
+    NA_CK(launch_ranges(keys, (uint32_t)K, ranges, T, s));
+    NA_CK(launch_forward(dg, V, rec, crec, vals, ranges, out_I, nullptr, s));
+    return RGRT_OK;
+}

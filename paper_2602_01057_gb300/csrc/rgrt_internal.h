@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/rgrt.h"
+
 namespace rgrt {
 
 // Geometry as the kernels see it.  kind: 0 = parallel rays (CT parallel and
@@ -44,6 +46,10 @@ struct Stats {
 
 // number of kernels the library has launched (all contexts, all threads)
 void count_launches(int k);
+
+// geometry validation and the thread-local error message of the C ABI
+int validate_geometry(const rgrt_geom_desc *d);
+int report_error(int code, const char *msg);
 
 // ---- launchers (each returns cudaGetLastError of its launch) -------------
 cudaError_t launch_records(const float *mu, const float *ls, const float *q, const float *rho,

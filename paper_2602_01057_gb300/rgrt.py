@@ -65,6 +65,8 @@ _EXPORTS = {
     "project_backward": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "loss_step": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
                   ctypes.c_int),
+    "project_forward_noalloc": ([ctypes.POINTER(GeomDesc), ctypes.c_int64, _VP, _VP, _VP, _VP,
+                                 _VP, _VP], ctypes.c_int),
     "rgrt_last_error": ([], ctypes.c_char_p),
     "rgrt_launch_count": ([], ctypes.c_int64),
     "rgrt_debug_records": ([_VP, _VP, _VP, _VP], ctypes.c_int),
@@ -292,6 +294,17 @@ def project_backward(ctx, gauss, geom, dLdI, g_mu=None, g_ls=None, g_q=None, g_r
     _check(lib().project_backward(ctx.h, gauss.h, geom.h, _ptr(dLdI), _ptr(g_mu), _ptr(g_ls),
                                   _ptr(g_q), _ptr(g_rho), _stream(stream)))
     return g_mu, g_ls, g_q, g_rho
+
+
+def project_forward_noalloc(desc: dict, mu, ls, q, rho, out, stream=None):
+    """Forward projection that allocates no memory (static device scratch);
+    all arrays must be CUDA tensors / device memory."""
+    d, angles = make_desc(desc)
+    n = int(mu.shape[0])
+    _check(lib().project_forward_noalloc(ctypes.byref(d), n, _ptr(mu), _ptr(ls), _ptr(q), _ptr(rho),
+                                         _ptr(out), _stream(stream)))
+    del angles
+    return out
 
 
 def adam_params(lr_mu=2e-4, lr_logscale=5e-3, lr_quat=1e-3, lr_rho=1e-2, beta1=0.9, beta2=0.999,
