@@ -48,8 +48,6 @@ constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
 constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
 constexpr int NG = 10;            // general path: dmu[3], G_P[6], drho
 constexpr int NV_CONE = 12;       // view-space moments, cone beam
-constexpr int NV_PAR = 7;         // view-space moments, parallel rays
-constexpr int NSLOT = 12;
 
 // a Gaussian in the view of the current tile (shared memory)
 // The Q coefficients carry the factor -log2(e)/2 (and, for parallel rays, 1/A)
@@ -671,121 +669,181 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
     val[9] = gw * (SQRT2PI * q.rA * E * phi);
 }
 
-template <bool CONE>
-__global__ void __launch_bounds__(256, 3) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
-                                                    const float4 *__restrict__ crec,
-                                                    const uint32_t *__restrict__ gids,
-                                                    const uint2 *__restrict__ ranges,
-                                                    const float *__restrict__ dLdI,
-                                                    float4 *__restrict__ grad)
+// Adjoint, one Gaussian per thread.  A CTA takes a tile: it stages the
+// tile's dL/dI (times |d~| for cone beam) and pixel coordinates in shared
+// memory, then every thread walks the tile's rays for one Gaussian of the
+// list at a time (all lanes of a warp read the same ray: broadcasts), keeping
+// that Gaussian's view-space moments in registers -- no cross-thread
+// reduction -- and finishes with the parameter chain and one set of vector
+// atomics per (Gaussian, tile).  Rows of the tile that miss every box of the
+// warp's Gaussians are skipped; within a row the Q and A quadratics are
+// evaluated in Horner form in du with the dv terms hoisted.
+template <bool CONE, int TW>
+__global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
+                                                 const float4 *__restrict__ crec,
+                                                 const uint32_t *__restrict__ gids,
+                                                 const uint2 *__restrict__ ranges,
+                                                 const float *__restrict__ dLdI,
+                                                 float4 *__restrict__ grad)
 {
-    __shared__ VRec sv[CH];
-    __shared__ ChunkLists lists;
-    __shared__ uint32_t msk[CH];
-    __shared__ float part[CH][NSLOT];   // per record: moments summed over the tile's warps
-    __shared__ float4 wbox[8];
+    __shared__ float sgl[256];   // dL/dI |d~| of the tile's rays, row-major (0 outside the detector)
+    __shared__ float su[32], svr[32];
     __shared__ float Fs[9];
-    const TileCtx c = tile_ctx(g);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
-    warp_box(c, wbox);
+    const int T = g.tiles_x * g.tiles_y;
+    const int vl = blockIdx.x / T;
+    const int tin = blockIdx.x - vl * T;
+    const int ty = tin / g.tiles_x, tx = tin - ty * g.tiles_x;
+    const int view = g.v0 + vl;
+    const int TH = g.tile_h;
+    const int c0 = tx * TW, r0 = ty * TH;
+    if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)view + threadIdx.x);
+    if (threadIdx.x < TW) su[threadIdx.x] = __ldg(g.utab + min(c0 + (int)threadIdx.x, g.n_cols - 1));
+    if (threadIdx.x < TH) svr[threadIdx.x] = __ldg(g.vtab + min(r0 + (int)threadIdx.x, g.n_rows - 1));
+    for (int r = threadIdx.x; r < TW * TH; r += blockDim.x) {
+        const int col = c0 + r % TW, row = r0 + r / TW;
+        float gl = 0.0f;
+        if (col < g.n_cols && row < g.n_rows) {
+            const long long idx = (long long)view * g.stride_view + (long long)row * g.stride_row + col;
+            gl = __ldg(dLdI + idx);
+            if (CONE) {
+                const float u = __ldg(g.utab + col), v = __ldg(g.vtab + row);
+                gl *= sqrtf(u * u + v * v + g.dsd * g.dsd);
+            }
+        }
+        sgl[r] = gl;
+    }
     __syncthreads();
     float F[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) F[i] = Fs[i];
-    const float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
-    const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
-    const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd) : 1.0f;
-    const float gw = c.valid ? __ldg(dLdI + c.out_idx) : 0.0f;
-    const float gL = gw * L;
     const uint2 rg = ranges[blockIdx.x];
-    for (uint32_t base = rg.x; base < rg.y; base += CH) {
-        const int cnt = min((uint32_t)CH, rg.y - base);
-        prep_chunk<CONE>(g, F, gids, base, cnt, rec, crec, sv, wbox, nw, msk);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    // every lane of a warp runs the same number of rounds (inactive lanes idle)
+    const uint32_t n = rg.y - rg.x;
+    const uint32_t rounds = (n + blockDim.x - 1) / blockDim.x;
+    for (uint32_t rd = 0; rd < rounds; rd++) {
+        const uint32_t k = rg.x + rd * blockDim.x + threadIdx.x;
+        const bool active = k < rg.y;
+        VRec r;
+        uint32_t gid = 0;
+        if (active) {
+            gid = __ldg(gids + k);
+            prep_record<CONE>(g, F, gid, rec, crec, r);
+        } else {
+            r.bb = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+            r.g2 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+        }
+        const float4 bb = r.bb;
+        const bool vs = r.g2.w != 0.0f;
+        float o[16];
+        bool any = false;
+        if (__any_sync(0xffffffffu, active && vs)) {
+            // view-space moments (see view_chain for their meaning)
+            const float u0 = r.c0.x, v0 = r.c0.y, kMuu = r.c0.z, kMuv2 = r.c0.w, kMvv = r.c1.x;
+            float s[NV_CONE];
 #pragma unroll
-            for (int k = 0; k < NSLOT; k++) part[i][k] = 0.0f;
-        }
-        __syncthreads();
-        int nvs, ngen;
-        build_lists(cnt, msk, lists, w, lane, nvs, ngen);
-        for (int k = 0; k < nvs; k++) {
-            // view-space path: moments of dL/dQ and dL/dA over the rays
-            const int j = lists.vs[w][k];
-            const float4 c0 = sv[j].c0, c1 = sv[j].c1, c2 = sv[j].c2;
-            const float du = u - c0.x, dv = v - c0.y;
-            const float du2 = du * du, dudv = du * dv, dv2 = dv * dv;
-            const float q = c0.z * du2 + c0.w * dudv + c1.x * dv2;
-            float rA, iA;
-            if (CONE) {
-                const float A = c1.y + c1.z * du + c1.w * dv + c2.x * du2 + c2.y * dudv + c2.z * dv2;
-                rA = rsqrt_approx(A);
-                iA = rA * rA;
-            } else {
-                iA = c1.y;
-                rA = c1.z;
-            }
-            const float arg = CONE ? q * iA : q;
-            const float m = arg * M_PER_ARG;
-            // wv = dL/dI |d~| A^-1/2 e^{-m/2}; dL/dQ = -alpha wv/(2A), dL/dA = alpha wv (m-1)/(2A)
-            const float wv = arg >= CUT_ARG ? gL * rA * ex2_approx(arg) : 0.0f;
-            const float h = 0.5f * wv * iA;
-            const float gQ = -h, gA = h * (m - 1.0f);
-            if (CONE) {
-                float val[NV_CONE] = { gQ * du, gQ * dv, gQ * du2, gQ * dudv, gQ * dv2, gA,
-                                       gA * du, gA * dv, gA * du2, gA * dudv, gA * dv2, wv };
-                const int idx = tr_reduce<NV_CONE>(val, lane);
-                if (idx < NV_CONE) atomicAdd(&part[j][idx], val[0]);
-            } else {
-                float val[NV_PAR] = { gQ * du, gQ * dv, gQ * du2, gQ * dudv, gQ * dv2, gA, wv };
-                const int idx = tr_reduce<NV_PAR>(val, lane);
-                if (idx < NV_PAR) atomicAdd(&part[j][idx], val[0]);
-            }
-        }
-        if (ngen > 0) {
-            const Ray ray = make_ray<CONE>(g, F, u, v);
-            for (int k = 0; k < ngen; k++) {
-                const int j = lists.gen[w][k];
-                PairGeo q;
-                pair_geo(ray, sv[j], q);
-                float val[NG];
-                if (q.m <= PAIR_CUT2 && gw != 0.0f) {
-                    general_grad(ray, q, sv[j].g0.w, gw, val);
+            for (int q = 0; q < NV_CONE; q++) s[q] = 0.0f;
+            for (int j = 0; j < TH; j++) {
+                const float vj = svr[j];
+                const bool rowin = active && vs && vj >= bb.z && vj <= bb.w;
+                if (!__any_sync(0xffffffffu, rowin)) continue;
+                if (!rowin) continue;
+                const float dv = vj - v0, dv2 = dv * dv;
+                const float a1 = kMuv2 * dv, a0 = kMvv * dv2;
+                float b2 = 0.0f, b1 = 0.0f, b0 = 0.0f, iAc = 0.0f, rAc = 0.0f;
+                if (CONE) {
+                    b2 = r.c2.x;
+                    b1 = r.c1.z + r.c2.y * dv;
+                    b0 = r.c1.y + r.c1.w * dv + r.c2.z * dv2;
                 } else {
+                    iAc = r.c1.y;
+                    rAc = r.c1.z;
+                }
+                float H0 = 0.0f, H1 = 0.0f, H2 = 0.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, Sw = 0.0f;
+                const float *gl_row = sgl + j * TW;
 #pragma unroll
-                    for (int kk = 0; kk < NG; kk++) val[kk] = 0.0f;
+                for (int i = 0; i < TW; i++) {
+                    const float du = su[i] - u0;
+                    const float qv = (kMuu * du + a1) * du + a0;
+                    float rA, iA, arg;
+                    if (CONE) {
+                        const float A = (b2 * du + b1) * du + b0;
+                        rA = rsqrt_approx(A);
+                        iA = rA * rA;
+                        arg = qv * iA;
+                    } else {
+                        rA = rAc;
+                        iA = iAc;
+                        arg = qv;
+                    }
+                    const float wv = arg >= CUT_ARG ? gl_row[i] * rA * ex2_approx(arg) : 0.0f;
+                    const float h = 0.5f * wv * iA;
+                    const float gA = h * (arg * M_PER_ARG - 1.0f);
+                    const float hd = h * du, gd = gA * du;
+                    H0 += h; H1 += hd; H2 += hd * du;
+                    G0 += gA; G1 += gd; G2 += gd * du;
+                    Sw += wv;
                 }
-                const int idx = tr_reduce<NG>(val, lane);
-                if (idx < NG) atomicAdd(&part[j][idx], val[0]);
+                // dL/dQ = -h:  SQ_x = -sum h x ;  SA_x = sum gA x
+                s[0] -= H1;
+                s[1] -= H0 * dv;
+                s[2] -= H2;
+                s[3] -= H1 * dv;
+                s[4] -= H0 * dv2;
+                s[5] += G0;
+                s[6] += G1;
+                s[7] += G0 * dv;
+                s[8] += G2;
+                s[9] += G1 * dv;
+                s[10] += G0 * dv2;
+                s[11] += Sw;
+            }
+            if (active && vs) {
+                if (!CONE) s[6] = s[11];   // parallel layout: [SQ.. (5), SA, Sw]
+#pragma unroll
+                for (int q = 0; q < NV_CONE; q++) any |= s[q] != 0.0f;
+                if (any) view_chain<CONE>(g, F, rec, gid, s, o);
             }
         }
-        __syncthreads();
-        // one set of vector atomics per Gaussian of the chunk
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            if ((msk[j] & 0xffu) == 0u) continue;
-            const float *p = part[j];
-            const bool vs = (msk[j] & 0x100u) != 0u;
-            const int nk = vs ? (CONE ? NV_CONE : NV_PAR) : NG;
-            bool any = false;
-            for (int k = 0; k < nk; k++) any |= p[k] != 0.0f;
-            if (any) {
-                const uint32_t gid = __float_as_uint(sv[j].g2.z);
-                float4 *gp = grad + GRAD_F4 * (size_t)gid;
-                if (vs) {
-                    float o[16];
-                    view_chain<CONE>(g, F, rec, gid, p, o);
-                    atomicAdd(gp, make_float4(o[0], o[1], o[2], o[3]));
-                    atomicAdd(gp + 1, make_float4(o[4], o[5], o[6], o[7]));
-                    atomicAdd(gp + 2, make_float4(o[8], o[9], o[10], o[11]));
-                    atomicAdd(gp + 3, make_float4(o[12], o[13], o[14], o[15]));
-                } else {
-                    atomicAdd(gp, make_float4(p[0], p[1], p[2], p[9]));
-                    atomicAdd(gp + 1, make_float4(p[3], p[4], p[5], p[6]));
-                    atomicAdd(reinterpret_cast<float2 *>(gp + 2), make_float2(p[7], p[8]));
+        if (__any_sync(0xffffffffu, active && !vs)) {
+            float val[NG];
+#pragma unroll
+            for (int q = 0; q < NG; q++) val[q] = 0.0f;
+            if (active && !vs) {
+                for (int j = 0; j < TH; j++) {
+                    const float vj = svr[j];
+                    if (!(vj >= bb.z && vj <= bb.w)) continue;
+                    for (int i = 0; i < TW; i++) {
+                        const float gw0 = sgl[j * TW + i];
+                        if (gw0 == 0.0f) continue;
+                        const float u = su[i];
+                        const Ray ray = make_ray<CONE>(g, F, u, vj);
+                        PairGeo q;
+                        pair_geo(ray, r, q);
+                        if (!(q.m <= PAIR_CUT2)) continue;
+                        // sgl holds dL/dI |d~|; the general form wants dL/dI
+                        const float gw = CONE ? gw0 * rsqrtf(u * u + vj * vj + g.dsd * g.dsd) : gw0;
+                        float pv[NG];
+                        general_grad(ray, q, r.g0.w, gw, pv);
+#pragma unroll
+                        for (int qq = 0; qq < NG; qq++) val[qq] += pv[qq];
+                    }
                 }
+#pragma unroll
+                for (int q = 0; q < NG; q++) any |= val[q] != 0.0f;
+                o[0] = val[0]; o[1] = val[1]; o[2] = val[2]; o[3] = val[9];
+                o[4] = val[3]; o[5] = val[4]; o[6] = val[5]; o[7] = val[6];
+                o[8] = val[7]; o[9] = val[8];
+#pragma unroll
+                for (int q = 10; q < 16; q++) o[q] = 0.0f;
             }
         }
-        __syncthreads();
+        if (active && any) {
+            float4 *gp = grad + GRAD_F4 * (size_t)gid;
+            atomicAdd(gp, make_float4(o[0], o[1], o[2], o[3]));
+            atomicAdd(gp + 1, make_float4(o[4], o[5], o[6], o[7]));
+            atomicAdd(gp + 2, make_float4(o[8], o[9], o[10], o[11]));
+            if (vs) atomicAdd(gp + 3, make_float4(o[12], o[13], o[14], o[15]));
+        }
     }
 }
 
@@ -815,11 +873,18 @@ cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const fl
 {
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
-    int bs = g.tile_w * g.tile_h;
-    if (g.kind == 1)
-        k_adjoint<true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
-    else
-        k_adjoint<false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
+    const int bs = 128;
+#define RGRT_ADJ(CONE, TW) k_adjoint<CONE, TW><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
+    if (g.kind == 1) {
+        if (g.tile_w == 8) RGRT_ADJ(true, 8);
+        else if (g.tile_w == 16) RGRT_ADJ(true, 16);
+        else RGRT_ADJ(true, 32);
+    } else {
+        if (g.tile_w == 8) RGRT_ADJ(false, 8);
+        else if (g.tile_w == 16) RGRT_ADJ(false, 16);
+        else RGRT_ADJ(false, 32);
+    }
+#undef RGRT_ADJ
     count_launches(1);
     return cudaGetLastError();
 }
