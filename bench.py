@@ -39,6 +39,11 @@ SM_MAX_MHZ = 2070.0
 # adjoint; see the kernel notes for the count.
 FLOP_PER_PAIR_FWD = 78
 FLOP_PER_PAIR_ADJ = 180
+# DRAM bytes (read + write) of one launch of the dominant kernels on the
+# cone-beam CT workload, from the ncu captures summarised in
+# profiles/k_adjoint_c2_cone.md and profiles/k_forward_c2_cone.md; None once a
+# kernel has changed since its capture.
+TRAFFIC_C2 = {"k_adjoint": 272.782592e6 + 4.123136e6, "k_forward": 221.411328e6 + 36.705536e6}
 WORKLOADS = {
     "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
           "180 views over 360 deg, 256x256 detector, source-origin 1000 mm, source-detector 1500 mm",
@@ -319,8 +324,9 @@ def run_ours(args):
     flop = pairs * (FLOP_PER_PAIR_ADJ if dom == "k_adjoint" else FLOP_PER_PAIR_FWD)
     achieved = flop / (per / 1e3) / 1e12
     peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = TRAFFIC_C2.get(dom) if args.workload == "c2" else None
     roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=None, kernel=dom, kernel_ms=per,
+                traffic=traffic, kernel=dom, kernel_ms=per,
                 note="FP32 FLOP of the kept pairs (m <= 9) / kernel time; peak = 152 SMs x 128 "
                      "FP32 lanes x 2 (FMA) x 2070 MHz")
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
