@@ -217,9 +217,11 @@ int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *
 
 /* Tile lists of views [v0, v1): n_keys_out = number of (tile, Gaussian)
  * entries; tile_start[n_tiles + 1] (CSR offsets, tile id = (view - v0) *
- * tiles_per_view + ty * tiles_x + tx) and gid[cap] (Gaussian ids, ascending
- * within each tile).  Host or device outputs; RGRT_E_CAPACITY if cap is
- * smaller than the number of entries (n_keys_out is still set). */
+ * tiles_per_view + ty * tiles_x + tx) and gid[cap] (Gaussian ids; within a
+ * tile ordered by the position code of the Gaussian's pixel box in the tile
+ * -- row bucket, column bucket, 4 bits each, bucket = (lo + hi) * 8 / tile
+ * size -- then by ascending id).  Host or device outputs; RGRT_E_CAPACITY if
+ * cap is smaller than the number of entries (n_keys_out is still set). */
 int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
                           int v1, int64_t *n_keys_out, uint32_t *tile_start, uint32_t *gid,
                           int64_t cap, void *stream);

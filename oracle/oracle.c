@@ -726,10 +726,10 @@ void or_records_fp32(int64_t n, const float *ls, const float *q, float *sig6)
 #define OG32_CULL_K2 9.0625f
 
 /*
- * FP32 cull of every (view, Gaussian): tile rectangle (tx0, tx1, ty0, ty1) of
- * the detector pixels whose centre lies inside the bounding box of the
- * projected K-sigma ellipsoid; count = number of tiles (0 when empty).
- * Output index = view * n + gid.
+ * FP32 cull of every (view, Gaussian): pixel box (i0, i1, j0, j1) of the
+ * detector pixels whose centre lies inside the bounding box of the projected
+ * K-sigma ellipsoid, and count = number of tiles of tile_w x tile_h pixels it
+ * touches (0 and a box of -1 when empty).  Output index = view * n + gid.
  */
 void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls, const float *q,
                   int tile_w, int tile_h, int32_t *rect, int32_t *count)
@@ -771,7 +771,7 @@ void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls,
                 rect[4 * x] = rect[4 * x + 1] = rect[4 * x + 2] = rect[4 * x + 3] = -1;
             } else {
                 int tx0 = i0 / tile_w, tx1 = i1 / tile_w, ty0 = j0 / tile_h, ty1 = j1 / tile_h;
-                rect[4 * x] = tx0; rect[4 * x + 1] = tx1; rect[4 * x + 2] = ty0; rect[4 * x + 3] = ty1;
+                rect[4 * x] = i0; rect[4 * x + 1] = i1; rect[4 * x + 2] = j0; rect[4 * x + 3] = j1;
                 count[x] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
             }
         }

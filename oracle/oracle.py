@@ -233,43 +233,49 @@ def records_fp32(ls, q):
 
 
 def cull_fp32(geom, G, tile_w, tile_h):
-    """(rect[V, n, 4] = tx0, tx1, ty0, ty1; count[V, n]) of the FP32 cull."""
+    """FP32 cull: (pixel box[V, n, 4] = i0, i1, j0, j1; tile rectangle[V, n, 4]
+    = tx0, tx1, ty0, ty1; tile count[V, n])."""
     g = _geom(geom)
     n, mu, ls, q, rho = _gauss(G)
     V = int(g.desc["n_views"])
-    rect = np.zeros((V, n, 4), dtype=np.int32)
+    box = np.zeros((V, n, 4), dtype=np.int32)
     cnt = np.zeros((V, n), dtype=np.int32)
     lib().or_cull_fp32(g.ref, ctypes.c_int64(n), _p(mu), _p(ls), _p(q),
-                       ctypes.c_int(tile_w), ctypes.c_int(tile_h), _p(rect), _p(cnt))
-    return rect, cnt
+                       ctypes.c_int(tile_w), ctypes.c_int(tile_h), _p(box), _p(cnt))
+    rect = np.where(box >= 0, box // np.array([tile_w, tile_w, tile_h, tile_h]), -1).astype(np.int32)
+    return box, rect, cnt
 
 
 def tile_lists_fp32(geom, G, tile_w, tile_h):
     """Per-tile Gaussian lists implied by the FP32 cull, in CSR form:
-    (start[T+1], gid[K]); tile id = view * tiles_per_view + ty * tiles_x + tx,
-    gids ascending within each tile."""
+    (start[T+1], gid[K]); tile id = view * tiles_per_view + ty * tiles_x + tx.
+    Within a tile, entries are ordered by a position code and then by id: the
+    code is (4-bit row bucket, 4-bit column bucket) of the centre of the
+    Gaussian's pixel box clipped to the tile, bucket = (lo + hi) * 8 // size."""
     desc = geom.desc if isinstance(geom, Geometry) else geom
-    rect, cnt = cull_fp32(geom, G, tile_w, tile_h)
+    box, rect, cnt = cull_fp32(geom, G, tile_w, tile_h)
     V, n = cnt.shape
     tx_n = (int(desc["n_cols"]) + tile_w - 1) // tile_w
     ty_n = (int(desc["n_rows"]) + tile_h - 1) // tile_h
     T = V * tx_n * ty_n
-    tiles, gids = [], []
+    tiles, codes, gids = [], [], []
     for v in range(V):
-        ks = np.nonzero(cnt[v])[0]
-        for k in ks:
+        for k in np.nonzero(cnt[v])[0]:
+            i0, i1, j0, j1 = box[v, k]
             tx0, tx1, ty0, ty1 = rect[v, k]
-            tys, txs = np.meshgrid(np.arange(ty0, ty1 + 1), np.arange(tx0, tx1 + 1), indexing="ij")
-            t = v * tx_n * ty_n + tys.ravel() * tx_n + txs.ravel()
-            tiles.append(t)
-            gids.append(np.full(t.size, k, dtype=np.int64))
-    if tiles:
-        tiles = np.concatenate(tiles)
-        gids = np.concatenate(gids)
-    else:
-        tiles = np.zeros(0, dtype=np.int64)
-        gids = np.zeros(0, dtype=np.int64)
-    order = np.lexsort((gids, tiles))
+            for ty in range(ty0, ty1 + 1):
+                jl, jh = max(j0 - ty * tile_h, 0), min(j1 - ty * tile_h, tile_h - 1)
+                rb = ((jl + jh) * 8) // tile_h
+                for tx in range(tx0, tx1 + 1):
+                    il, ih = max(i0 - tx * tile_w, 0), min(i1 - tx * tile_w, tile_w - 1)
+                    cb = ((il + ih) * 8) // tile_w
+                    tiles.append(v * tx_n * ty_n + ty * tx_n + tx)
+                    codes.append(rb * 16 + cb)
+                    gids.append(k)
+    tiles = np.asarray(tiles, dtype=np.int64)
+    codes = np.asarray(codes, dtype=np.int64)
+    gids = np.asarray(gids, dtype=np.int64)
+    order = np.lexsort((gids, codes, tiles))
     tiles, gids = tiles[order], gids[order]
     start = np.zeros(T + 1, dtype=np.int64)
     np.add.at(start, tiles + 1, 1)

@@ -260,6 +260,8 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     DevGeom dg = geom->dg;
     dg.v0 = v0;
     const uint32_t T = (uint32_t)nv * (uint32_t)geom->tiles_per_view;
+    if (T >= (1u << 24))  // tile ids share the key with an 8-bit position code
+        return fail(RGRT_E_CAPACITY, "views %d..%d hold %u tiles (2^24 at most)", v0, v0 + nv, T);
     TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)E));
     TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)E));
     TRY(ensure(ctx, ctx->rect, sizeof(uint2) * (size_t)E));
@@ -301,7 +303,7 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     {
         PROF("radix_sort");
         CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
-                       (uint32_t)K, ceil_log2(T), (uint32_t *)ctx->sort_tmp.p, s));
+                       (uint32_t)K, ceil_log2(T) + 8, (uint32_t *)ctx->sort_tmp.p, s));
     }
     {
         PROF("k_ranges");

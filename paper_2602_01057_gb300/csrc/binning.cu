@@ -1,8 +1,9 @@
 // Binning (a2, second half): exclusive scan of per-(view, Gaussian) tile
-// counts, emission of (tile, Gaussian) keys, a stable LSD radix sort on the
-// tile bits, and per-tile ranges.  Keys are emitted in (view, Gaussian) order
-// and the sort is stable, so each tile's list ends up in ascending Gaussian
-// order: the lists are canonical and the per-ray sums deterministic.
+// counts, emission of (tile, position, Gaussian) keys, a stable LSD radix
+// sort on the key bits, and per-tile ranges.  Keys are emitted in (view,
+// Gaussian) order and the sort is stable, so each tile's list is ordered by
+// footprint position and then by Gaussian id: the lists are canonical and the
+// per-ray sums deterministic.
 #include "rgrt_internal.h"
 
 namespace rgrt {
@@ -129,7 +130,11 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restric
     }
 }
 
-// one thread per (view of the chunk, Gaussian): write its tiles' keys
+// one thread per (view of the chunk, Gaussian): write its tiles' keys.
+// key = tile id << 8 | position code, the code being the 4-bit row and
+// column buckets of the centre of the Gaussian's pixel box within the tile:
+// sorting by it orders each tile's list by footprint position (Gaussians of
+// the same position keep ascending ids, the sort being stable).
 __global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict__ cnt,
                        const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
                        uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t cap)
@@ -142,15 +147,22 @@ __global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict_
     int vl = (int)(idx / n);
     uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
     uint2 r = rect[idx];
-    uint32_t tx0 = r.x & 0xffffu, tx1 = r.x >> 16, ty0 = r.y & 0xffffu, ty1 = r.y >> 16;
+    const int i0 = r.x & 0xffff, i1 = r.x >> 16, j0 = r.y & 0xffff, j1 = r.y >> 16;
+    const int tw = g.tile_w, th = g.tile_h;
+    const int tx0 = i0 / tw, tx1 = i1 / tw, ty0 = j0 / th, ty1 = j1 / th;
     uint32_t o = off[idx];
     uint32_t tbase = (uint32_t)vl * (uint32_t)(g.tiles_x * g.tiles_y);
-    for (uint32_t ty = ty0; ty <= ty1; ty++)
-        for (uint32_t tx = tx0; tx <= tx1; tx++) {
-            keys[o] = tbase + ty * (uint32_t)g.tiles_x + tx;
+    for (int ty = ty0; ty <= ty1; ty++) {
+        const int jl = max(j0 - ty * th, 0), jh = min(j1 - ty * th, th - 1);
+        const uint32_t rb = (uint32_t)(((jl + jh) * 8) / th);
+        for (int tx = tx0; tx <= tx1; tx++) {
+            const int il = max(i0 - tx * tw, 0), ih = min(i1 - tx * tw, tw - 1);
+            const uint32_t cb = (uint32_t)(((il + ih) * 8) / tw);
+            keys[o] = ((tbase + (uint32_t)ty * (uint32_t)g.tiles_x + (uint32_t)tx) << 8) | (rb << 4) | cb;
             vals[o] = k;
             o++;
         }
+    }
 }
 
 constexpr int SORT_BS = 256;     // one thread per digit value
@@ -221,10 +233,10 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n, uint2 *_
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t k = keys[i];
-    if (k >= n_tiles) return;  // never taken: emitted tile ids are < n_tiles
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    uint32_t k = keys[i] >> 8;   // tile id (the low byte is the position code)
+    if (k >= n_tiles) return;    // never taken: emitted tile ids are < n_tiles
+    if (i == 0 || (keys[i - 1] >> 8) != k) ranges[k].x = i;
+    if (i == n - 1 || (keys[i + 1] >> 8) != k) ranges[k].y = i + 1;
 }
 
 }  // namespace

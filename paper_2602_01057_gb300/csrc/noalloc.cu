@@ -196,6 +196,8 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
     unsigned long long *stmp = cv.take<unsigned long long>(scan_tmp_elems(E));
     unsigned long long *total = cv.take<unsigned long long>(2);
     uint2 *ranges = cv.take<uint2>(T);
+    if (T >= (1u << 24))
+        return report_error(RGRT_E_CAPACITY, "project_forward_noalloc: more than 2^24 tiles");
     if (cv.used > SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof(msg),
@@ -230,7 +232,7 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
         return report_error(RGRT_E_CAPACITY, msg);
     }
     NA_CK(launch_emit(dg, V, n, cnt, off, rect, keys, vals, (uint32_t)K, s));
-    NA_CK(launch_sort(keys, vals, keys_alt, vals_alt, (uint32_t)K, ceil_log2_u(T), sort_tmp, s));
+    NA_CK(launch_sort(keys, vals, keys_alt, vals_alt, (uint32_t)K, ceil_log2_u(T) + 8, sort_tmp, s));
     // tiles without entries keep the zero range: clear before filling
     NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)T, s));
     NA_CK(launch_ranges(keys, (uint32_t)K, ranges, T, s));

@@ -675,9 +675,11 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
 // list at a time (all lanes of a warp read the same ray: broadcasts), keeping
 // that Gaussian's view-space moments in registers -- no cross-thread
 // reduction -- and finishes with the parameter chain and one set of vector
-// atomics per (Gaussian, tile).  Rows of the tile that miss every box of the
-// warp's Gaussians are skipped; within a row the Q and A quadratics are
-// evaluated in Horner form in du with the dv terms hoisted.
+// atomics per (Gaussian, tile).  The tile list is ordered by footprint
+// position, so the 32 Gaussians of a warp sit close together: rows and
+// 8-column groups that none of their boxes touches are skipped.  Within a row
+// the Q and A quadratics are evaluated in Horner form in du with the dv terms
+// hoisted.
 template <bool CONE, int TW>
 __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
                                                  const float4 *__restrict__ crec,
@@ -734,6 +736,23 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
         }
         const float4 bb = r.bb;
         const bool vs = r.g2.w != 0.0f;
+        // the Gaussian's box in tile pixels (rows jlo..jhi, columns ilo..ihi)
+        int jlo = TH, jhi = -1, ilo = TW, ihi = -1;
+        for (int j = 0; j < TH; j++) {
+            const bool in = svr[j] >= bb.z && svr[j] <= bb.w;
+            jlo = in && j < jlo ? j : jlo;
+            jhi = in ? j : jhi;
+        }
+#pragma unroll
+        for (int i = 0; i < TW; i++) {
+            const bool in = su[i] >= bb.x && su[i] <= bb.y;
+            ilo = in && i < ilo ? i : ilo;
+            ihi = in ? i : ihi;
+        }
+        // 8-column groups of the tile the box touches
+        uint32_t groups = 0;
+#pragma unroll
+        for (int c8 = 0; c8 < TW / 8; c8++) groups |= (uint32_t)(ilo <= 8 * c8 + 7 && ihi >= 8 * c8) << c8;
         float o[16];
         bool any = false;
         if (__any_sync(0xffffffffu, active && vs)) {
@@ -744,9 +763,12 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
             for (int q = 0; q < NV_CONE; q++) s[q] = 0.0f;
             for (int j = 0; j < TH; j++) {
                 const float vj = svr[j];
-                const bool rowin = active && vs && vj >= bb.z && vj <= bb.w;
-                if (!__any_sync(0xffffffffu, rowin)) continue;
-                if (!rowin) continue;
+                const bool rowin = active && vs && j >= jlo && j <= jhi;
+                // rows and 8-column groups that no Gaussian of the warp touches
+                // are skipped (the lists are ordered by footprint position, so
+                // a warp's Gaussians sit close together in the tile)
+                const uint32_t need = __reduce_or_sync(0xffffffffu, rowin ? groups : 0u);
+                if (need == 0u || !rowin) continue;
                 const float dv = vj - v0, dv2 = dv * dv;
                 const float a1 = kMuv2 * dv, a0 = kMvv * dv2;
                 float b2 = 0.0f, b1 = 0.0f, b0 = 0.0f, iAc = 0.0f, rAc = 0.0f;
@@ -761,7 +783,10 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
                 float H0 = 0.0f, H1 = 0.0f, H2 = 0.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, Sw = 0.0f;
                 const float *gl_row = sgl + j * TW;
 #pragma unroll
-                for (int i = 0; i < TW; i++) {
+                for (int c8 = 0; c8 < TW / 8; c8++) {
+                if (!((need >> c8) & 1u)) continue;
+#pragma unroll
+                for (int i = 8 * c8; i < 8 * c8 + 8; i++) {
                     const float du = su[i] - u0;
                     const float qv = (kMuu * du + a1) * du + a0;
                     float rA, iA, arg;
@@ -782,6 +807,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
                     H0 += h; H1 += hd; H2 += hd * du;
                     G0 += gA; G1 += gd; G2 += gd * du;
                     Sw += wv;
+                }
                 }
                 // dL/dQ = -h:  SQ_x = -sum h x ;  SA_x = sum gA x
                 s[0] -= H1;
@@ -809,10 +835,9 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
 #pragma unroll
             for (int q = 0; q < NG; q++) val[q] = 0.0f;
             if (active && !vs) {
-                for (int j = 0; j < TH; j++) {
+                for (int j = jlo; j <= jhi; j++) {
                     const float vj = svr[j];
-                    if (!(vj >= bb.z && vj <= bb.w)) continue;
-                    for (int i = 0; i < TW; i++) {
+                    for (int i = ilo; i <= ihi; i++) {
                         const float gw0 = sgl[j * TW + i];
                         if (gw0 == 0.0f) continue;
                         const float u = su[i];

@@ -184,7 +184,8 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
     } else {
         unsigned tx0 = i0 / g.tile_w, tx1 = i1 / g.tile_w, ty0 = j0 / g.tile_h, ty1 = j1 / g.tile_h;
         cnt[idx] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-        rect[idx] = make_uint2(tx0 | (tx1 << 16), ty0 | (ty1 << 16));
+        // pixel box (the tiles follow from it)
+        rect[idx] = make_uint2((unsigned)i0 | ((unsigned)i1 << 16), (unsigned)j0 | ((unsigned)j1 << 16));
     }
 }
 

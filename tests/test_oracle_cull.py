@@ -63,7 +63,7 @@ def test_cull_is_conservative(oracle, kind):
         G = synth.gaussians_uniform(25, 63, half_box=30.0, log_sigma=math.log(3.0))
         G["mu"][:, 2] *= 0.2
     m = _all_pairs_m(oracle, g, G)
-    rect, cnt = oracle.cull_fp32(g, G, tw, th)
+    box, rect, cnt = oracle.cull_fp32(g, G, tw, th)
     V, H, W = g["n_views"], g["n_rows"], g["n_cols"]
     kept = 0
     for k in range(G["mu"].shape[0]):
@@ -88,7 +88,7 @@ def test_cull_tiles_not_wider_than_needed(oracle):
     corner tiles hold a pixel within that box (checked in FP64, away from ties)."""
     g = synth.geom_cone(4, 64, 64, 0.04, 0.04, 3.0, 4.5)
     G = synth.gaussians_uniform(200, 64, half_box=0.9, log_sigma=math.log(0.08))
-    rect, cnt = oracle.cull_fp32(g, G, 8, 8)
+    box, rect, cnt = oracle.cull_fp32(g, G, 8, 8)
     assert (cnt > 0).mean() > 0.9
     # rectangle sizes bounded by the projected 3-sigma extent plus one tile
     sig, _ = oracle.cov(G["ls"], G["q"])
