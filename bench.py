@@ -43,13 +43,16 @@ FLOP_PER_PAIR_ADJ = 180
 # cone-beam CT workload, from the ncu captures summarised in
 # profiles/k_adjoint_c2_cone.md and profiles/k_forward_c2_cone.md; None once a
 # kernel has changed since its capture.
-TRAFFIC_C2 = {"k_adjoint": 272.782592e6 + 4.123136e6, "k_forward": 221.411328e6 + 36.705536e6}
+TRAFFIC_C2 = {"k_adjoint": 272.897792e6 + 4.044800e6, "k_forward": None}
 WORKLOADS = {
     "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
           "180 views over 360 deg, 256x256 detector, source-origin 1000 mm, source-detector 1500 mm",
     "c3": "PET fwd+bwd (Poisson NLL + Adam): 200,000 Gaussians, ring radius 400 mm, 576 crystals, "
           "arc-corrected 288 angles x 329 radial x 63 planes",
     "c1": "parallel-beam CT fwd+bwd (L2 + Adam): 1,000 Gaussians, 16 views x 64x64",
+    "c4": "batching: 64 cone-beam CT scans of uneven size (Gaussians log-uniform 5k-500k, views "
+          "U{30..360}, detector side U{128,256,384,512}), fwd+bwd (L2 + Adam) as one graph-captured "
+          "step with persistent launches, tile shape from the autotuner; against 64 plain steps",
 }
 
 
@@ -60,6 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--scans", type=int, default=64, help="c4: number of scans")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
@@ -391,10 +395,98 @@ def e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world):
                 d2h_bytes_per_step=d2h, steps=steps)
 
 
+def c4_scans(n_scans, seed=0):
+    """The batching workload: uneven cone-beam scans (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scans):
+        n = int(round(math.exp(rng.uniform(math.log(5_000), math.log(500_000)))))
+        v = int(rng.integers(30, 361))
+        side = int(rng.choice([128, 256, 384, 512]))
+        G, gd = synth.workload_c2(10_000 + i, n=n, n_views=v, side=side)
+        out.append((_params(G), gd))
+    return out
+
+
+def run_c4(args):
+    """Batched step over uneven scans vs one plain step per scan (rays/s)."""
+    import torch
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    dev = torch.device("cuda", 0)
+    scans = c4_scans(args.scans)
+    ctx = rgrt.Context(0)
+    # tile shape from the autotuner, on the median-size scan
+    order = sorted(range(len(scans)), key=lambda i: scans[i][0]["mu"].shape[0])
+    G, gd = scans[order[len(order) // 2]]
+    gt = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
+    tw, th, _ = rgrt.autotune_tile(ctx, gt, gd, max_views=12)
+    gt.close()
+    geoms, gb, gp, ys = [], [], [], []
+    rays = 0
+    for i, (G, gd) in enumerate(scans):
+        gd = dict(gd, tile_w=tw, tile_h=th)
+        geom = rgrt.Geometry(ctx, gd)
+        tr = synth.perturbed(G, 20_000 + i, pos_std=0.01)
+        g_true = rgrt.Gaussians(ctx, *[torch.from_numpy(tr[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
+        y = torch.empty(geom.n_rays, device=dev)
+        rgrt.project_forward(ctx, g_true, geom, y)
+        g_true.close()
+        geoms.append(geom)
+        ys.append(y)
+        gb.append(rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")]))
+        gp.append(rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")]))
+        rays += geom.n_rays
+    hp = rgrt.adam_params()
+    batch = rgrt.Batch(ctx, gb, geoms)
+    step = 0
+    for _ in range(args.warmup):
+        step += 1
+        batch.loss_step(ys, rgrt.RGRT_LOSS_L2, hp, step)
+    torch.cuda.synchronize()
+    l0 = rgrt.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step += 1
+        batch.loss_step(ys, rgrt.RGRT_LOSS_L2, hp, step)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    launches = rgrt.launch_count() - l0
+    # one plain loss_step per scan (each with its own binning read-back)
+    lo = torch.zeros(1, device=dev)
+    pstep = 0
+    for _ in range(args.warmup):
+        pstep += 1
+        for g, geom, y in zip(gp, geoms, ys):
+            rgrt.loss_step(ctx, g, geom, y, rgrt.RGRT_LOSS_L2, hp, pstep, lo)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pstep += 1
+        for g, geom, y in zip(gp, geoms, ys):
+            rgrt.loss_step(ctx, g, geom, y, rgrt.RGRT_LOSS_L2, hp, pstep, lo)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / args.steps
+    info = batch.info()
+    line = dict(metric=METRIC, value=rays / t_batch, unit=UNIT, n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOADS["c4"], scans=len(scans), rays_per_step=rays,
+                            tile=f"{tw}x{th}", gaussians=int(sum(G["mu"].shape[0] for G, _ in scans)),
+                            l2="step working set far above L2 (not flushed)"),
+                plain=dict(value=rays / t_plain, ms_per_step=1e3 * t_plain,
+                           note="the same step as 64 loss_step calls, one scan at a time"),
+                speedup_vs_plain=t_plain / t_batch, batch=info, gpu_launches=launches,
+                e2e=None)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_c4(args)
     else:
         run_ours(args)
 

@@ -176,6 +176,45 @@ int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom,
 int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
               const rgrt_adam *hp, int t, float *loss_out, void *stream);
 
+/* ---- batched scans ---------------------------------------------------- */
+
+typedef struct rgrt_batch rgrt_batch;
+
+/* A batch of n_scans independent scans (scan i = Gaussians g[i] projected
+ * with geometry geom[i]); all scans share one ray kind (cone vs parallel)
+ * and one tile shape.  Creation plans key capacities from one binning pass
+ * per scan (it synchronises).  The handles must outlive the batch; the
+ * Gaussians are updated in place by rgrt_batch_loss_step.  RGRT_E_INVAL for
+ * mixed kinds or tile shapes, RGRT_E_NOMEM when the plan exceeds the budget. */
+int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g,
+                      const rgrt_geom *const *geom, rgrt_batch **out);
+int rgrt_batch_destroy(rgrt_batch *b);
+
+/* Forward projection of every scan (binning of all scans, then one persistent
+ * launch over every (scan, tile) work item; captured once in a CUDA graph and
+ * replayed).  out_I[i] receives scan i's projection (host or device; null
+ * skips it).  Re-plans and repeats when the parameters have moved so far that
+ * a scan's tile entries no longer fit.  Synchronises with `stream`. */
+int rgrt_batch_forward(rgrt_batch *b, float *const *out_I, void *stream);
+
+/* One optimisation step of every scan, as loss_step does for one: forward,
+ * loss against y[i] (device arrays), adjoint (one persistent launch over all
+ * scans), parameter chain and Adam (step t).  loss_out[n_scans] (host or
+ * device, may be null) receives the losses.  Captured in a CUDA graph that is
+ * replayed while y, loss and hp stay the same.  Synchronises with `stream`. */
+int rgrt_batch_loss_step(rgrt_batch *b, const float *const *y, int loss, const rgrt_adam *hp, int t,
+                         float *loss_out, void *stream);
+
+/* work items (tiles of all scans), planned key capacity, re-plans so far */
+int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans);
+
+/* Tile-shape autotuner: times project_forward + project_backward of g on
+ * `desc` (CT: an evenly spaced subset of max_views views; max_views <= 0 keeps
+ * all) for the tile shapes 16x16, 16x8, 8x8 and 32x8, and returns the
+ * fastest (and its time in ms for the subset). */
+int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc, int max_views,
+                       int *tile_w, int *tile_h, double *ms_out);
+
 /* ---- allocation-free forward projection ----------------------------- */
 
 /* Maximum scratch, in bytes, of project_forward_noalloc (one static device

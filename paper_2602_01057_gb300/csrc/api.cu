@@ -15,6 +15,7 @@
 
 #include "../../include/rgrt.h"
 #include "rgrt_internal.h"
+#include "rgrt_objects.h"
 
 using namespace rgrt;
 
@@ -53,62 +54,7 @@ int fail(int code, const char *fmt, ...)
         if (r_ != RGRT_OK) return r_;  \
     } while (0)
 
-struct Buf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct ProfRec {
-    std::string name;
-    cudaEvent_t a, b;
-};
-
 }  // namespace
-
-struct rgrt_ctx {
-    int device = 0;
-    size_t budget = 0;
-    size_t used = 0;
-    // scratch
-    Buf cnt, off, rect, keys, vals, keys_alt, vals_alt, sort_tmp, scan_tmp, ranges, total;
-    Buf stage_in[4], stage_out[4], I, dLdI, y, grad, gflat, partial, stats, loss;
-    unsigned long long *h_total = nullptr;  // pinned
-    // binning cache
-    const rgrt_gauss *bin_g = nullptr;
-    const rgrt_geom *bin_geom = nullptr;
-    unsigned long long bin_version = 0;
-    int bin_v0 = -1, bin_nv = 0;
-    uint32_t bin_keys = 0;
-    bool bin_valid = false;
-    // profiling
-    bool prof = false;
-    bool stats_on = false;
-    std::vector<ProfRec> pending;
-    std::map<std::string, std::pair<long long, double>> prof_acc;
-    long long last_keys = 0;
-};
-
-struct rgrt_gauss {
-    rgrt_ctx *ctx = nullptr;
-    int64_t n = 0;
-    bool owned = false;
-    float *mu = nullptr, *ls = nullptr, *q = nullptr, *rho = nullptr;
-    void *block = nullptr;     // owned parameter block (COPY)
-    float4 *rec = nullptr, *crec = nullptr;
-    float *adam_m = nullptr, *adam_v = nullptr;
-    unsigned long long version = 1;
-    size_t bytes = 0;
-};
-
-struct rgrt_geom {
-    rgrt_ctx *ctx = nullptr;
-    rgrt_geom_desc desc{};
-    DevGeom dg{};
-    float *d_tables = nullptr;
-    int64_t n_rays = 0;
-    int tiles_per_view = 0;
-    size_t bytes = 0;
-};
 
 namespace {
 
@@ -298,7 +244,7 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     {
         PROF("k_emit");
         CK(launch_emit(dg, nv, N, (uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p,
-                       (uint2 *)ctx->rect.p, keys, vals, (uint32_t)K, s));
+                       (uint2 *)ctx->rect.p, keys, vals, (uint32_t)K, nullptr, s));
     }
     {
         PROF("radix_sort");
@@ -473,6 +419,20 @@ int validate_desc(const rgrt_geom_desc *d)
 }
 
 }  // namespace
+
+int rgrt::ctx_alloc(rgrt_ctx *c, void **p, size_t bytes) { return dev_alloc(c, p, bytes); }
+void rgrt::ctx_free(rgrt_ctx *c, void *p, size_t bytes) { dev_free(c, p, bytes); }
+
+int rgrt::gauss_adam(rgrt_gauss *g, cudaStream_t s)
+{
+    if (g->adam_m || g->n == 0) return RGRT_OK;
+    void *p = nullptr;
+    TRY(dev_alloc(g->ctx, &p, sizeof(float) * 22 * (size_t)g->n));
+    CK(cudaMemsetAsync(p, 0, sizeof(float) * 22 * (size_t)g->n, s));
+    g->adam_m = (float *)p;
+    g->adam_v = g->adam_m + 11 * g->n;
+    return RGRT_OK;
+}
 
 // validation and error reporting shared with the allocation-free entry point
 int rgrt::validate_geometry(const rgrt_geom_desc *d) { return validate_desc(d); }
@@ -818,7 +778,7 @@ int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *
         PROF("k_adam");
         for (int k = 0; k < 4; k++)
             CK(launch_adam(ps[k], gf + off[k], g->adam_m + off[k], g->adam_v + off[k], len[k], lr[k],
-                           hp->beta1, hp->beta2, hp->eps, bc1, bc2, s));
+                           hp->beta1, hp->beta2, hp->eps, bc1, bc2, nullptr, nullptr, s));
         g->version++;
     }
     if (loss_out) CK(cudaMemcpyAsync(loss_out, ctx->loss.p, sizeof(float), cudaMemcpyDefault, s));

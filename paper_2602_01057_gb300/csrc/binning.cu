@@ -137,13 +137,17 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restric
 // the same position keep ascending ids, the sort being stable).
 __global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict__ cnt,
                        const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
-                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t cap)
+                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t cap,
+                       uint32_t *overflow)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)nv * n) return;
     uint32_t c = cnt[idx];
     if (c == 0) return;
-    if ((uint64_t)off[idx] + c > cap) return;  // never taken when the scan is consistent
+    if ((uint64_t)off[idx] + c > cap) {   // more entries than the buffer holds
+        if (overflow) atomicOr(overflow, 1u);
+        return;
+    }
     int vl = (int)(idx / n);
     uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
     uint2 r = rect[idx];
@@ -260,11 +264,12 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
 
 cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
                         const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
-                        uint32_t cap, cudaStream_t s)
+                        uint32_t cap, uint32_t *overflow, cudaStream_t s)
 {
     int64_t tot = (int64_t)nv * n;
     if (tot <= 0) return cudaSuccess;
-    k_emit<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap);
+    k_emit<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap,
+                                                        overflow);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -231,7 +231,7 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
                  K, cv.used, SCRATCH_BYTES);
         return report_error(RGRT_E_CAPACITY, msg);
     }
-    NA_CK(launch_emit(dg, V, n, cnt, off, rect, keys, vals, (uint32_t)K, s));
+    NA_CK(launch_emit(dg, V, n, cnt, off, rect, keys, vals, (uint32_t)K, nullptr, s));
     NA_CK(launch_sort(keys, vals, keys_alt, vals_alt, (uint32_t)K, ceil_log2_u(T) + 8, sort_tmp, s));
     // tiles without entries keep the zero range: clear before filling
     NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)T, s));

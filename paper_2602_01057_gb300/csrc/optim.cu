@@ -120,10 +120,12 @@ __global__ void k_loss_final(const double *partial, int nblk, float *loss_out)
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
-                       float bc1, float bc2)
+                       float bc1, float bc2, const float *bc_dev, const uint32_t *skip)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (skip && *skip) return;
+    if (bc_dev) { bc1 = bc_dev[0]; bc2 = bc_dev[1]; }
     float gi = g[i];
     float mi = b1 * m[i] + (1.0f - b1) * gi;
     float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -165,10 +167,12 @@ cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, flo
 }
 
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr,
-                        float beta1, float beta2, float eps, float bc1, float bc2, cudaStream_t s)
+                        float beta1, float beta2, float eps, float bc1, float bc2,
+                        const float *bc_dev, const uint32_t *skip, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, lr, beta1, beta2, eps, bc1, bc2);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, g, m, v, n, lr, beta1, beta2, eps, bc1, bc2,
+                                                       bc_dev, skip);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -43,6 +43,7 @@ constexpr float SKIP_K2 = 9.2f;   // skip boxes: a little wider than the 3-sigma
 constexpr float W_SAT = 4.0f;     // |w| >= 4: erf(w) == +-1 in binary32
 constexpr float SAT_BALL = 8.66f; // (3 + 4 sqrt 2) sigma_max
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
+constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
 constexpr float NEG_HALF_LOG2E = -0.721347520444481703f;   // -log2(e)/2
 constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
 constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
@@ -305,12 +306,12 @@ struct TileCtx {
     long long out_idx;
 };
 
-__device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g)
+__device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
 {
     TileCtx c;
     int T = g.tiles_x * g.tiles_y;
-    c.vl = blockIdx.x / T;
-    int tin = blockIdx.x - c.vl * T;
+    c.vl = (int)(tile / (uint32_t)T);
+    int tin = (int)tile - c.vl * T;
     c.ty = tin / g.tiles_x;
     c.tx = tin - c.ty * g.tiles_x;
     c.view = g.v0 + c.vl;
@@ -369,12 +370,12 @@ struct ChunkLists {
 
 template <bool CONE>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
-                                           uint32_t base, int cnt, const float4 *rec,
-                                           const float4 *crec, VRec *sv, const float4 *wbox,
-                                           int nw, uint32_t *msk)
+                                           uint32_t base, uint32_t stride, int cnt,
+                                           const float4 *rec, const float4 *crec, VRec *sv,
+                                           const float4 *wbox, int nw, uint32_t *msk)
 {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        prep_record<CONE>(g, F, __ldg(gids + base + i), rec, crec, sv[i]);
+        prep_record<CONE>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i]);
         const float4 bb = sv[i].bb;
         uint32_t m = 0;
         for (int w = 0; w < nw; w++) {
@@ -432,19 +433,21 @@ __device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float
     return c2.w * ex2_approx(arg);
 }
 
+// forward integration of tile `tile` of geometry g (one ray per thread)
 template <bool CONE, bool STATS>
-__global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__restrict__ rec,
-                                                    const float4 *__restrict__ crec,
-                                                    const uint32_t *__restrict__ gids,
-                                                    const uint2 *__restrict__ ranges,
-                                                    float *__restrict__ out, Stats *stats)
+__device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
+                                             const float4 *__restrict__ rec,
+                                             const float4 *__restrict__ crec,
+                                             const uint32_t *__restrict__ gids,
+                                             const uint2 *__restrict__ ranges,
+                                             float *__restrict__ out, Stats *stats)
 {
     __shared__ VRec sv[CH];
     __shared__ ChunkLists lists;
     __shared__ uint32_t msk[CH];
     __shared__ float4 wbox[8];
     __shared__ float Fs[9];
-    const TileCtx c = tile_ctx(g);
+    const TileCtx c = tile_ctx(g, tile);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
     warp_box(c, wbox);
@@ -455,12 +458,17 @@ __global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__r
     const float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
     const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
     const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd) : 1.0f;
-    const uint2 rg = ranges[blockIdx.x];
+    const uint2 rg = ranges[tile];
     float acc_vs = 0.0f, acc_gen = 0.0f;
     unsigned n_eval = 0, n_kept = 0;
-    for (uint32_t base = rg.x; base < rg.y; base += CH) {
-        const int cnt = min((uint32_t)CH, rg.y - base);
-        prep_chunk<CONE>(g, F, gids, base, cnt, rec, crec, sv, wbox, nw, msk);
+    // chunk c takes list entries c, c + nch, c + 2 nch, ...: the lists are
+    // ordered by footprint position, and interleaving spreads every chunk
+    // over the whole tile, which keeps the warps' shares of it even
+    const uint32_t nlist = rg.y - rg.x;
+    const uint32_t nch = (nlist + CH - 1) / CH;
+    for (uint32_t ch = 0; ch < nch; ch++) {
+        const int cnt = (int)((nlist - ch + nch - 1) / nch);
+        prep_chunk<CONE>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk);
         __syncthreads();
         int nvs, ngen;
         build_lists(cnt, msk, lists, w, lane, nvs, ngen);
@@ -507,6 +515,16 @@ __global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__r
             atomicAdd(&stats->pairs_kept, kk);
         }
     }
+}
+
+template <bool CONE, bool STATS>
+__global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__restrict__ rec,
+                                                    const float4 *__restrict__ crec,
+                                                    const uint32_t *__restrict__ gids,
+                                                    const uint2 *__restrict__ ranges,
+                                                    float *__restrict__ out, Stats *stats)
+{
+    forward_tile<CONE, STATS>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
 }
 
 // symmetric 3x3 (packed 00 01 02 11 12 22) back to world: G = E G' E^T
@@ -681,19 +699,20 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
 // the Q and A quadratics are evaluated in Horner form in du with the dv terms
 // hoisted.
 template <bool CONE, int TW>
-__global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
-                                                 const float4 *__restrict__ crec,
-                                                 const uint32_t *__restrict__ gids,
-                                                 const uint2 *__restrict__ ranges,
-                                                 const float *__restrict__ dLdI,
-                                                 float4 *__restrict__ grad)
+__device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
+                                             const float4 *__restrict__ rec,
+                                             const float4 *__restrict__ crec,
+                                             const uint32_t *__restrict__ gids,
+                                             const uint2 *__restrict__ ranges,
+                                             const float *__restrict__ dLdI,
+                                             float4 *__restrict__ grad)
 {
     __shared__ float sgl[256];   // dL/dI |d~| of the tile's rays, row-major (0 outside the detector)
     __shared__ float su[32], svr[32];
     __shared__ float Fs[9];
     const int T = g.tiles_x * g.tiles_y;
-    const int vl = blockIdx.x / T;
-    const int tin = blockIdx.x - vl * T;
+    const int vl = (int)(tile / (uint32_t)T);
+    const int tin = (int)tile - vl * T;
     const int ty = tin / g.tiles_x, tx = tin - ty * g.tiles_x;
     const int view = g.v0 + vl;
     const int TH = g.tile_h;
@@ -718,7 +737,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
     float F[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) F[i] = Fs[i];
-    const uint2 rg = ranges[blockIdx.x];
+    const uint2 rg = ranges[tile];
     // every lane of a warp runs the same number of rounds (inactive lanes idle)
     const uint32_t n = rg.y - rg.x;
     const uint32_t rounds = (n + blockDim.x - 1) / blockDim.x;
@@ -872,7 +891,123 @@ __global__ void __launch_bounds__(128) k_adjoint(DevGeom g, const float4 *__rest
     }
 }
 
+template <bool CONE, int TW>
+__global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
+                                                 const float4 *__restrict__ crec,
+                                                 const uint32_t *__restrict__ gids,
+                                                 const uint2 *__restrict__ ranges,
+                                                 const float *__restrict__ dLdI,
+                                                 float4 *__restrict__ grad)
+{
+    adjoint_tile<CONE, TW>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
+}
+
+// Persistent forms over a batch of scans: every CTA takes (scan, tile) work
+// items from an atomic counter until all are done.  Items are numbered scan
+// by scan (ScanDesc::item_begin); the CTA finds its scan by binary search.
+__device__ __forceinline__ bool next_item(const ScanDesc *d, int nscan, uint32_t total,
+                                          uint32_t *queue, uint32_t &item, int &scan)
+{
+    __shared__ uint32_t s_item;
+    __shared__ int s_scan;
+    __syncthreads();   // the previous item is finished by every thread
+    if (threadIdx.x == 0) {
+        const uint32_t it = atomicAdd(queue, 1u);
+        int lo = 0, hi = nscan - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].item_begin <= it) lo = mid; else hi = mid - 1;
+        }
+        s_item = it;
+        s_scan = lo;
+    }
+    __syncthreads();
+    item = s_item;
+    scan = s_scan;
+    return item < total;
+}
+
+template <bool CONE>
+__global__ void __launch_bounds__(256, 3) k_forward_persistent(const ScanDesc *__restrict__ d,
+                                                               int nscan, uint32_t total,
+                                                               uint32_t *queue)
+{
+    uint32_t item;
+    int scan;
+    while (next_item(d, nscan, total, queue, item, scan)) {
+        const ScanDesc &sd = d[scan];
+        forward_tile<CONE, false>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+                                  sd.out, nullptr);
+    }
+}
+
+template <bool CONE, int TW>
+__global__ void __launch_bounds__(ADJ_BS) k_adjoint_persistent(const ScanDesc *__restrict__ d, int nscan,
+                                                              uint32_t total, uint32_t *queue)
+{
+    uint32_t item;
+    int scan;
+    while (next_item(d, nscan, total, queue, item, scan)) {
+        const ScanDesc &sd = d[scan];
+        adjoint_tile<CONE, TW>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+                               sd.dLdI, sd.grad);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_forward_persistent(bool cone, const ScanDesc *d, int nscan, uint32_t total,
+                                      uint32_t *queue, int tile_threads, int grid, cudaStream_t s)
+{
+    if (total == 0) return cudaSuccess;
+    if (cone) k_forward_persistent<true><<<grid, tile_threads, 0, s>>>(d, nscan, total, queue);
+    else k_forward_persistent<false><<<grid, tile_threads, 0, s>>>(d, nscan, total, queue);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_persistent(bool cone, int tile_w, const ScanDesc *d, int nscan,
+                                      uint32_t total, uint32_t *queue, int grid, cudaStream_t s)
+{
+    if (total == 0) return cudaSuccess;
+#define RGRT_ADJP(C, TW) k_adjoint_persistent<C, TW><<<grid, ADJ_BS, 0, s>>>(d, nscan, total, queue)
+    if (cone) {
+        if (tile_w == 8) RGRT_ADJP(true, 8);
+        else if (tile_w == 16) RGRT_ADJP(true, 16);
+        else RGRT_ADJP(true, 32);
+    } else {
+        if (tile_w == 8) RGRT_ADJP(false, 8);
+        else if (tile_w == 16) RGRT_ADJP(false, 16);
+        else RGRT_ADJP(false, 32);
+    }
+#undef RGRT_ADJP
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <class K>
+int grid_for(K kernel, int threads)
+{
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    return nsm * (per < 1 ? 1 : per);
+}
+
+int persistent_grid(bool forward, bool cone, int tile_w, int tile_threads)
+{
+    if (forward)
+        return cone ? grid_for(k_forward_persistent<true>, tile_threads)
+                    : grid_for(k_forward_persistent<false>, tile_threads);
+    if (cone)
+        return tile_w == 8 ? grid_for(k_adjoint_persistent<true, 8>, ADJ_BS)
+             : tile_w == 16 ? grid_for(k_adjoint_persistent<true, 16>, ADJ_BS)
+                            : grid_for(k_adjoint_persistent<true, 32>, ADJ_BS);
+    return tile_w == 8 ? grid_for(k_adjoint_persistent<false, 8>, ADJ_BS)
+         : tile_w == 16 ? grid_for(k_adjoint_persistent<false, 16>, ADJ_BS)
+                        : grid_for(k_adjoint_persistent<false, 32>, ADJ_BS);
+}
 
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, float *out, Stats *stats,
@@ -898,7 +1033,7 @@ cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const fl
 {
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
-    const int bs = 128;
+    const int bs = ADJ_BS;
 #define RGRT_ADJ(CONE, TW) k_adjoint<CONE, TW><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
     if (g.kind == 1) {
         if (g.tile_w == 8) RGRT_ADJ(true, 8);

@@ -58,7 +58,7 @@ cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n,
                         uint2 *rect, cudaStream_t s);
 cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
                         const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
-                        uint32_t cap, cudaStream_t s);
+                        uint32_t cap, uint32_t *overflow, cudaStream_t s);
 cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
                           cudaStream_t s);
 
@@ -81,6 +81,28 @@ cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const fl
 cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, const float *dLdI,
                            float4 *grad, cudaStream_t s);
+// one scan of a batch, as the persistent kernels see it
+struct ScanDesc {
+    DevGeom g;
+    const float4 *rec, *crec;
+    const uint32_t *gids;
+    const uint2 *ranges;
+    float *out;             // forward output
+    const float *dLdI;      // adjoint input
+    float4 *grad;           // adjoint accumulator
+    uint32_t item_begin;    // first (scan, tile) work item of the scan
+    uint32_t n_items;       // tiles of the scan
+};
+// persistent integration / adjoint over every tile of a batch of scans; the
+// queue counter must be zero at launch.  tile_threads = tile_w * tile_h of
+// every scan (one ray per thread in the forward).
+cudaError_t launch_forward_persistent(bool cone, const ScanDesc *d, int nscan, uint32_t total,
+                                      uint32_t *queue, int tile_threads, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_persistent(bool cone, int tile_w, const ScanDesc *d, int nscan,
+                                      uint32_t total, uint32_t *queue, int grid, cudaStream_t s);
+// CTAs of a persistent launch: SMs x resident CTAs per SM
+int persistent_grid(bool forward, bool cone, int tile_w, int tile_threads);
+
 cudaError_t launch_param_chain(const float *mu, const float *ls, const float *q, const float *rho,
                                int64_t n, const float4 *grad, float *g_mu, float *g_ls,
                                float *g_q, float *g_rho, cudaStream_t s);
@@ -88,7 +110,11 @@ cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, flo
                         float eps, float *dLdI, double *partial, int nblk, float *loss_out,
                         cudaStream_t s);
 int loss_blocks(int64_t n);
+// Adam; bc_dev (optional) supplies the bias corrections (1 - beta^t) from
+// device memory instead of bc1, bc2; skip (optional) leaves everything
+// unchanged when *skip != 0
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr,
-                        float beta1, float beta2, float eps, float bc1, float bc2, cudaStream_t s);
+                        float beta1, float beta2, float eps, float bc1, float bc2,
+                        const float *bc_dev, const uint32_t *skip, cudaStream_t s);
 
 }  // namespace rgrt

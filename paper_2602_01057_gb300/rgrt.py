@@ -65,6 +65,15 @@ _EXPORTS = {
     "project_backward": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "loss_step": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
                   ctypes.c_int),
+    "rgrt_batch_create": ([_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "rgrt_batch_destroy": ([_VP], ctypes.c_int),
+    "rgrt_batch_forward": ([_VP, _VP, _VP], ctypes.c_int),
+    "rgrt_batch_loss_step": ([_VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
+                             ctypes.c_int),
+    "rgrt_batch_info": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "rgrt_autotune_tile": ([_VP, _VP, ctypes.POINTER(GeomDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "project_forward_noalloc": ([ctypes.POINTER(GeomDesc), ctypes.c_int64, _VP, _VP, _VP, _VP,
                                  _VP, _VP], ctypes.c_int),
     "rgrt_last_error": ([], ctypes.c_char_p),
@@ -305,6 +314,63 @@ def project_forward_noalloc(desc: dict, mu, ls, q, rho, out, stream=None):
                                          _ptr(out), _stream(stream)))
     del angles
     return out
+
+
+class Batch:
+    """Many independent scans stepped together: one persistent launch per pass
+    over every (scan, tile) work item, the whole step replayed from a CUDA graph."""
+
+    def __init__(self, ctx: Context, gauss: list, geoms: list):
+        assert len(gauss) == len(geoms) and gauss
+        self.ctx = ctx
+        self.gauss = list(gauss)
+        self.geoms = list(geoms)
+        self.n = len(gauss)
+        gh = (_VP * self.n)(*[g.h for g in gauss])
+        mh = (_VP * self.n)(*[g.h for g in geoms])
+        h = _VP()
+        _check(lib().rgrt_batch_create(ctx.h, self.n, ctypes.cast(gh, _VP), ctypes.cast(mh, _VP),
+                                       ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().rgrt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, outs, stream=None):
+        arr = (_VP * self.n)(*[_ptr(o) for o in outs])
+        _check(lib().rgrt_batch_forward(self.h, ctypes.cast(arr, _VP), _stream(stream)))
+        return outs
+
+    def loss_step(self, ys, loss=RGRT_LOSS_L2, hp=None, t=1, stream=None):
+        hp = hp or adam_params()
+        arr = (_VP * self.n)(*[_ptr(y) for y in ys])
+        out = np.zeros(self.n, np.float32)
+        _check(lib().rgrt_batch_loss_step(self.h, ctypes.cast(arr, _VP), int(loss), ctypes.byref(hp),
+                                          int(t), _ptr(out), _stream(stream)))
+        return out
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().rgrt_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(work_items=a.value, key_capacity=b.value, replans=c.value)
+
+
+def autotune_tile(ctx, gauss, desc: dict, max_views=12):
+    """(tile_w, tile_h, ms) of the fastest tile shape for this scan."""
+    d, angles = make_desc(desc)
+    tw, th, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().rgrt_autotune_tile(ctx.h, gauss.h, ctypes.byref(d), int(max_views), ctypes.byref(tw),
+                                    ctypes.byref(th), ctypes.byref(ms)))
+    del angles
+    return tw.value, th.value, ms.value
 
 
 def adam_params(lr_mu=2e-4, lr_logscale=5e-3, lr_quat=1e-3, lr_rho=1e-2, beta1=0.9, beta2=0.999,
