@@ -84,7 +84,8 @@ typedef struct rgrt_geom rgrt_geom;
  *   CT_PARALLEL  ray o = u e_u + v e_v, d = e_w, t in [t_a, t_b].
  *   CT_CONE      source S = -dso e_w, pixel D = S + dsd e_w + u e_u + v e_v;
  *                the ray runs from S to D.
- * PET frame of angle k: phi = pi k / n_views, e_u = (cos phi, sin phi, 0),
+ * PET frame of angle k: phi = pi k / n_views (phi = angles[k] when angles
+ * is not null, e.g. a subset of a sinogram's angles), e_u = (cos phi, sin phi, 0),
  * e_v = (0,0,1), e_w = (sin phi, -cos phi, 0); radial bin i at
  *   arc_mode 0 (arc-corrected): s_i = (i - c) pi radius / n_crystals
  *   arc_mode 1 (raw chords):    s_i = radius sin((i - c) pi / n_crystals)
@@ -99,7 +100,7 @@ typedef struct {
     int32_t n_views;     /* CT projections / PET sinogram angles */
     int32_t n_rows;      /* CT detector rows / PET planes */
     int32_t n_cols;      /* CT detector columns / PET radial bins */
-    const double *angles;/* CT: n_views angles in radians (host memory); PET: unused */
+    const double *angles;/* CT: n_views angles in radians (host memory); PET: null or n_views angles */
     double pitch_u, pitch_v;
     double t_a, t_b;     /* CT_PARALLEL segment */
     double dso, dsd;     /* CT_CONE source-origin and source-detector distances */
@@ -175,6 +176,16 @@ int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom,
  * null) receives the loss as a float. */
 int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
               const rgrt_adam *hp, int t, float *loss_out, void *stream);
+
+/* Loss and its gradient without an update: forward, loss against
+ * y[geometry_num_rays] (only kappa and poisson_eps of hp are read), dL/dI,
+ * adjoint and parameter chain; writes dL/dmu, dL/dlogscale, dL/dquat, dL/drho
+ * (host or device; null skips) and the loss (host or device, may be null).
+ * The Gaussians are not changed.  For callers that run their own optimiser.
+ * Errors as loss_step. */
+int loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
+              const rgrt_adam *hp, float *loss_out, float *g_mu3, float *g_logscale3,
+              float *g_quat4, float *g_rho, void *stream);
 
 /* ---- batched scans ---------------------------------------------------- */
 

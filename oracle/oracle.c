@@ -40,7 +40,9 @@
  *   kind 1  cone-beam CT: same frame, source S = -dso e_w, detector point
  *           D = S + dsd e_w + u e_u + v e_v; o = S, d = (D-S)/|D-S|,
  *           t in [0, |D-S|].
- *   kind 2  PET ring: phi_j = pi j / n_views, e_u=(cos phi, sin phi, 0),
+ *   kind 2  PET ring: phi_j = pi j / n_views (or angles[j] when the caller
+ *           gives the angles, e.g. a subset of a sinogram's angles),
+ *           e_u=(cos phi, sin phi, 0),
  *           e_v=(0,0,1), e_w=(sin phi, -cos phi, 0); o = s e_u + z e_v,
  *           d = e_w, t in [-sqrt(R^2-s^2), +sqrt(R^2-s^2)].
  *           Arc-corrected: s_k = (k-c) pi R / n_crystals; raw chords:
@@ -81,7 +83,7 @@ static const double OG_PI = 3.14159265358979323846;
 static void og_frame(const og_geom *g, int v, double eu[3], double ev[3], double ew[3])
 {
     if (g->kind == OG_PET) {
-        double phi = (OG_PI * (double)v) / (double)g->n_views;
+        double phi = g->angles ? g->angles[v] : (OG_PI * (double)v) / (double)g->n_views;
         double c = cos(phi), s = sin(phi);
         eu[0] = c;  eu[1] = s;  eu[2] = 0.0;
         ev[0] = 0.; ev[1] = 0.; ev[2] = 1.0;

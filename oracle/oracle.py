@@ -83,11 +83,12 @@ class Geometry:
     def __init__(self, desc: dict):
         self.desc = desc
         self._angles = _f64(desc.get("angles", np.zeros(0)))
-        if self._angles.size == 0:
-            self._angles = np.zeros(1)
+        # no angles: null (PET then spaces its n_views angles evenly over pi)
+        aptr = (self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if self._angles.size
+                else ctypes.POINTER(ctypes.c_double)())
         self.s = _Geom(
             _KIND[desc["kind"]], int(desc["n_views"]), int(desc["n_rows"]), int(desc["n_cols"]),
-            self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            aptr,
             float(desc.get("pitch_u", 0.0)), float(desc.get("pitch_v", 0.0)),
             float(desc.get("t_a", 0.0)), float(desc.get("t_b", 0.0)),
             float(desc.get("dso", 0.0)), float(desc.get("dsd", 0.0)),

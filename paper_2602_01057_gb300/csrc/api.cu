@@ -386,6 +386,10 @@ int validate_desc(const rgrt_geom_desc *d)
         return fail(RGRT_E_INVAL, "too many tiles per detector axis");
     if ((int64_t)d->n_views * ((d->n_cols + tw - 1) / tw) * ((d->n_rows + th - 1) / th) > (1 << 30))
         return fail(RGRT_E_INVAL, "too many tiles");
+    if (d->kind == RGRT_GEOM_PET_RING && d->angles) {
+        for (int v = 0; v < d->n_views; v++)
+            if (!std::isfinite(d->angles[v])) return fail(RGRT_E_INVAL, "non-finite view angle %d", v);
+    }
     if (d->kind != RGRT_GEOM_PET_RING) {
         if (!d->angles) return fail(RGRT_E_INVAL, "CT geometry needs view angles");
         for (int v = 0; v < d->n_views; v++)
@@ -611,7 +615,7 @@ int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *d, rgrt_geom **out)
     for (int v = 0; v < V; v++) {
         double eu[3], ev[3], ew[3];
         if (d->kind == RGRT_GEOM_PET_RING) {
-            double phi = (PI * (double)v) / (double)V;
+            double phi = d->angles ? d->angles[v] : (PI * (double)v) / (double)V;
             double c = cos(phi), s = sin(phi);
             eu[0] = c; eu[1] = s; eu[2] = 0.0;
             ew[0] = s; ew[1] = -c; ew[2] = 0.0;
@@ -736,18 +740,13 @@ int project_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, 
     return RGRT_OK;
 }
 
-int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
-              const rgrt_adam *hp, int t, float *loss_out, void *stream)
+// forward, loss and dL/dI into ctx->dLdI, adjoint and parameter chain into
+// the four device gradient arrays (shared by loss_step and loss_grad)
+static int run_loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const void *dy,
+                         int loss, const rgrt_adam *hp, float *gm, float *gl, float *gq, float *gr,
+                         cudaStream_t s)
 {
-    TRY(check_ctx(ctx));
-    if (!g || !geom || !y || !hp) return fail(RGRT_E_INVAL, "null argument");
-    if (g->ctx != ctx || geom->ctx != ctx) return fail(RGRT_E_INVAL, "objects of another context");
-    if (loss != RGRT_LOSS_L2 && loss != RGRT_LOSS_POISSON) return fail(RGRT_E_INVAL, "loss %d", loss);
-    if (t < 1) return fail(RGRT_E_INVAL, "Adam step t must be >= 1");
-    cudaStream_t s = (cudaStream_t)stream;
     const int64_t R = geom->n_rays, N = g->n;
-    const void *dy;
-    TRY(stage_input(ctx, ctx->stage_in[0], y, sizeof(float) * (size_t)R, s, &dy));
     TRY(ensure(ctx, ctx->I, sizeof(float) * (size_t)R));
     TRY(ensure(ctx, ctx->dLdI, sizeof(float) * (size_t)R));
     int nblk = loss_blocks(R);
@@ -759,10 +758,37 @@ int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *
         CK(launch_loss(loss, (float *)ctx->I.p, (const float *)dy, R, hp->kappa, hp->poisson_eps,
                        (float *)ctx->dLdI.p, (double *)ctx->partial.p, nblk, (float *)ctx->loss.p, s));
     }
+    if (N > 0) TRY(run_backward(ctx, g, geom, (float *)ctx->dLdI.p, gm, gl, gq, gr, s));
+    return RGRT_OK;
+}
+
+static int check_loss_args(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const float *y,
+                           int loss, const rgrt_adam *hp)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !geom || !y || !hp) return fail(RGRT_E_INVAL, "null argument");
+    if (g->ctx != ctx || geom->ctx != ctx) return fail(RGRT_E_INVAL, "objects of another context");
+    if (loss != RGRT_LOSS_L2 && loss != RGRT_LOSS_POISSON) return fail(RGRT_E_INVAL, "loss %d", loss);
+    return RGRT_OK;
+}
+
+int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
+              const rgrt_adam *hp, int t, float *loss_out, void *stream)
+{
+    TRY(check_loss_args(ctx, g, geom, y, loss, hp));
+    if (t < 1) return fail(RGRT_E_INVAL, "Adam step t must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t R = geom->n_rays, N = g->n;
+    const void *dy;
+    TRY(stage_input(ctx, ctx->stage_in[0], y, sizeof(float) * (size_t)R, s, &dy));
+    float *gf = nullptr;
     if (N > 0) {
         TRY(ensure(ctx, ctx->gflat, sizeof(float) * 11 * (size_t)N));
-        float *gf = (float *)ctx->gflat.p;
-        TRY(run_backward(ctx, g, geom, (float *)ctx->dLdI.p, gf, gf + 3 * N, gf + 6 * N, gf + 10 * N, s));
+        gf = (float *)ctx->gflat.p;
+    }
+    TRY(run_loss_grad(ctx, g, geom, dy, loss, hp, gf, gf ? gf + 3 * N : nullptr,
+                      gf ? gf + 6 * N : nullptr, gf ? gf + 10 * N : nullptr, s));
+    if (N > 0) {
         if (!g->adam_m) {
             void *p = nullptr;
             TRY(dev_alloc(ctx, &p, sizeof(float) * 22 * (size_t)N));
@@ -783,6 +809,38 @@ int loss_step(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom *geom, const float *
     }
     if (loss_out) CK(cudaMemcpyAsync(loss_out, ctx->loss.p, sizeof(float), cudaMemcpyDefault, s));
     if (loss_out && !is_device_ptr(loss_out)) CK(cudaStreamSynchronize(s));
+    return RGRT_OK;
+}
+
+int loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const float *y, int loss,
+              const rgrt_adam *hp, float *loss_out, float *g_mu3, float *g_ls3, float *g_q4,
+              float *g_rho, void *stream)
+{
+    TRY(check_loss_args(ctx, g, geom, y, loss, hp));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t R = geom->n_rays;
+    const size_t n = (size_t)g->n;
+    const void *dy;
+    TRY(stage_input(ctx, ctx->stage_in[0], y, sizeof(float) * (size_t)R, s, &dy));
+    float *outs[4] = { g_mu3, g_ls3, g_q4, g_rho };
+    const size_t sz[4] = { 3 * n, 3 * n, 4 * n, n };
+    void *dev[4];
+    bool back[4];
+    for (int k = 0; k < 4; k++)
+        TRY(stage_output(ctx, ctx->stage_out[k], outs[k], sizeof(float) * sz[k], &dev[k], &back[k]));
+    TRY(run_loss_grad(ctx, g, geom, dy, loss, hp, (float *)dev[0], (float *)dev[1], (float *)dev[2],
+                      (float *)dev[3], s));
+    bool sync = false;
+    for (int k = 0; k < 4; k++)
+        if (back[k]) {
+            CK(cudaMemcpyAsync(outs[k], dev[k], sizeof(float) * sz[k], cudaMemcpyDeviceToHost, s));
+            sync = true;
+        }
+    if (loss_out) {
+        CK(cudaMemcpyAsync(loss_out, ctx->loss.p, sizeof(float), cudaMemcpyDefault, s));
+        sync = sync || !is_device_ptr(loss_out);
+    }
+    if (sync) CK(cudaStreamSynchronize(s));
     return RGRT_OK;
 }
 

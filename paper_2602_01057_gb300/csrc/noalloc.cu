@@ -136,7 +136,7 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
     for (int v = 0; v < V; v++) {
         double eu[3], ev[3] = { 0.0, 0.0, 1.0 }, ew[3];
         if (d->kind == RGRT_GEOM_PET_RING) {
-            double phi = (PI * (double)v) / (double)V;
+            double phi = d->angles ? d->angles[v] : (PI * (double)v) / (double)V;
             double c = cos(phi), sn = sin(phi);
             eu[0] = c; eu[1] = sn; eu[2] = 0.0;
             ew[0] = sn; ew[1] = -c; ew[2] = 0.0;

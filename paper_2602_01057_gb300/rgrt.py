@@ -65,6 +65,8 @@ _EXPORTS = {
     "project_backward": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "loss_step": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
                   ctypes.c_int),
+    "loss_grad": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP],
+                  ctypes.c_int),
     "rgrt_batch_create": ([_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "rgrt_batch_destroy": ([_VP], ctypes.c_int),
     "rgrt_batch_forward": ([_VP, _VP, _VP], ctypes.c_int),
@@ -244,11 +246,12 @@ class Gaussians:
 def make_desc(d: dict):
     """ctypes description from a synth geometry dict (keeps the angle array alive)."""
     angles = np.ascontiguousarray(d.get("angles", np.zeros(0)), dtype=np.float64)
-    if angles.size == 0:
-        angles = np.zeros(1)
+    # no angles: null (a PET sinogram then spaces its n_views angles evenly over pi)
+    aptr = (angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if angles.size
+            else ctypes.POINTER(ctypes.c_double)())
     desc = GeomDesc(
         _KIND[d["kind"]], int(d["n_views"]), int(d["n_rows"]), int(d["n_cols"]),
-        angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        aptr,
         float(d.get("pitch_u", 0.0)), float(d.get("pitch_v", 0.0)),
         float(d.get("t_a", 0.0)), float(d.get("t_b", 0.0)),
         float(d.get("dso", 0.0)), float(d.get("dsd", 0.0)), float(d.get("radius", 0.0)),
@@ -383,6 +386,15 @@ def loss_step(ctx, gauss, geom, y, loss=RGRT_LOSS_L2, hp: Adam | None = None, t:
     hp = hp or adam_params()
     _check(lib().loss_step(ctx.h, gauss.h, geom.h, _ptr(y), int(loss), ctypes.byref(hp), int(t),
                            _ptr(loss_out), _stream(stream)))
+    return loss_out
+
+
+def loss_grad(ctx, gauss, geom, y, loss=RGRT_LOSS_L2, hp: Adam | None = None, loss_out=None,
+              g_mu=None, g_ls=None, g_q=None, g_rho=None, stream=None):
+    """Loss and dL/d(mu, logscale, quat, rho) without updating the Gaussians."""
+    hp = hp or adam_params()
+    _check(lib().loss_grad(ctx.h, gauss.h, geom.h, _ptr(y), int(loss), ctypes.byref(hp), _ptr(loss_out),
+                           _ptr(g_mu), _ptr(g_ls), _ptr(g_q), _ptr(g_rho), _stream(stream)))
     return loss_out
 
 

@@ -318,3 +318,63 @@ def test_loss_step_matches_oracle(rg, ctx, torch, oracle, loss):
         d_got = (new[k].astype(np.float64) - G[k])[strong]
         d_ref = (p_ref - G[k])[strong]
         assert rel_l2(d_got, d_ref) < 1e-3, k
+
+
+# ------------------------------------------------------------------ loss_grad
+
+@pytest.mark.parametrize("loss", ["l2", "poisson"])
+def test_loss_grad_matches_oracle(rg, ctx, torch, oracle, loss):
+    """loss_grad: the loss and the gradient (no update) against the FP64
+    oracle's loss, dL/dI and adjoint; the Gaussians stay unchanged."""
+    G, gd = case("pet_arc" if loss == "poisson" else "cone_small")
+    ref_fwd = oracle.forward(gd, G)
+    rng = np.random.default_rng(4)
+    if loss == "l2":
+        y = (ref_fwd["I"] * rng.uniform(0.8, 1.2, ref_fwd["I"].size)).astype(np.float32)
+        kappa, eps = 1.0, 0.0
+        L_ref, dLdI = oracle.loss_l2(ref_fwd["I"], y)
+        kind = rg.RGRT_LOSS_L2
+    else:
+        kappa, eps = 50.0, 1e-3
+        y = rng.poisson(kappa * ref_fwd["I"] + eps).astype(np.float32)
+        L_ref, dLdI = oracle.loss_poisson(ref_fwd["I"], y, kappa, eps)
+        kind = rg.RGRT_LOSS_POISSON
+    hp = rg.adam_params(kappa=kappa, poisson_eps=eps)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    geom = rg.Geometry(ctx, gd)
+    n = gs.n
+    outs = [np.zeros(s, np.float32) for s in ((n, 3), (n, 3), (n, 4), (n,))]   # host outputs
+    lo = np.zeros(1, np.float32)
+    rg.loss_grad(ctx, gs, geom, y, kind, hp, lo, *outs)
+    assert float(lo[0]) == pytest.approx(L_ref, rel=1e-5)
+    ref = oracle.backward(gd, G, dLdI)
+    got = dict(zip(("mu", "ls", "q", "rho"), outs))
+    for k in ("mu", "ls", "q", "rho"):
+        assert grad_err(got, ref, k) < GRAD_TOL, k
+    after = gs.numpy()
+    for k in ("mu", "ls", "q", "rho"):
+        np.testing.assert_array_equal(after[k], G[k])
+
+
+# ------------------------------------------------------------------ view subsets
+
+@pytest.mark.parametrize("name", ["cone_small", "pet_arc"])
+def test_view_subset_geometry_bit_exact(rg, ctx, torch, oracle, name):
+    """A geometry holding a subset of a scan's views (explicit angles; for PET
+    the sinogram angles pi j / n_views) projects to exactly those views of the
+    full scan, and matches the oracle on its own."""
+    G, gd = case(name)
+    full, _, _ = gpu_forward(torch, rg, ctx, G, gd)
+    V, H, W = gd["n_views"], gd["n_rows"], gd["n_cols"]
+    idx = np.array([5, 0, V - 1, 7])
+    sub = dict(gd)
+    sub["n_views"] = idx.size
+    base = (np.pi * np.arange(V, dtype=np.float64) / V) if gd["kind"] == "pet" else gd["angles"]
+    sub["angles"] = np.asarray(base, np.float64)[idx].copy()
+    part, _, _ = gpu_forward(torch, rg, ctx, G, sub)
+    if gd["kind"] == "pet":
+        want = full.reshape(H, V, W)[:, idx, :].reshape(-1)
+    else:
+        want = full.reshape(V, H, W)[idx].reshape(-1)
+    np.testing.assert_array_equal(part, want)
+    assert fwd_err(part, oracle.forward(sub, G)) < FWD_TOL
