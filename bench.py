@@ -53,6 +53,13 @@ WORKLOADS = {
     "c4": "batching: 64 cone-beam CT scans of uneven size (Gaussians log-uniform 5k-500k, views "
           "U{30..360}, detector side U{128,256,384,512}), fwd+bwd (L2 + Adam) as one graph-captured "
           "step with persistent launches, tile shape from the autotuner; against 64 plain steps",
+    "c4-small": "batching, small scans: 64 cone-beam CT scans (Gaussians log-uniform 1k-20k, views "
+                "U{16..64}, detector side U{64,96,128}), fwd+bwd (L2 + Adam) as one graph-captured step; "
+                "against 64 plain steps",
+    "c5": "serving: Poisson arrivals, 70% loss+gradient jobs / 30% 200-iteration Adam reconstructions "
+          "(8 views per iteration); CT (cone, C2 geometry scaled to the side) and PET (288x329x63 "
+          "arc-corrected) 50:50; admission by a 150 GB HBM budget; continuous batching vs a "
+          "one-job-at-a-time server",
 }
 
 
@@ -64,6 +71,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--scans", type=int, default=64, help="c4: number of scans")
+    ap.add_argument("--jobs", type=int, default=48, help="c5: jobs per run")
+    ap.add_argument("--slots", type=int, default=4, help="c5: slots of the continuous server")
+    ap.add_argument("--rate", type=float, default=200.0, help="c5: arrival rate (jobs/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
@@ -395,14 +405,16 @@ def e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world):
                 d2h_bytes_per_step=d2h, steps=steps)
 
 
-def c4_scans(n_scans, seed=0):
+def c4_scans(n_scans, seed=0, small=False):
     """The batching workload: uneven cone-beam scans (seeded)."""
     rng = np.random.default_rng(seed)
     out = []
+    lo, hi, vmin, vmax, sides = ((1_000, 20_000, 16, 64, [64, 96, 128]) if small else
+                                 (5_000, 500_000, 30, 360, [128, 256, 384, 512]))
     for i in range(n_scans):
-        n = int(round(math.exp(rng.uniform(math.log(5_000), math.log(500_000)))))
-        v = int(rng.integers(30, 361))
-        side = int(rng.choice([128, 256, 384, 512]))
+        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        v = int(rng.integers(vmin, vmax + 1))
+        side = int(rng.choice(sides))
         G, gd = synth.workload_c2(10_000 + i, n=n, n_views=v, side=side)
         out.append((_params(G), gd))
     return out
@@ -414,7 +426,8 @@ def run_c4(args):
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
     dev = torch.device("cuda", 0)
-    scans = c4_scans(args.scans)
+    small = args.workload == "c4-small"
+    scans = c4_scans(args.scans, small=small)
     ctx = rgrt.Context(0)
     # tile shape from the autotuner, on the median-size scan
     order = sorted(range(len(scans)), key=lambda i: scans[i][0]["mu"].shape[0])
@@ -471,13 +484,159 @@ def run_c4(args):
     line = dict(metric=METRIC, value=rays / t_batch, unit=UNIT, n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOADS["c4"], scans=len(scans), rays_per_step=rays,
+                config=dict(workload=WORKLOADS[args.workload], scans=len(scans), rays_per_step=rays,
                             tile=f"{tw}x{th}", gaussians=int(sum(G["mu"].shape[0] for G, _ in scans)),
-                            l2="step working set far above L2 (not flushed)"),
+                            l2=("step working set far above L2 (not flushed)" if not small else
+                                "not flushed: the whole step is timed, small scans partly L2-resident")),
                 plain=dict(value=rays / t_plain, ms_per_step=1e3 * t_plain,
-                           note="the same step as 64 loss_step calls, one scan at a time"),
+                           note=f"the same step as {len(scans)} loss_step calls, one scan at a time"),
                 speedup_vs_plain=t_plain / t_batch, batch=info, gpu_launches=launches,
                 e2e=None)
+    print(json.dumps(line), flush=True)
+
+
+C5_CT_N = (20_000, 200_000)     # Gaussians (log-uniform)
+C5_CT_VIEWS = (30, 180)         # views (uniform)
+C5_CT_SIDE = (128, 256)         # detector side (uniform, multiple of 16)
+C5_PET_N = (50_000, 400_000)
+C5_ITERS, C5_VIEWS_PER_ITER = 200, 8
+C5_PET_COUNTS = 1e8
+
+
+def c5_jobs(n_jobs, rate, seed, rgrt, serve, ctx, dev):
+    """The serving stream (seeded): kinds, sizes, measurements, arrival offsets.
+
+    Measurements are the library's projection of a perturbed copy of each
+    job's Gaussians (CT), or Poisson counts of it scaled to 1e8 in total (PET);
+    both are made before any timing."""
+    import torch
+    rng = np.random.default_rng(seed)
+    ct_ph = synth.ellipsoid_phantom(12, seed=1000 + seed, semi=(0.05, 0.6), dens=(0.1, 1.0))
+    pet_ph = synth.pet_phantom(seed)
+    jobs, gaps = [], rng.exponential(1.0 / rate, n_jobs)
+    for i in range(n_jobs):
+        kind = serve.GRAD if rng.uniform() < 0.7 else serve.RECON
+        pet = rng.uniform() < 0.5
+        if pet:
+            n = int(round(math.exp(rng.uniform(*np.log(C5_PET_N)))))
+            G = synth.phantom_gaussians_mixture(pet_ph, n, seed=50_000 + i)
+            gd = synth.geom_c3()
+        else:
+            n = int(round(math.exp(rng.uniform(*np.log(C5_CT_N)))))
+            v = int(rng.integers(C5_CT_VIEWS[0], C5_CT_VIEWS[1] + 1))
+            side = 16 * int(rng.integers(C5_CT_SIDE[0] // 16, C5_CT_SIDE[1] // 16 + 1))
+            G = synth.phantom_gaussians_mixture(ct_ph, n, seed=50_000 + i)
+            gd = synth.geom_c2(n_views=v, side=side)
+        G = _params(G)
+        true = synth.perturbed(G, 60_000 + i, pos_std=1.0 if pet else 0.01)
+        geom = rgrt.Geometry(ctx, gd)
+        gt = rgrt.Gaussians(ctx, *[torch.from_numpy(true[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
+        I = torch.empty(geom.n_rays, device=dev)
+        rgrt.project_forward(ctx, gt, geom, I)
+        I = I.cpu().numpy().astype(np.float64)
+        gt.close()
+        geom.close()
+        if pet:
+            kappa = C5_PET_COUNTS / max(I.sum(), 1e-30)
+            y = rng.poisson(kappa * I).astype(np.float32)
+            hp, loss = dict(kappa=float(kappa), poisson_eps=1e-3), rgrt.RGRT_LOSS_POISSON
+        else:
+            y = I.astype(np.float32)
+            hp, loss = None, rgrt.RGRT_LOSS_L2
+        jobs.append(dict(kind=kind, G=G, geom=gd, y=y, loss=loss, hp=hp, n_iter=C5_ITERS,
+                         views_per_iter=C5_VIEWS_PER_ITER, seed=70_000 + i,
+                         tag=("pet" if pet else "ct", kind, n)))
+    return jobs, np.cumsum(gaps) - gaps[0]
+
+
+def c5_run(serve, rgrt, specs, offsets, n_slots, budget, rate_scale=1.0):
+    """Replay the stream on a server with n_slots slots; arrival i at
+    offsets[i] / rate_scale seconds after the start."""
+    import torch
+    srv = serve.Server(n_slots=n_slots, hbm_budget_bytes=budget, device=0)
+    jobs = [serve.Job(**sp) for sp in specs]
+    l0 = rgrt.launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    futs = []
+    for j, off in zip(jobs, offsets / rate_scale):
+        wait = t0 + off - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        j.t_arrive = t0 + off
+        futs.append(srv.submit(j))
+    for f in futs:
+        f.result()
+    t1 = time.perf_counter()
+    srv.close()
+    launches = rgrt.launch_count() - l0
+    lat = np.array([j.t_done - j.t_arrive for j in jobs])
+    rays = sum(j.rays for j in jobs)
+    # host<->device bytes of the jobs: parameters and measurements in;
+    # gradients (+ loss) or fitted parameters (+ loss history) out
+    h2d = sum(44 * j.G["mu"].shape[0] + (0 if j.y is None else 4 * j.y.size) for j in jobs)
+    d2h = sum(44 * j.G["mu"].shape[0] + 4 * (j.n_iter if j.kind == serve.RECON else 1) for j in jobs)
+    by_kind = {}
+    for k in (serve.GRAD, serve.RECON):
+        sel = np.array([j.kind == k for j in jobs])
+        if sel.any():
+            by_kind[k] = dict(jobs=int(sel.sum()), p50_s=float(np.percentile(lat[sel], 50)),
+                              p99_s=float(np.percentile(lat[sel], 99)))
+    return dict(slots=n_slots, jobs=len(jobs), wall_s=t1 - t0, jobs_per_s=len(jobs) / (t1 - t0),
+                rays_per_s=rays / (t1 - t0), p50_s=float(np.percentile(lat, 50)),
+                p99_s=float(np.percentile(lat, 99)), mean_s=float(lat.mean()), by_kind=by_kind,
+                peak_running=srv.peak_running, peak_budget_gb=srv.peak_used / 1e9,
+                gpu_launches=int(launches), h2d_bytes_per_job=h2d / len(jobs),
+                d2h_bytes_per_job=d2h / len(jobs))
+
+
+def run_c5(args):
+    """Serving: the same job stream through a continuous-batching server and
+    a one-job-at-a-time server, at the stated arrival rate and at a rate the
+    one-job server can sustain."""
+    import torch
+    from paper_2602_01057_gb300 import build, rgrt, serve
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = rgrt.Context(0)
+    budget = 150 * 10**9
+    specs, offsets = c5_jobs(args.jobs, args.rate, 0, rgrt, serve, ctx, dev)
+    ctx.close()
+    # warm-up: a few jobs through the continuous server (module load, allocator)
+    warm = [dict(sp, n_iter=5) for sp in specs[:max(args.warmup, 1)]]
+    c5_run(serve, rgrt, warm, np.zeros(len(warm)), args.slots, budget)
+    clocks = ClockSampler(0)
+    clocks.start()
+    cont = c5_run(serve, rgrt, specs, offsets, args.slots, budget)
+    fifo = c5_run(serve, rgrt, specs, offsets, 1, budget)
+    # a load the one-job server sustains: 80% of its measured throughput
+    lam80 = 0.8 * fifo["jobs_per_s"]
+    scale = lam80 / args.rate
+    cont80 = c5_run(serve, rgrt, specs, offsets, args.slots, budget, rate_scale=scale)
+    fifo80 = c5_run(serve, rgrt, specs, offsets, 1, budget, rate_scale=scale)
+    ck = clocks.stop()
+    n_ct = sum(1 for sp in specs if sp["tag"][0] == "ct")
+    n_recon = sum(1 for sp in specs if sp["kind"] == serve.RECON)
+    line = dict(metric=METRIC, value=cont["rays_per_s"], unit=UNIT, n_gpus=1, steps=len(specs),
+                warmup=len(warm), ms_per_step=1e3 * cont["wall_s"] / len(specs), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOADS["c5"], jobs=len(specs), ct_jobs=n_ct, recon_jobs=n_recon,
+                            rate_per_s=args.rate, slots=args.slots, hbm_budget_gb=150,
+                            scale_down=(f"CT Gaussians log-uniform {C5_CT_N[0]}-{C5_CT_N[1]} (of 20k-1M), "
+                                        f"views U{{{C5_CT_VIEWS[0]}..{C5_CT_VIEWS[1]}}} (of 30..720), "
+                                        f"side U{{{C5_CT_SIDE[0]}..{C5_CT_SIDE[1]}}} (of 128..512); "
+                                        "PET and reconstructions at full size"),
+                            l2="not flushed: jobs far above L2"),
+                serving=dict(continuous=cont, fifo=fifo,
+                             at_80pct_fifo_capacity=dict(rate_per_s=lam80, continuous=cont80, fifo=fifo80),
+                             throughput_vs_fifo=cont["jobs_per_s"] / fifo["jobs_per_s"],
+                             p99_vs_fifo_at_80pct=cont80["p99_s"] / fifo80["p99_s"]),
+                gpu_launches=cont["gpu_launches"], clocks=ck,
+                e2e=dict(value=cont["rays_per_s"], unit=UNIT,
+                         h2d_bytes_per_step=cont["h2d_bytes_per_job"],
+                         d2h_bytes_per_step=cont["d2h_bytes_per_job"],
+                         note="a step is one job; jobs enter and leave as host arrays, every copy "
+                              "inside the timed run"))
     print(json.dumps(line), flush=True)
 
 
@@ -485,8 +644,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c4":
+    elif args.workload in ("c4", "c4-small"):
         run_c4(args)
+    elif args.workload == "c5":
+        run_c5(args)
     else:
         run_ours(args)
 

@@ -191,9 +191,8 @@ def workload_c2(seed: int = 0, n: int = 50_000, n_views: int = 180, side: int = 
     return gs, geom_c2(n_views=n_views, side=side)
 
 
-def workload_c3(seed: int = 0, n: int = 200_000, n_angles: int = 288, n_radial: int = 329,
-                n_planes: int = 63) -> tuple[dict, dict]:
-    # activity ellipsoids inside a cylinder of radius 250 mm, |z| <= 60 mm
+def pet_phantom(seed: int = 0) -> dict:
+    """20 activity ellipsoids inside a cylinder of radius 250 mm, |z| <= 60 mm."""
     rng = np.random.default_rng(3000 + seed)
     k = 20
     axes = np.column_stack([rng.uniform(5, 80, k), rng.uniform(5, 80, k), rng.uniform(5, 40, k)])
@@ -204,10 +203,54 @@ def workload_c3(seed: int = 0, n: int = 200_000, n_angles: int = 288, n_radial: 
     ang = rng.uniform(0, 2 * math.pi, k)
     z_lim = np.maximum(60.0 - axes[:, 2], 0.0)
     centre = np.column_stack([rad * np.cos(ang), rad * np.sin(ang), rng.uniform(-1, 1, k) * z_lim])
-    ph = dict(axes=axes, rot=rot, centre=centre, density=rng.uniform(0.1, 1.0, k))
+    return dict(axes=axes, rot=rot, centre=centre, density=rng.uniform(0.1, 1.0, k))
+
+
+def workload_c3(seed: int = 0, n: int = 200_000, n_angles: int = 288, n_radial: int = 329,
+                n_planes: int = 63) -> tuple[dict, dict]:
+    ph = pet_phantom(seed)
     gs = phantom_fitted_gaussians(ph, n, seed=4000 + seed, box_lo=(-250, -250, -60),
                                   box_hi=(250, 250, 60))
     return gs, geom_c3(n_angles, n_radial, n_planes)
+
+
+def phantom_gaussians_mixture(ph: dict, n: int, seed: int, log_sigma_std: float = 0.3) -> dict:
+    """The recipe of phantom_fitted_gaussians without rejection sampling (for
+    large counts): the additive density is a mixture of uniform ellipsoids
+    with weights density x volume, so centres are drawn by picking an
+    ellipsoid with that probability and a uniform point inside it.  The
+    support volume (union of the ellipsoids) is sum_k vol_k E_k[1/cover(x)],
+    cover(x) = number of ellipsoids holding x, estimated from 4096 points
+    per ellipsoid."""
+    rng = np.random.default_rng(seed)
+    axes, rot, centre, dens = ph["axes"], ph["rot"], ph["centre"], ph["density"]
+    k = axes.shape[0]
+    vol = 4.0 / 3.0 * math.pi * np.prod(axes, axis=1)
+
+    def inside_points(idx):
+        m = idx.size
+        d = rng.normal(size=(m, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        r = rng.uniform(0.0, 1.0, m) ** (1.0 / 3.0)
+        local = d * r[:, None] * axes[idx]
+        return centre[idx] + np.einsum("nij,nj->ni", rot[idx], local)
+
+    v_union = 0.0
+    for e in range(k):
+        x = inside_points(np.full(4096, e))
+        cover = np.zeros(x.shape[0])
+        for a, r, c in zip(axes, rot, centre):
+            cover += np.sum((((x - c) @ r) / a) ** 2, axis=1) <= 1.0
+        v_union += vol[e] * float(np.mean(1.0 / np.maximum(cover, 1.0)))
+    h = (v_union / n) ** (1.0 / 3.0)
+    w = dens * vol
+    which = rng.choice(k, size=n, p=w / w.sum())
+    mu = inside_points(which)
+    ls = rng.normal(math.log(h), log_sigma_std, size=(n, 3))
+    q = _random_quaternions(rng, n)
+    rho = _phantom_density(ph, mu) * h ** 3 / ((2.0 * math.pi) ** 1.5 * np.exp(ls.sum(axis=1)))
+    return dict(mu=mu.astype(np.float32), ls=ls.astype(np.float32), q=q,
+                rho=rho.astype(np.float32), h=h)
 
 
 def perturbed(gs: dict, seed: int, pos_std: float, ls_std: float = 0.05) -> dict:
