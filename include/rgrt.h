@@ -151,6 +151,20 @@ int64_t gaussians_count(const rgrt_gauss *g);
  * degenerate constants (dsd <= dso <= 0, radius^2 < s^2 of a bin, ...). */
 int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *desc, rgrt_geom **out);
 int geometry_destroy(rgrt_geom *g);
+/* Explicit rays (any set of lines, e.g. a helical cone-beam trajectory or
+ * list-mode events): ray r is the line through o3[3r..3r+2] along
+ * d3[3r..3r+2] (any nonzero length; the library normalises it), integrated
+ * over t in [t2[2r], t2[2r+1]], t measured along the unit direction from o
+ * (either end may be infinite).  The arrays may be host or device memory and
+ * are copied.  Projections I[n_rays] follow the rays' order; consecutive rays
+ * are binned in blocks of 128, so keeping neighbouring rays close makes the
+ * binning tight (incoherent rays still give the exact result, more slowly).
+ * Explicit-ray geometries work with every projector call except the batch
+ * calls.  RGRT_E_INVAL for n_rays <= 0, a null array, a non-finite origin, a
+ * zero or non-finite direction, or a NaN or reversed segment.  This is the
+ * ray-level form of Eq. 3 (o + t d) with no detector structure. */
+int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
+                      const float *t2, rgrt_geom **out);
 int64_t geometry_num_rays(const rgrt_geom *g);
 
 /* ---- projector (Eqs. 4, 11, 12) ------------------------------------- */

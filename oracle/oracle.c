@@ -551,6 +551,59 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
     free(P);
 }
 
+/* one Gaussian's gradient sums: unambiguous pairs (gm, gP, grho, chained at
+ * the end) and, per parameter, the nominal / negative / positive sums of the
+ * pairs within the band of the cut (each chained on its own) */
+typedef struct {
+    double gm[3], gP[3][3], grho;
+    double bnom[11], bneg[11], bpos[11];
+} og_gradacc;
+
+static void og_grad_pair(og_gradacc *a, const double o[3], const double d[3], double ta, double tb,
+                         const double m3[3], double P[3][3], double rho, double w, double cut2,
+                         double band, const float *ls, const float *q)
+{
+    og_pairval r;
+    og_eval(o, d, ta, tb, m3, P, rho, &r);
+    if (!(r.m <= cut2 + band) || w == 0.0) return;
+    if (r.m <= cut2 - band) {
+        og_pair_grad(o, d, ta, tb, m3, P, rho, w, &r, a->gm, a->gP, &a->grho);
+        return;
+    }
+    /* ambiguous pair: its own full parameter gradient */
+    double bm[3] = { 0, 0, 0 }, bP[3][3] = { { 0 } }, br = 0.0, bl[3], bq[4], b[11];
+    og_pair_grad(o, d, ta, tb, m3, P, rho, w, &r, bm, bP, &br);
+    og_chain(ls, q, bP, bl, bq);
+    for (int c = 0; c < 3; c++) { b[c] = bm[c]; b[3 + c] = bl[c]; }
+    for (int c = 0; c < 4; c++) b[6 + c] = bq[c];
+    b[10] = br;
+    for (int c = 0; c < 11; c++) {
+        if (r.m <= cut2) a->bnom[c] += b[c];
+        if (b[c] < 0) a->bneg[c] += b[c]; else a->bpos[c] += b[c];
+    }
+}
+
+static void og_grad_finish(og_gradacc *a, int64_t k, const float *ls, const float *q, double *g_mu,
+                           double *g_ls, double *g_q, double *g_rho, double *lohi)
+{
+    double gl[3], gq[4], mainv[11];
+    og_chain(ls, q, a->gP, gl, gq);
+    for (int c = 0; c < 3; c++) { mainv[c] = a->gm[c]; mainv[3 + c] = gl[c]; }
+    for (int c = 0; c < 4; c++) mainv[6 + c] = gq[c];
+    mainv[10] = a->grho;
+    for (int c = 0; c < 3; c++) {
+        g_mu[3 * k + c] = mainv[c] + a->bnom[c];
+        g_ls[3 * k + c] = mainv[3 + c] + a->bnom[3 + c];
+    }
+    for (int c = 0; c < 4; c++) g_q[4 * k + c] = mainv[6 + c] + a->bnom[6 + c];
+    g_rho[k] = mainv[10] + a->bnom[10];
+    if (lohi)
+        for (int c = 0; c < 11; c++) {
+            lohi[22 * k + c] = mainv[c] + a->bneg[c];
+            lohi[22 * k + 11 + c] = mainv[c] + a->bpos[c];
+        }
+}
+
 /*
  * adjoint: dL/d(mu, l, q, rho) = sum over pairs with m <= cut2 of
  * dLdI[ray] * d(contribution)/d(parameter).  sel (length nsel) restricts the
@@ -576,8 +629,8 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
         double Sig[3][3], P[3][3];
         og_cov(ls + 3 * k, q + 4 * k, Sig, P);
         double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
-        double gm[3] = { 0, 0, 0 }, gP[3][3] = { { 0 } }, grho = 0.0, gl[3], gq[4];
-        double bnom[11] = { 0 }, bneg[11] = { 0 }, bpos[11] = { 0 };
+        og_gradacc acc;
+        memset(&acc, 0, sizeof(acc));
         for (int v = 0; v < g->n_views; v++) {
             int i0 = 0, i1 = g->n_cols - 1, j0 = 0, j1 = g->n_rows - 1;
             if (!brute) og_bbox(g, v, m3, Sig, og_box_k2(cut2, band), ut, vt, &i0, &i1, &j0, &j1);
@@ -585,43 +638,76 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
                     og_ray(g, v, j, i, o, d, &ta, &tb);
-                    og_pairval r;
-                    og_eval(o, d, ta, tb, m3, P, rho[k], &r);
-                    if (!(r.m <= cut2 + band)) continue;
-                    double w = dLdI[og_index(g, v, j, i)];
-                    if (w == 0.0) continue;
-                    if (r.m <= cut2 - band) {
-                        og_pair_grad(o, d, ta, tb, m3, P, rho[k], w, &r, gm, gP, &grho);
-                        continue;
-                    }
-                    /* ambiguous pair: its own full parameter gradient */
-                    double bm[3] = { 0, 0, 0 }, bP[3][3] = { { 0 } }, br = 0.0, bl[3], bq[4], b[11];
-                    og_pair_grad(o, d, ta, tb, m3, P, rho[k], w, &r, bm, bP, &br);
-                    og_chain(ls + 3 * k, q + 4 * k, bP, bl, bq);
-                    for (int c = 0; c < 3; c++) { b[c] = bm[c]; b[3 + c] = bl[c]; }
-                    for (int c = 0; c < 4; c++) b[6 + c] = bq[c];
-                    b[10] = br;
-                    for (int c = 0; c < 11; c++) {
-                        if (r.m <= cut2) bnom[c] += b[c];
-                        if (b[c] < 0) bneg[c] += b[c]; else bpos[c] += b[c];
-                    }
+                    og_grad_pair(&acc, o, d, ta, tb, m3, P, rho[k], dLdI[og_index(g, v, j, i)], cut2,
+                                 band, ls + 3 * k, q + 4 * k);
                 }
         }
-        og_chain(ls + 3 * k, q + 4 * k, gP, gl, gq);
-        double mainv[11];
-        for (int c = 0; c < 3; c++) { mainv[c] = gm[c]; mainv[3 + c] = gl[c]; }
-        for (int c = 0; c < 4; c++) mainv[6 + c] = gq[c];
-        mainv[10] = grho;
-        for (int c = 0; c < 3; c++) { g_mu[3 * k + c] = mainv[c] + bnom[c]; g_ls[3 * k + c] = mainv[3 + c] + bnom[3 + c]; }
-        for (int c = 0; c < 4; c++) g_q[4 * k + c] = mainv[6 + c] + bnom[6 + c];
-        g_rho[k] = mainv[10] + bnom[10];
-        if (lohi)
-            for (int c = 0; c < 11; c++) {
-                lohi[22 * k + c] = mainv[c] + bneg[c];
-                lohi[22 * k + 11 + c] = mainv[c] + bpos[c];
-            }
+        og_grad_finish(&acc, k, ls + 3 * k, q + 4 * k, g_mu, g_ls, g_q, g_rho, lohi);
     }
     free(ut); free(vt);
+}
+
+/*
+ * Explicit rays (any set of lines): ray r runs through o[3r..3r+2] along
+ * d[3r..3r+2] (any nonzero length; normalised here), over t in
+ * [t[2r], t[2r+1]] measured along the unit direction (+-inf allowed).
+ * Every (ray, Gaussian) pair is evaluated: the plain definition, Eqs. 7-12
+ * with the cut m <= cut2 and the band bracket as above.
+ */
+static void og_list_ray(const double *o, const double *d, const double *t, int64_t r,
+                        double oo[3], double dd[3], double *ta, double *tb)
+{
+    double len = sqrt(d[3 * r] * d[3 * r] + d[3 * r + 1] * d[3 * r + 1] + d[3 * r + 2] * d[3 * r + 2]);
+    for (int c = 0; c < 3; c++) { oo[c] = o[3 * r + c]; dd[c] = d[3 * r + c] / len; }
+    *ta = t[2 * r];
+    *tb = t[2 * r + 1];
+}
+
+void or_forward_list(int64_t nr, const double *o, const double *d, const double *t, int64_t n,
+                     const float *mu, const float *ls, const float *q, const float *rho, double cut2,
+                     double band, int nthreads, double *I, double *Ilo, double *Ihi, int64_t *pairs)
+{
+    og_set_threads(nthreads);
+    double (*P)[3][3] = malloc(sizeof(double[3][3]) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; k++) { double S[3][3]; og_cov(ls + 3 * k, q + 4 * k, S, P[k]); }
+    int64_t npair = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : npair)
+    for (int64_t r = 0; r < nr; r++) {
+        double oo[3], dd[3], ta, tb, s = 0.0, slo = 0.0, shi = 0.0;
+        og_list_ray(o, d, t, r, oo, dd, &ta, &tb);
+        for (int64_t k = 0; k < n; k++) {
+            double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
+            og_pairval pv;
+            og_eval(oo, dd, ta, tb, m3, P[k], rho[k], &pv);
+            og_accum(pv.f, pv.m, cut2, band, &s, &slo, &shi);
+            if (pv.m <= cut2) npair++;
+        }
+        I[r] = s; Ilo[r] = slo; Ihi[r] = shi;
+    }
+    if (pairs) *pairs = npair;
+    free(P);
+}
+
+void or_backward_list(int64_t nr, const double *o, const double *d, const double *t, int64_t n,
+                      const float *mu, const float *ls, const float *q, const float *rho, double cut2,
+                      double band, const double *dLdI, int nthreads, double *g_mu, double *g_ls,
+                      double *g_q, double *g_rho, double *lohi)
+{
+    og_set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; k++) {
+        double Sig[3][3], P[3][3];
+        og_cov(ls + 3 * k, q + 4 * k, Sig, P);
+        double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
+        og_gradacc acc;
+        memset(&acc, 0, sizeof(acc));
+        for (int64_t r = 0; r < nr; r++) {
+            double oo[3], dd[3], ta, tb;
+            og_list_ray(o, d, t, r, oo, dd, &ta, &tb);
+            og_grad_pair(&acc, oo, dd, ta, tb, m3, P, rho[k], dLdI[r], cut2, band, ls + 3 * k, q + 4 * k);
+        }
+        og_grad_finish(&acc, k, ls + 3 * k, q + 4 * k, g_mu, g_ls, g_q, g_rho, lohi);
+    }
 }
 
 /* ------------------------------------------------------------------ */

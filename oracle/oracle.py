@@ -219,6 +219,46 @@ def backward(geom, G, dLdI, sel=None, cut2=CUT2, band=BAND, brute=False, nthread
     return dict(mu=gm, ls=gl, q=gq, rho=gr, lo=split(lohi[:, :11]), hi=split(lohi[:, 11:]))
 
 
+def _ray_arrays(o, d, t):
+    o = _f64(o).reshape(-1, 3)
+    d = _f64(d).reshape(-1, 3)
+    t = _f64(t).reshape(-1, 2)
+    assert o.shape[0] == d.shape[0] == t.shape[0]
+    return o, d, t
+
+
+def forward_list(o, d, t, G, cut2=CUT2, band=BAND, nthreads=0):
+    """FP64 projection of explicit rays (o[R,3], d[R,3] any length, t[R,2]
+    along the unit direction): dict(I, I_lo, I_hi, pairs); every pair evaluated."""
+    o, d, t = _ray_arrays(o, d, t)
+    nr = o.shape[0]
+    n, mu, ls, q, rho = _gauss(G)
+    I = np.zeros(nr); Ilo = np.zeros(nr); Ihi = np.zeros(nr)
+    pairs = ctypes.c_int64(0)
+    lib().or_forward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), ctypes.c_int64(n), _p(mu), _p(ls),
+                          _p(q), _p(rho), ctypes.c_double(cut2), ctypes.c_double(band),
+                          ctypes.c_int(nthreads), _p(I), _p(Ilo), _p(Ihi), ctypes.byref(pairs))
+    return dict(I=I, I_lo=Ilo, I_hi=Ihi, pairs=int(pairs.value))
+
+
+def backward_list(o, d, t, G, dLdI, cut2=CUT2, band=BAND, nthreads=0):
+    """FP64 adjoint for explicit rays; same outputs as backward()."""
+    o, d, t = _ray_arrays(o, d, t)
+    nr = o.shape[0]
+    n, mu, ls, q, rho = _gauss(G)
+    w = _f64(dLdI).reshape(-1)
+    assert w.size == nr
+    gm = np.zeros((n, 3)); gl = np.zeros((n, 3)); gq = np.zeros((n, 4)); gr = np.zeros(n)
+    lohi = np.zeros((n, 22))
+    lib().or_backward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), ctypes.c_int64(n), _p(mu), _p(ls),
+                           _p(q), _p(rho), ctypes.c_double(cut2), ctypes.c_double(band), _p(w),
+                           ctypes.c_int(nthreads), _p(gm), _p(gl), _p(gq), _p(gr), _p(lohi))
+
+    def split(a):
+        return dict(mu=a[:, 0:3], ls=a[:, 3:6], q=a[:, 6:10], rho=a[:, 10])
+    return dict(mu=gm, ls=gl, q=gq, rho=gr, lo=split(lohi[:, :11]), hi=split(lohi[:, 11:]))
+
+
 # ---------------------------------------------------------------------------
 # FP32 culling specification (bit-exact tile lists)
 # ---------------------------------------------------------------------------

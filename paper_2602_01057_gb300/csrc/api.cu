@@ -320,9 +320,117 @@ int check_ctx(rgrt_ctx *c)
     return RGRT_OK;
 }
 
+// ---- explicit rays --------------------------------------------------------
+
+// balls, scene box, block lines and per-block counts, then split the blocks
+// into consecutive ranges whose lists fit the budget; body(b0, nb) runs after
+// each range's lists are built.  reuse: keep cached lists of a single range.
+template <class F>
+int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cudaStream_t s,
+                   bool reuse, F body)
+{
+    const int64_t N = g->n;
+    const int T = geom->n_blocks;
+    if (reuse && ctx->bin_valid && ctx->bin_g == g && ctx->bin_geom == geom &&
+        ctx->bin_version == g->version && ctx->bin_v0 == 0 && ctx->bin_nv == T)
+        return body(0, T);
+    ctx->bin_valid = false;
+    const int parts = rays_ball_parts(N);
+    TRY(ensure(ctx, ctx->ball, sizeof(float4) * (size_t)N));
+    TRY(ensure(ctx, ctx->part, sizeof(float4) * 2 * (size_t)parts));
+    TRY(ensure(ctx, ctx->scene, sizeof(float4) * 2));
+    TRY(ensure(ctx, ctx->blk, sizeof(float4) * 2 * (size_t)T));
+    TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)T));
+    TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)T));
+    TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)T));
+    TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems(T)));
+    TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
+    {
+        PROF("rays_bin");
+        CK(launch_rays_bin(geom->d_ro, geom->d_rd, geom->n_rays, g->rec, N, (float4 *)ctx->ball.p,
+                           (float4 *)ctx->part.p, (float4 *)ctx->scene.p, (float4 *)ctx->blk.p,
+                           (uint32_t *)ctx->cnt.p, s));
+    }
+    ctx->h_cnt.resize((size_t)T);
+    CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * (size_t)T,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // list capacity: what the budget leaves (the current list buffer included)
+    size_t avail = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
+    avail += ctx->vals.bytes;
+    avail = avail > ((size_t)1 << 20) ? avail - ((size_t)1 << 20) : 0;
+    uint64_t cap = avail / sizeof(uint32_t);
+    if (cap > 0x7fffffffull) cap = 0x7fffffffull;
+    std::vector<std::pair<int, int>> rng;
+    uint64_t acc = 0, total = 0;
+    int b0 = 0;
+    for (int b = 0; b < T; b++) {
+        const uint64_t c = ctx->h_cnt[(size_t)b];
+        if (c > cap)
+            return fail(RGRT_E_CAPACITY, "ray block %d lists %llu Gaussians, over the budget", b,
+                        (unsigned long long)c);
+        if (acc + c > cap) {
+            rng.push_back({ b0, b - b0 });
+            b0 = b;
+            acc = 0;
+        }
+        acc += c;
+        total += c;
+    }
+    rng.push_back({ b0, T - b0 });
+    uint64_t kmax = 0;
+    for (auto &r : rng) {
+        uint64_t k = 0;
+        for (int b = r.first; b < r.first + r.second; b++) k += ctx->h_cnt[(size_t)b];
+        kmax = k > kmax ? k : kmax;
+    }
+    TRY(ensure(ctx, ctx->vals, sizeof(uint32_t) * (size_t)(kmax > 0 ? kmax : 1)));
+    ctx->last_keys += (long long)total;
+    for (auto &r : rng) {
+        {
+            PROF("rays_emit");
+            CK(launch_scan((const uint32_t *)ctx->cnt.p + r.first, (uint32_t *)ctx->off.p, r.second,
+                           (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
+            CK(launch_rays_emit((const float4 *)ctx->blk.p, (const float4 *)ctx->ball.p, N, r.first,
+                                r.second, (const uint32_t *)ctx->off.p, (const uint32_t *)ctx->cnt.p,
+                                (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p, s));
+        }
+        if (rng.size() == 1) {
+            ctx->bin_g = g;
+            ctx->bin_geom = geom;
+            ctx->bin_version = g->version;
+            ctx->bin_v0 = 0;
+            ctx->bin_nv = T;
+            ctx->bin_valid = true;
+        }
+        TRY(body(r.first, r.second));
+    }
+    return RGRT_OK;
+}
+
+int run_forward_rays(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out,
+                     cudaStream_t s)
+{
+    TRY(build_records(ctx, g, s));
+    ctx->last_keys = 0;
+    return for_ray_ranges(ctx, g, geom, s, false, [&](int b0, int nb) -> int {
+        PROF("k_rays_forward");
+        CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
+                               (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, s));
+        return RGRT_OK;
+    });
+}
+
 int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out,
                 cudaStream_t s)
 {
+    if (geom->rays) {
+        if (g->n == 0) {
+            CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)geom->n_rays, s));
+            return RGRT_OK;
+        }
+        return run_forward_rays(ctx, g, geom, out, s);
+    }
     if (g->n == 0) {
         CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)geom->n_rays, s));
         return RGRT_OK;
@@ -358,6 +466,18 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
     bool reuse = ctx->bin_valid && ctx->bin_g == g && ctx->bin_geom == geom &&
                  ctx->bin_version == g->version;
     if (!reuse) TRY(build_records(ctx, g, s));
+    if (geom->rays) {
+        TRY(for_ray_ranges(ctx, g, geom, s, reuse, [&](int b0, int nb) -> int {
+            PROF("k_rays_adjoint");
+            CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
+                                   (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, dLdI,
+                                   (float4 *)ctx->grad.p, s));
+            return RGRT_OK;
+        }));
+        PROF("k_param_chain");
+        CK(launch_param_chain(g->mu, g->ls, g->q, g->rho, N, (float4 *)ctx->grad.p, gm, gl, gq, gr, s));
+        return RGRT_OK;
+    }
     TRY(for_chunks(ctx, g, geom, s, reuse, [&](int v0, int nv, uint32_t K) -> int {
         (void)K;
         DevGeom dg = geom->dg;
@@ -483,7 +603,8 @@ int rgrt_ctx_destroy(rgrt_ctx *c)
     prof_harvest(c);
     Buf *bufs[] = { &c->cnt, &c->off, &c->rect, &c->keys, &c->vals, &c->keys_alt, &c->vals_alt,
                     &c->sort_tmp, &c->scan_tmp, &c->ranges, &c->total, &c->I, &c->dLdI, &c->y,
-                    &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss };
+                    &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss, &c->ball, &c->part,
+                    &c->scene, &c->blk };
     for (Buf *b : bufs) release(c, *b);
     for (auto &b : c->stage_in) release(c, b);
     for (auto &b : c->stage_out) release(c, b);
@@ -686,8 +807,65 @@ int geometry_destroy(rgrt_geom *g)
     rgrt_ctx *c = g->ctx;
     cudaSetDevice(c->device);
     if (c->bin_geom == g) c->bin_valid = false;
-    dev_free(c, g->d_tables, g->bytes);
+    if (g->rays) {
+        dev_free(c, g->d_ro, sizeof(float4) * (size_t)g->n_rays);
+        dev_free(c, g->d_rd, sizeof(float4) * (size_t)g->n_rays);
+    } else {
+        dev_free(c, g->d_tables, g->bytes);
+    }
     delete g;
+    return RGRT_OK;
+}
+
+int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
+                      const float *t2, rgrt_geom **out)
+{
+    TRY(check_ctx(ctx));
+    if (!out) return fail(RGRT_E_INVAL, "null output");
+    *out = nullptr;
+    if (n_rays <= 0) return fail(RGRT_E_INVAL, "n_rays must be positive (%lld)", (long long)n_rays);
+    if (!o3 || !d3 || !t2) return fail(RGRT_E_INVAL, "null ray array");
+    if ((n_rays + 127) / 128 > 0x7fffffffLL) return fail(RGRT_E_INVAL, "too many rays");
+    rgrt_geom *g = new (std::nothrow) rgrt_geom();
+    if (!g) return fail(RGRT_E_NOMEM, "host allocation failed");
+    g->ctx = ctx;
+    g->rays = true;
+    g->n_rays = n_rays;
+    g->n_blocks = rays_blocks(n_rays);
+    g->desc.n_views = 1;
+    g->desc.n_rows = 1;
+    g->desc.n_cols = 0;
+    cudaStream_t s = nullptr;
+    const size_t nb = sizeof(float4) * (size_t)n_rays;
+    int r = dev_alloc(ctx, (void **)&g->d_ro, nb);
+    if (r == RGRT_OK) r = dev_alloc(ctx, (void **)&g->d_rd, nb);
+    const void *po = nullptr, *pd = nullptr, *pt = nullptr;
+    if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[0], o3, 3 * sizeof(float) * (size_t)n_rays, s, &po);
+    if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[1], d3, 3 * sizeof(float) * (size_t)n_rays, s, &pd);
+    if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[2], t2, 2 * sizeof(float) * (size_t)n_rays, s, &pt);
+    if (r == RGRT_OK) r = ensure(ctx, ctx->total, sizeof(unsigned long long) * 2);
+    if (r == RGRT_OK) {
+        uint32_t bad = 0;
+        cudaError_t e = cudaMemsetAsync(ctx->total.p, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess)
+            e = launch_rays_prep((const float *)po, (const float *)pd, (const float *)pt, n_rays, g->d_ro,
+                                 g->d_rd, (uint32_t *)ctx->total.p, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            r = fail(RGRT_E_CUDA, "preparing rays: %s", cudaGetErrorString(e));
+        else if (bad)
+            r = fail(RGRT_E_INVAL, "a ray has a non-finite origin, a zero or non-finite direction, or "
+                                   "a segment with t_a > t_b or NaN");
+    }
+    for (int k = 0; k < 3; k++) release(ctx, ctx->stage_in[k]);  // staged copies are not kept
+    if (r != RGRT_OK) {
+        if (g->d_ro) dev_free(ctx, g->d_ro, nb);
+        if (g->d_rd) dev_free(ctx, g->d_rd, nb);
+        delete g;
+        return r;
+    }
+    *out = g;
     return RGRT_OK;
 }
 

@@ -341,6 +341,10 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g, const rg
             delete b;
             return report_error(RGRT_E_INVAL, "batch scan with a null handle or one of another context");
         }
+        if (geom[i]->rays) {
+            delete b;
+            return report_error(RGRT_E_INVAL, "explicit-ray geometries are not batched");
+        }
         const DevGeom &dg = geom[i]->dg;
         const bool cone = dg.kind == 1;
         if (i == 0) {
@@ -478,10 +482,14 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
     static const int cand[][2] = { { 16, 16 }, { 16, 8 }, { 8, 8 }, { 32, 8 } };
     rgrt_geom_desc sub = *desc;
     std::vector<double> ang;
-    if (desc->kind != RGRT_GEOM_PET_RING && max_views > 0 && max_views < desc->n_views) {
-        // evenly spaced subset of the views (PET angles are implied by their count: all are kept)
-        for (int k = 0; k < max_views; k++)
-            ang.push_back(desc->angles[(int64_t)k * desc->n_views / max_views]);
+    if (max_views > 0 && max_views < desc->n_views) {
+        // evenly spaced subset of the views (a PET sinogram without explicit
+        // angles spaces its angles pi j / n_views)
+        for (int k = 0; k < max_views; k++) {
+            const int64_t j = (int64_t)k * desc->n_views / max_views;
+            ang.push_back(desc->angles ? desc->angles[j]
+                                       : 3.14159265358979323846 * (double)j / (double)desc->n_views);
+        }
         sub.angles = ang.data();
         sub.n_views = max_views;
     }

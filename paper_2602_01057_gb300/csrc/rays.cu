@@ -1,0 +1,427 @@
+// Explicit rays: any set of lines (o, d, [t_a, t_b]) given by the caller, e.g.
+// a helical cone-beam trajectory or a list-mode PET event set, projected with
+// the closed form of Eqs. 7-12 (general path, world coordinates).
+//
+// Rays are grouped in blocks of RB consecutive rays (one CTA, one ray per
+// thread); a caller whose neighbouring rays are close gets tight blocks.
+// Binning per projection:
+//  * every Gaussian gets a bounding ball (mu, K sigma_max), K^2 = 9.0625: its
+//    K-sigma ellipsoid -- which holds every point where m <= 9 -- lies inside
+//    it; the scene box is the union of the balls;
+//  * every block gets a reference line L0 (one of its rays, re-based at the
+//    point nearest the scene centre) and dev = the largest distance from L0 of
+//    the end points of its rays' lines clipped to the scene box.  A line that
+//    meets a Gaussian's ellipsoid does so inside the scene box, at a point no
+//    further than dev from L0 (distance to a line is convex along a segment),
+//    so the Gaussian can pair with the block only if
+//        dist(mu, L0) <= K sigma_max + dev;
+//  * per block, a pass over all Gaussians counts and then emits, in ascending
+//    Gaussian order, those passing that test.
+// Integration and adjoint then walk a block's list in shared-memory chunks.
+#include "pair.cuh"
+
+namespace rgrt {
+namespace {
+
+constexpr int RB = 128;    // rays per block
+constexpr int RCH = 128;   // records per shared-memory chunk
+constexpr int CULL_BS = 256;
+constexpr int NG_RAYS = 10;  // general_grad components: dmu[3], G_P[6], drho
+
+struct SRec {
+    float4 g0, g1, g2;     // (mu, rho), (P00 P01 P02 P11), (P12 P22, -, -)
+};
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float norm2(float3 a) { return a.x * a.x + a.y * a.y + a.z * a.z; }
+
+// normalise d, re-base o at the point of the line nearest the world origin
+// (FP64, once per ray), shift the segment accordingly; flag invalid rays
+__global__ void k_rays_prep(const float *__restrict__ o3, const float *__restrict__ d3,
+                            const float *__restrict__ t2, int64_t n, float4 *ro, float4 *rd,
+                            uint32_t *bad)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double ox = o3[3 * r], oy = o3[3 * r + 1], oz = o3[3 * r + 2];
+    const double dx = d3[3 * r], dy = d3[3 * r + 1], dz = d3[3 * r + 2];
+    const double ta = t2[2 * r], tb = t2[2 * r + 1];
+    const double len = sqrt(dx * dx + dy * dy + dz * dz);
+    const bool ok = isfinite(ox) && isfinite(oy) && isfinite(oz) && isfinite(len) && len > 0.0 &&
+                    !isnan(ta) && !isnan(tb) && ta <= tb;
+    if (!ok) {
+        atomicOr(bad, 1u);
+        ro[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        rd[r] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+        return;
+    }
+    const double ux = dx / len, uy = dy / len, uz = dz / len;
+    const double s = ox * ux + oy * uy + oz * uz;   // o = o' + s u
+    ro[r] = make_float4((float)(ox - s * ux), (float)(oy - s * uy), (float)(oz - s * uz), (float)(ta + s));
+    rd[r] = make_float4((float)ux, (float)uy, (float)uz, (float)(tb + s));
+}
+
+// bounding balls (mu, K sigma_max) and per-CTA partial scene boxes
+__global__ void k_balls(const float4 *__restrict__ rec, int64_t n, float4 *ball, float4 *part)
+{
+    __shared__ float red[6][CULL_BS / 32];
+    float lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    const float K = sqrtf(CULL_K2) * (1.0f + 1e-5f);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 m = __ldg(rec + REC_F4 * k);
+        const float r = K * __ldg(rec + REC_F4 * k + 4).x;
+        ball[k] = make_float4(m.x, m.y, m.z, r);
+        lo[0] = fminf(lo[0], m.x - r); hi[0] = fmaxf(hi[0], m.x + r);
+        lo[1] = fminf(lo[1], m.y - r); hi[1] = fmaxf(hi[1], m.y + r);
+        lo[2] = fminf(lo[2], m.z - r); hi[2] = fmaxf(hi[2], m.z + r);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 3; c++) {
+            lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+            hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+        }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; c++) { red[c][w] = lo[c]; red[3 + c][w] = hi[c]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < CULL_BS / 32; j++)
+            for (int c = 0; c < 3; c++) {
+                red[c][0] = fminf(red[c][0], red[c][j]);
+                red[3 + c][0] = fmaxf(red[3 + c][0], red[3 + c][j]);
+            }
+        part[2 * blockIdx.x] = make_float4(red[0][0], red[1][0], red[2][0], 0.0f);
+        part[2 * blockIdx.x + 1] = make_float4(red[3][0], red[4][0], red[5][0], 0.0f);
+    }
+}
+
+// scene box from the partials, widened by a margin; also the margin
+// (scene[0].w) used by the block test
+__global__ void k_scene(const float4 *part, int nparts, float4 *scene)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int j = 0; j < nparts; j++) {
+        const float4 a = part[2 * j], b = part[2 * j + 1];
+        lo[0] = fminf(lo[0], a.x); lo[1] = fminf(lo[1], a.y); lo[2] = fminf(lo[2], a.z);
+        hi[0] = fmaxf(hi[0], b.x); hi[1] = fmaxf(hi[1], b.y); hi[2] = fmaxf(hi[2], b.z);
+    }
+    float ext = 0.0f;
+    for (int c = 0; c < 3; c++) ext = fmaxf(ext, fmaxf(fabsf(lo[c]), fabsf(hi[c])));
+    // FP32 slack of the clipping and distance arithmetic (a few ulp of the
+    // largest coordinate), generously
+    const float eps = ext * 6.1e-5f + 1e-30f;
+    scene[0] = make_float4(lo[0] - eps, lo[1] - eps, lo[2] - eps, eps);
+    scene[1] = make_float4(hi[0] + eps, hi[1] + eps, hi[2] + eps, 0.0f);
+}
+
+// clip the line (o + t d) to the box; false if it misses
+__device__ __forceinline__ bool clip_line(float3 o, float3 d, float4 lo, float4 hi, float &t0, float &t1)
+{
+    t0 = -INFINITY;
+    t1 = INFINITY;
+    const float oo[3] = { o.x, o.y, o.z }, dd[3] = { d.x, d.y, d.z };
+    const float ll[3] = { lo.x, lo.y, lo.z }, hh[3] = { hi.x, hi.y, hi.z };
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (dd[c] == 0.0f) {
+            if (oo[c] < ll[c] || oo[c] > hh[c]) return false;
+        } else {
+            const float inv = 1.0f / dd[c];
+            const float a = (ll[c] - oo[c]) * inv, b = (hh[c] - oo[c]) * inv;
+            t0 = fmaxf(t0, fminf(a, b));
+            t1 = fminf(t1, fmaxf(a, b));
+        }
+    }
+    return t0 <= t1;
+}
+
+// per block: reference line (p0, d0) and deviation dev; blk[2b] = (p0, dev),
+// blk[2b+1] = (d0, 1) or (0, 0, 0, 0) for a block none of whose lines meets
+// the scene box
+__global__ void __launch_bounds__(RB) k_ray_blocks(const float4 *__restrict__ ro,
+                                                   const float4 *__restrict__ rd, int64_t n,
+                                                   const float4 *__restrict__ scene, float4 *blk)
+{
+    __shared__ int s_hit[RB];
+    __shared__ float s_dev[RB / 32];
+    __shared__ float4 s_ref[2];
+    const int64_t r = blockIdx.x * (int64_t)RB + threadIdx.x;
+    const float4 lo = scene[0], hi = scene[1];
+    float3 o = make_float3(0.0f, 0.0f, 0.0f), d = make_float3(0.0f, 0.0f, 1.0f);
+    float t0 = 0.0f, t1 = 0.0f;
+    bool hit = false;
+    if (r < n) {
+        const float4 a = __ldg(ro + r), b = __ldg(rd + r);
+        o = make_float3(a.x, a.y, a.z);
+        d = make_float3(b.x, b.y, b.z);
+        hit = clip_line(o, d, lo, hi, t0, t1);
+    }
+    s_hit[threadIdx.x] = hit;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ref = -1;
+        for (int j = 0; j < RB && ref < 0; j++) {
+            const int k = (j + RB / 2) % RB;
+            if (s_hit[k]) ref = k;
+        }
+        if (ref < 0) {
+            s_ref[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            s_ref[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            const int64_t rr = blockIdx.x * (int64_t)RB + ref;
+            const float4 a = __ldg(ro + rr), b = __ldg(rd + rr);
+            // point of the reference line nearest the scene centre
+            const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+            const float s = (cx - a.x) * b.x + (cy - a.y) * b.y + (cz - a.z) * b.z;
+            s_ref[0] = make_float4(a.x + s * b.x, a.y + s * b.y, a.z + s * b.z, 0.0f);
+            s_ref[1] = make_float4(b.x, b.y, b.z, 1.0f);
+        }
+    }
+    __syncthreads();
+    const float4 P = s_ref[0], D = s_ref[1];
+    float dev = 0.0f;
+    if (hit && D.w != 0.0f) {
+        const float3 d0 = make_float3(D.x, D.y, D.z);
+        const float3 ea = make_float3(o.x + t0 * d.x - P.x, o.y + t0 * d.y - P.y, o.z + t0 * d.z - P.z);
+        const float3 eb = make_float3(o.x + t1 * d.x - P.x, o.y + t1 * d.y - P.y, o.z + t1 * d.z - P.z);
+        dev = sqrtf(fmaxf(norm2(cross3(ea, d0)), norm2(cross3(eb, d0))));
+    }
+    for (int k = 16; k > 0; k >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, k));
+    if ((threadIdx.x & 31) == 0) s_dev[threadIdx.x >> 5] = dev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < RB / 32; j++) dev = fmaxf(dev, s_dev[j]);
+        blk[2 * blockIdx.x] = make_float4(P.x, P.y, P.z, dev + lo.w);
+        blk[2 * blockIdx.x + 1] = D;
+    }
+}
+
+// the block test, written with explicit IEEE operations so that the count
+// and emit kernels take the same decision for every (block, Gaussian)
+__device__ __forceinline__ bool block_hit(const float4 P, const float4 D, const float4 ball)
+{
+    const float vx = __fsub_rn(ball.x, P.x), vy = __fsub_rn(ball.y, P.y), vz = __fsub_rn(ball.z, P.z);
+    const float cx = __fsub_rn(__fmul_rn(vy, D.z), __fmul_rn(vz, D.y));
+    const float cy = __fsub_rn(__fmul_rn(vz, D.x), __fmul_rn(vx, D.z));
+    const float cz = __fsub_rn(__fmul_rn(vx, D.y), __fmul_rn(vy, D.x));
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
+    const float R = __fadd_rn(ball.w, P.w);
+    return d2 <= __fmul_rn(R, R);
+}
+
+__global__ void __launch_bounds__(CULL_BS) k_rays_count(const float4 *__restrict__ blk,
+                                                        const float4 *__restrict__ ball, int64_t n,
+                                                        uint32_t *cnt)
+{
+    __shared__ uint32_t s_c[CULL_BS / 32];
+    const float4 P = blk[2 * blockIdx.x], D = blk[2 * blockIdx.x + 1];
+    uint32_t c = 0;
+    if (D.w != 0.0f)
+        for (int64_t k = threadIdx.x; k < n; k += CULL_BS) c += block_hit(P, D, __ldg(ball + k));
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int j = 0; j < CULL_BS / 32; j++) t += s_c[j];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// blocks b0 .. b0 + gridDim.x - 1; off[] relative to the range
+__global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict__ blk,
+                                                       const float4 *__restrict__ ball, int64_t n,
+                                                       int64_t b0, const uint32_t *__restrict__ off,
+                                                       const uint32_t *__restrict__ cnt,
+                                                       uint32_t *gids, uint2 *ranges)
+{
+    __shared__ uint32_t s_w[CULL_BS / 32];
+    const int64_t b = b0 + blockIdx.x;
+    const float4 P = blk[2 * b], D = blk[2 * b + 1];
+    const uint32_t beg = off[blockIdx.x], num = cnt[b];
+    if (threadIdx.x == 0) ranges[blockIdx.x] = make_uint2(beg, beg + num);
+    if (D.w == 0.0f || num == 0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t pos = beg;
+    for (int64_t base = 0; base < n; base += CULL_BS) {
+        const int64_t k = base + threadIdx.x;
+        const bool h = k < n && block_hit(P, D, __ldg(ball + k));
+        const uint32_t bal = __ballot_sync(0xffffffffu, h);
+        if (lane == 0) s_w[w] = __popc(bal);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int j = 0; j < CULL_BS / 32; j++) {
+            before += j < w ? s_w[j] : 0u;
+            total += s_w[j];
+        }
+        const uint32_t at = pos + before + __popc(bal & ((1u << lane) - 1u));
+        if (h && at < beg + num) gids[at] = (uint32_t)k;
+        pos += total;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec,
+                                            const uint32_t *__restrict__ gids, uint32_t beg, int cnt,
+                                            SRec *sr)
+{
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t gid = __ldg(gids + beg + i);
+        const float4 *r = rec + REC_F4 * (size_t)gid;
+        const float4 r2 = __ldg(r + 2);
+        sr[i].g0 = __ldg(r);
+        sr[i].g1 = __ldg(r + 1);
+        sr[i].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), 0.0f);
+    }
+}
+
+__device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int64_t r)
+{
+    const float4 a = __ldg(ro + r), b = __ldg(rd + r);
+    Ray y;
+    y.ox = a.x; y.oy = a.y; y.oz = a.z; y.ta = a.w;
+    y.dx = b.x; y.dy = b.y; y.dz = b.z; y.tb = b.w;
+    return y;
+}
+
+// one ray per thread; blocks b0 .. b0 + gridDim.x - 1
+__global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ ro,
+                                                     const float4 *__restrict__ rd, int64_t n,
+                                                     int64_t b0, const float4 *__restrict__ rec,
+                                                     const uint32_t *__restrict__ gids,
+                                                     const uint2 *__restrict__ ranges, float *out)
+{
+    __shared__ SRec sr[RCH];
+    const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
+    const bool valid = r < n;
+    const Ray ray = load_ray(ro, rd, valid ? r : 0);
+    const uint2 rg = ranges[blockIdx.x];
+    float acc = 0.0f;
+    for (uint32_t c = rg.x; c < rg.y; c += RCH) {
+        const int cnt = (int)min((uint32_t)RCH, rg.y - c);
+        __syncthreads();
+        stage_chunk(rec, gids, c, cnt, sr);
+        __syncthreads();
+        for (int i = 0; i < cnt; i++) {
+            PairGeo q;
+            pair_geo(ray, sr[i], q);
+            if (q.m <= PAIR_CUT2) acc += general_value(q, sr[i].g0.w);
+        }
+    }
+    if (valid) out[r] = acc;
+}
+
+// one ray per thread; per Gaussian a transposed warp reduction of the pair
+// gradients and one atomic per component per warp
+__global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ ro,
+                                                     const float4 *__restrict__ rd, int64_t n,
+                                                     int64_t b0, const float4 *__restrict__ rec,
+                                                     const uint32_t *__restrict__ gids,
+                                                     const uint2 *__restrict__ ranges,
+                                                     const float *__restrict__ dLdI, float *grad)
+{
+    __shared__ SRec sr[RCH];
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
+    const bool valid = r < n;
+    const Ray ray = load_ray(ro, rd, valid ? r : 0);
+    const float w = valid ? __ldg(dLdI + r) : 0.0f;
+    const uint2 rg = ranges[blockIdx.x];
+    // accumulator slot of general_grad's components: dmu[3], G_P[6], drho
+    const int slot[NG_RAYS] = { 0, 1, 2, 4, 5, 6, 7, 8, 9, 3 };
+    for (uint32_t c = rg.x; c < rg.y; c += RCH) {
+        const int cnt = (int)min((uint32_t)RCH, rg.y - c);
+        __syncthreads();
+        stage_chunk(rec, gids, c, cnt, sr);
+        __syncthreads();
+        for (int i = 0; i < cnt; i++) {
+            PairGeo q;
+            pair_geo(ray, sr[i], q);
+            const bool act = valid && w != 0.0f && q.m <= PAIR_CUT2;
+            if (!__any_sync(0xffffffffu, act)) continue;
+            float v[NG_RAYS];
+            if (act) {
+                general_grad(ray, q, sr[i].g0.w, w, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NG_RAYS; k++) v[k] = 0.0f;
+            }
+            const int own = tr_reduce<NG_RAYS>(v, lane);
+            if (own < NG_RAYS) {
+                const uint32_t gid = __float_as_uint(sr[i].g2.z);
+                atomicAdd(grad + 4 * GRAD_F4 * (size_t)gid + slot[own], v[0]);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, int64_t n, float4 *ro,
+                             float4 *rd, uint32_t *bad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_rays_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o3, d3, t2, n, ro, rd, bad);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int rays_blocks(int64_t n) { return (int)((n + RB - 1) / RB); }
+
+int rays_ball_parts(int64_t n)
+{
+    int64_t b = (n + CULL_BS - 1) / CULL_BS;
+    return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+
+cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
+                            int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
+                            uint32_t *cnt, cudaStream_t s)
+{
+    const int parts = rays_ball_parts(n);
+    k_balls<<<parts, CULL_BS, 0, s>>>(rec, n, ball, part);
+    k_scene<<<1, 32, 0, s>>>(part, parts, scene);
+    const int T = rays_blocks(n_rays);
+    k_ray_blocks<<<T, RB, 0, s>>>(ro, rd, n_rays, scene, blk);
+    k_rays_count<<<T, CULL_BS, 0, s>>>(blk, ball, n, cnt);
+    count_launches(4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, int64_t b0, int nb,
+                             const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
+                             cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_rays_emit<<<nb, CULL_BS, 0, s>>>(blk, ball, n, b0, off, cnt, gids, ranges);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
+                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
+                                float *out, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_rays_forward<<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
+                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
+                                const float *dLdI, float4 *grad, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_rays_adjoint<<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rgrt

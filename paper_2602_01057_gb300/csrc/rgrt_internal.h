@@ -117,4 +117,27 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
                         float beta1, float beta2, float eps, float bc1, float bc2,
                         const float *bc_dev, const uint32_t *skip, cudaStream_t s);
 
+// ---- explicit rays (rays.cu) ----------------------------------------------
+// ro[r] = (o', t_a'), rd[r] = (unit d, t_b'), o' re-based at the point of the
+// line nearest the world origin; *bad |= 1 for an invalid ray
+cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, int64_t n, float4 *ro,
+                             float4 *rd, uint32_t *bad, cudaStream_t s);
+int rays_blocks(int64_t n_rays);       // ray blocks (128 rays each)
+int rays_ball_parts(int64_t n);        // partial scene boxes of the ball pass
+// balls (n float4), partial boxes (2 x parts), scene box (2), block lines
+// (2 x blocks) and per-block Gaussian counts
+cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
+                            int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
+                            uint32_t *cnt, cudaStream_t s);
+// lists of blocks b0 .. b0+nb-1 (ascending Gaussian ids) at offsets off[0..nb)
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, int64_t b0, int nb,
+                             const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
+                             cudaStream_t s);
+cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
+                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
+                                float *out, cudaStream_t s);
+cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
+                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
+                                const float *dLdI, float4 *grad, cudaStream_t s);
+
 }  // namespace rgrt

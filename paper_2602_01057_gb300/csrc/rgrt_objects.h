@@ -28,6 +28,8 @@ struct rgrt_ctx {
     // scratch
     rgrt::Buf cnt, off, rect, keys, vals, keys_alt, vals_alt, sort_tmp, scan_tmp, ranges, total;
     rgrt::Buf stage_in[4], stage_out[4], I, dLdI, y, grad, gflat, partial, stats, loss;
+    rgrt::Buf ball, part, scene, blk;          // explicit-ray binning
+    std::vector<uint32_t> h_cnt;               // per-block list lengths (explicit rays)
     unsigned long long *h_total = nullptr;  // pinned
     // binning cache
     const rgrt_gauss *bin_g = nullptr;
@@ -62,6 +64,10 @@ struct rgrt_geom {
     rgrt::DevGeom dg{};
     float *d_tables = nullptr;
     int64_t n_rays = 0;
+    // explicit rays: per ray (o', t_a') and (unit d, t_b'); ray blocks
+    bool rays = false;
+    float4 *d_ro = nullptr, *d_rd = nullptr;
+    int n_blocks = 0;
     int tiles_per_view = 0;
     size_t bytes = 0;
 };

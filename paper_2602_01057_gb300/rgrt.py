@@ -59,6 +59,7 @@ _EXPORTS = {
     "gaussians_set": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gaussians_count": ([_VP], ctypes.c_int64),
     "geometry_set": ([_VP, ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], ctypes.c_int),
+    "geometry_set_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_destroy": ([_VP], ctypes.c_int),
     "geometry_num_rays": ([_VP], ctypes.c_int64),
     "project_forward": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -146,6 +147,13 @@ def _ptr(a):
             raise ValueError("tensor must be contiguous")
         return a.data_ptr()
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f32c(a):
+    """float32 C-contiguous view of a numpy array (copied if needed) or a tensor."""
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    return a
 
 
 def _stream(stream):
@@ -261,16 +269,28 @@ def make_desc(d: dict):
 
 
 class Geometry:
+    """A geometry from a description dict: a detector geometry (geometry_set)
+    or, for kind "rays", explicit rays o[R,3], d[R,3], t[R,2] (geometry_set_rays;
+    numpy arrays or contiguous float32 tensors)."""
+
     def __init__(self, ctx: Context, d: dict):
-        desc, angles = make_desc(d)
         h = _VP()
-        _check(lib().geometry_set(ctx.h, ctypes.byref(desc), ctypes.byref(h)))
+        if d["kind"] == "rays":
+            o = _f32c(d["o"])
+            dd = _f32c(d["d"])
+            t = _f32c(d["t"])
+            n = int(o.shape[0])
+            _check(lib().geometry_set_rays(ctx.h, n, _ptr(o), _ptr(dd), _ptr(t), ctypes.byref(h)))
+            self.tiles_per_view = 0
+        else:
+            desc, angles = make_desc(d)
+            _check(lib().geometry_set(ctx.h, ctypes.byref(desc), ctypes.byref(h)))
+            tw, th = int(d.get("tile_w", 16)), int(d.get("tile_h", 16))
+            self.tiles_per_view = ((int(d["n_cols"]) + tw - 1) // tw) * ((int(d["n_rows"]) + th - 1) // th)
         self.h = h
         self.ctx = ctx
         self.desc = d
         self.n_rays = int(lib().geometry_num_rays(h))
-        tw, th = int(d.get("tile_w", 16)), int(d.get("tile_h", 16))
-        self.tiles_per_view = ((int(d["n_cols"]) + tw - 1) // tw) * ((int(d["n_rows"]) + th - 1) // th)
 
     def close(self):
         if self.h:

@@ -174,7 +174,57 @@ def geom_c3(n_angles: int = 288, n_radial: int = 329, n_planes: int = 63, arc_mo
 
 
 def num_rays(g: dict) -> int:
+    if g["kind"] == "rays":
+        return int(np.asarray(g["o"]).shape[0])
     return int(g["n_views"]) * int(g["n_rows"]) * int(g["n_cols"])
+
+
+# ---------------------------------------------------------------------------
+# explicit ray sets
+# ---------------------------------------------------------------------------
+
+def rays_helical(n_views: int, n_rows: int, n_cols: int, pitch: float, dso: float, dsd: float,
+                 z_per_turn: float, turns: float = 1.0) -> dict:
+    """Helical cone-beam CT as explicit rays: the source at angle th_k =
+    2 pi turns k / n_views sits at (-dso e_w, z_k), z_k = z_per_turn th_k / 2 pi
+    - the middle height, with the flat detector frame of the circular cone beam
+    (e_w = (cos th, sin th, 0), e_u = (-sin th, cos th, 0), e_v = z) moving with
+    it; each ray runs from the source (t = 0) to its pixel (t = |D - S|).
+    Layout [view][row][col]."""
+    k = np.arange(n_views, dtype=np.float64)
+    th = 2.0 * math.pi * turns * k / n_views
+    z = z_per_turn * th / (2.0 * math.pi)
+    z -= 0.5 * (z[0] + z[-1])
+    ew = np.stack([np.cos(th), np.sin(th), np.zeros_like(th)], 1)
+    eu = np.stack([-np.sin(th), np.cos(th), np.zeros_like(th)], 1)
+    ev = np.array([0.0, 0.0, 1.0])
+    u = (np.arange(n_cols) - 0.5 * (n_cols - 1)) * pitch
+    v = (np.arange(n_rows) - 0.5 * (n_rows - 1)) * pitch
+    S = -dso * ew + z[:, None] * ev                                   # [V,3]
+    D = (S[:, None, None, :] + dsd * ew[:, None, None, :] + u[None, None, :, None] * eu[:, None, None, :]
+         + v[None, :, None, None] * ev[None, None, None, :])           # [V,H,W,3]
+    dvec = D - S[:, None, None, :]
+    L = np.linalg.norm(dvec, axis=-1)
+    o = np.broadcast_to(S[:, None, None, :], D.shape).reshape(-1, 3)
+    t = np.stack([np.zeros(L.size), L.reshape(-1)], 1)
+    return dict(kind="rays", o=o.astype(np.float32), d=dvec.reshape(-1, 3).astype(np.float32),
+                t=t.astype(np.float32))
+
+
+def rays_random(n: int, seed: int, radius: float = 1.0, seg: float | None = None) -> dict:
+    """Incoherent rays: lines through uniform points of the ball of the given
+    radius along uniform directions (unnormalised: length U(0.5, 2)), the
+    segment [-seg, seg] around that point (infinite when seg is None)."""
+    rng = np.random.default_rng(seed)
+    p = rng.normal(size=(n, 3))
+    p *= (radius * rng.uniform(0, 1, n) ** (1 / 3) / np.linalg.norm(p, axis=1))[:, None]
+    d = rng.normal(size=(n, 3))
+    d *= (rng.uniform(0.5, 2.0, n) / np.linalg.norm(d, axis=1))[:, None]
+    t = np.full((n, 2), np.inf)
+    t[:, 0] = -np.inf
+    if seg is not None:
+        t[:, 0], t[:, 1] = -seg, seg
+    return dict(kind="rays", o=p.astype(np.float32), d=d.astype(np.float32), t=t.astype(np.float32))
 
 
 # ---------------------------------------------------------------------------
