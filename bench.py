@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="c5: arrival rate (jobs/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fitted", action="store_true", help="skip the fitted-state timing")
+    ap.add_argument("--tile", default="auto", help="binning tile WxH, or auto (the autotuner)")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU sample (0 = auto)")
     return ap.parse_args()
@@ -138,31 +140,77 @@ def barrier(world):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(G, gd, loss, n_views):
-    """Oracle fwd + loss + bwd on the first n_views views: (seconds, rays)."""
-    from oracle import oracle
+def sample_geometry(gd, n_views):
+    """The first n_views views of a geometry."""
     sub = dict(gd)
     sub["n_views"] = n_views
     if gd["kind"] != "pet":
         sub["angles"] = gd["angles"][:n_views]
+    return sub
+
+
+def oracle_sample(G, gd, loss, n_views, nthreads=0, keep=False):
+    """Oracle fwd + loss + bwd on the first n_views views: (seconds, rays)
+    (and, with keep, the projection, dL/dI and gradients)."""
+    from oracle import oracle
+    sub = sample_geometry(gd, n_views)
     rays = synth.num_rays(sub)
     y = np.zeros(rays)
     t0 = time.perf_counter()
-    f = oracle.forward(sub, G)
+    f = oracle.forward(sub, G, nthreads=nthreads)
     if loss == "l2":
         _, w = oracle.loss_l2(f["I"], y)
     else:
         _, w = oracle.loss_poisson(f["I"], y + 1.0, 1.0, 1e-9)
-    oracle.backward(sub, G, w)
-    return time.perf_counter() - t0, rays
+    g = oracle.backward(sub, G, w, nthreads=nthreads)
+    sec = time.perf_counter() - t0
+    return (sec, rays, f, w, g) if keep else (sec, rays)
 
 
-def cpu_baseline(G, gd, loss, n_views):
+def cpu_baseline(G, gd, loss, n_views, rgrt=None, ctx=None):
+    """The oracle timed on the host cores on a sample of the workload (and on
+    one core on one view); with the library at hand, also the FP32-vs-FP64
+    error of the GPU projection and adjoint on that sample."""
     from oracle import oracle
-    sec, rays = oracle_sample(G, gd, loss, n_views)
-    return dict(value=rays / sec, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
-                sample=f"FP64 oracle fwd+loss+bwd on {n_views} of {gd['n_views']} views "
-                       f"({rays} rays, all Gaussians); {sec:.1f} s")
+    sec, rays, f, w, g = oracle_sample(G, gd, loss, n_views, keep=True)
+    out = dict(value=rays / sec, unit=UNIT, cores=oracle.max_threads(), kind="oracle",
+               sample=f"FP64 oracle fwd+loss+bwd on {n_views} of {gd['n_views']} views "
+                      f"({rays} rays, all Gaussians); {sec:.1f} s")
+    s1, r1 = oracle_sample(G, gd, loss, 1, nthreads=1)
+    out["single_core"] = dict(value=r1 / s1, unit=UNIT, cores=1,
+                              sample=f"1 view ({r1} rays, all Gaussians); {s1:.1f} s")
+    if rgrt is not None:
+        out["fp32_vs_fp64"] = gpu_error(rgrt, ctx, G, sample_geometry(gd, n_views), f, w, g)
+    return out
+
+
+def gpu_error(rgrt, ctx, G, sub, f, w, g):
+    """Relative L2 distance of the GPU projection and gradients from the
+    oracle's admissible bracket (pairs within the band of the 3-sigma cut may
+    go either way), on the sample geometry, from the initial Gaussians."""
+    import torch
+    geom = rgrt.Geometry(ctx, sub)
+    gs = rgrt.Gaussians(ctx, *[torch.from_numpy(np.ascontiguousarray(G[k])).cuda()
+                              for k in ("mu", "ls", "q", "rho")])
+    I = torch.empty(geom.n_rays, device="cuda")
+    rgrt.project_forward(ctx, gs, geom, I)
+    n = gs.n
+    outs = [torch.empty(sz, device="cuda") for sz in ((n, 3), (n, 3), (n, 4), (n,))]
+    rgrt.project_backward(ctx, gs, geom, torch.from_numpy(np.asarray(w, np.float32)).cuda(), *outs)
+    torch.cuda.synchronize()
+
+    def dist(x, lo, hi, nom):
+        x = np.asarray(x, np.float64).reshape(-1)
+        c = np.clip(x, np.asarray(lo).reshape(-1), np.asarray(hi).reshape(-1))
+        return float(np.linalg.norm(x - c) / max(np.linalg.norm(np.asarray(nom).reshape(-1)), 1e-300))
+
+    res = dict(forward_rel_l2=dist(I.cpu().numpy(), f["I_lo"], f["I_hi"], f["I"]))
+    for k, o in zip(("mu", "ls", "q", "rho"), outs):
+        res[f"grad_{k}_rel_l2"] = dist(o.cpu().numpy(), g["lo"][k], g["hi"][k], g[k])
+    res["tolerance"] = dict(forward=1e-5, gradient=1e-4)
+    gs.close()
+    geom.close()
+    return res
 
 
 def auto_views(name):
@@ -268,6 +316,15 @@ def run_ours(args):
     G, Gt, gd, loss = workload(args.workload, rank)
     R = synth.num_rays(gd)
     ctx = rgrt.Context(local)
+    t_auto = None
+    if args.tile == "auto":
+        # tile shape from the autotuner (forward + adjoint on 12 of the views), outside the timing
+        ga = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
+        tw, th, t_auto = rgrt.autotune_tile(ctx, ga, gd, max_views=12)
+        ga.close()
+    else:
+        tw, th = (int(x) for x in args.tile.split("x"))
+    gd = dict(gd, tile_w=tw, tile_h=th)
     geom = rgrt.Geometry(ctx, gd)
     # measured data: projections of the perturbed ("true") Gaussians
     tt = {k: torch.from_numpy(v).to(dev) for k, v in Gt.items()}
@@ -348,6 +405,7 @@ def run_ours(args):
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload=WORKLOADS[args.workload], rays_per_step=R,
                             gaussians=int(G["mu"].shape[0]),
+                            tile=f"{tw}x{th}" + (" (autotuner)" if t_auto is not None else ""),
                             l2=("flushed between timed steps (256 MiB write outside the events)"
                                 if flush is not None else "not flushed"),
                             parallelism=f"{world} independent scans (one per GPU)"),
@@ -360,14 +418,49 @@ def run_ours(args):
     # end to end: host parameters in, step, host loss + parameters out
     if not args.no_e2e:
         line["e2e"] = e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world)
+    if args.workload in ("c2", "c3") and not args.no_fitted:
+        line["fitted"] = fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world)
     if rank == 0 and not args.no_cpu_baseline:
         nv = args.cpu_views or auto_views(args.workload)
-        line["cpu_baseline"] = cpu_baseline(G, gd, loss, nv)
+        line["cpu_baseline"] = cpu_baseline(G, gd, loss, nv, rgrt, ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world):
+    """The same step timed again after 100 more optimisation steps (the
+    Gaussians have moved towards the measured object): rays/s and pairs."""
+    import torch
+    for _ in range(100):
+        step += 1
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, None)
+    ctx.stats_enable(True)
+    step += 1
+    rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, None)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.stats_enable(False)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        step += 1
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, None)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    return dict(after_steps=100 + args.warmup + args.steps, value=weak_value(R, args.steps, world, ms),
+                unit=UNIT, ms_per_step=ms / args.steps, pairs_kept_per_step=st["pairs_kept"],
+                pairs_evaluated_per_step=st["pairs_evaluated"], keys_per_step=st["keys"])
 
 
 def e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world):
