@@ -710,6 +710,65 @@ void or_backward_list(int64_t nr, const double *o, const double *d, const double
     }
 }
 
+/*
+ * Voxelisation: the density field of the Gaussians (the integrand of Eq. 4,
+ * rho exp(-1/2 (x - mu)^T P (x - mu)), Eq. 2) sampled at voxel centres
+ * x = origin + (i, j, k) * size, with the same cut as the projector: a
+ * Gaussian counts at x when its Mahalanobis distance squared is <= cut2
+ * (band bracket as for projections).  Output layout [k][j][i]; sums run in
+ * Gaussian order per voxel.  Each Gaussian visits the voxels of its FP64 box
+ * of radius sqrt((cut2 + band) Sigma_aa) per axis, which holds every voxel
+ * where it counts (or all voxels when brute != 0).
+ */
+void or_voxelize(const double *origin, const double *size, const int32_t *dims, int64_t n,
+                 const float *mu, const float *ls, const float *q, const float *rho, double cut2,
+                 double band, int brute, int nthreads, double *V, double *Vlo, double *Vhi)
+{
+    og_set_threads(nthreads);
+    const int nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    memset(V, 0, sizeof(double) * (size_t)nvox);
+    memset(Vlo, 0, sizeof(double) * (size_t)nvox);
+    memset(Vhi, 0, sizeof(double) * (size_t)nvox);
+    double (*Sig)[3][3] = malloc(sizeof(double[3][3]) * (size_t)(n > 0 ? n : 1));
+    double (*P)[3][3] = malloc(sizeof(double[3][3]) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; k++) og_cov(ls + 3 * k, q + 4 * k, Sig[k], P[k]);
+    /* parallel over z slices: every voxel is written by one thread, Gaussians in order */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int kz = 0; kz < nz; kz++) {
+        const double z = origin[2] + kz * size[2];
+        for (int64_t g = 0; g < n; g++) {
+            const double m3[3] = { mu[3 * g], mu[3 * g + 1], mu[3 * g + 2] };
+            int lo[2] = { 0, 0 }, hi[2] = { nx - 1, ny - 1 };
+            if (!brute) {
+                const double r2 = cut2 + band;
+                const double hz = sqrt(r2 * Sig[g][2][2]);
+                if (z < m3[2] - hz || z > m3[2] + hz) continue;
+                for (int a = 0; a < 2; a++) {
+                    const double h = sqrt(r2 * Sig[g][a][a]);
+                    const int na = a == 0 ? nx : ny;
+                    double l = ceil((m3[a] - h - origin[a]) / size[a]);
+                    double u = floor((m3[a] + h - origin[a]) / size[a]);
+                    lo[a] = l < 0 ? 0 : (l > na ? na : (int)l);
+                    hi[a] = u > na - 1 ? na - 1 : (u < -1 ? -1 : (int)u);
+                }
+            }
+            for (int j = lo[1]; j <= hi[1]; j++)
+                for (int i = lo[0]; i <= hi[0]; i++) {
+                    const double d[3] = { origin[0] + i * size[0] - m3[0], origin[1] + j * size[1] - m3[1],
+                                          z - m3[2] };
+                    double md = 0.0;
+                    for (int a = 0; a < 3; a++)
+                        for (int b = 0; b < 3; b++) md += d[a] * P[g][a][b] * d[b];
+                    const double f = rho[g] * exp(-0.5 * md);
+                    const int64_t x = ((int64_t)kz * ny + j) * nx + i;
+                    og_accum(f, md, cut2, band, V + x, Vlo + x, Vhi + x);
+                }
+        }
+    }
+    free(Sig); free(P);
+}
+
 /* ------------------------------------------------------------------ */
 /* FP32 replica of the culling predicate (bit-exact specification)     */
 /* Built with -ffp-contract=off: every + - * / sqrt below is one IEEE  */

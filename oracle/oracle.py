@@ -259,6 +259,22 @@ def backward_list(o, d, t, G, dLdI, cut2=CUT2, band=BAND, nthreads=0):
     return dict(mu=gm, ls=gl, q=gq, rho=gr, lo=split(lohi[:, :11]), hi=split(lohi[:, 11:]))
 
 
+def voxelize(vol, G, cut2=CUT2, band=BAND, brute=False, nthreads=0):
+    """FP64 density field on a voxel grid vol = dict(origin=(x, y, z) of voxel
+    (0, 0, 0), size=(vx, vy, vz), dims=(nx, ny, nz)): dict(V, V_lo, V_hi) with
+    arrays [nz, ny, nx]."""
+    origin = _f64(vol["origin"])
+    size = _f64(vol["size"])
+    dims = np.ascontiguousarray(vol["dims"], dtype=np.int32)
+    nx, ny, nz = (int(x) for x in dims)
+    n, mu, ls, q, rho = _gauss(G)
+    V = np.zeros((nz, ny, nx)); Vlo = np.zeros_like(V); Vhi = np.zeros_like(V)
+    lib().or_voxelize(_p(origin), _p(size), _p(dims), ctypes.c_int64(n), _p(mu), _p(ls), _p(q), _p(rho),
+                      ctypes.c_double(cut2), ctypes.c_double(band), ctypes.c_int(int(brute)),
+                      ctypes.c_int(nthreads), _p(V), _p(Vlo), _p(Vhi))
+    return dict(V=V, V_lo=Vlo, V_hi=Vhi)
+
+
 # ---------------------------------------------------------------------------
 # FP32 culling specification (bit-exact tile lists)
 # ---------------------------------------------------------------------------
