@@ -56,6 +56,8 @@ WORKLOADS = {
     "c4-small": "batching, small scans: 64 cone-beam CT scans (Gaussians log-uniform 1k-20k, views "
                 "U{16..64}, detector side U{64,96,128}), fwd+bwd (L2 + Adam) as one graph-captured step; "
                 "against 64 plain steps",
+    "vox": "voxelisation: the 50,000 Gaussians of the cone-beam CT workload on a 256^3 grid of "
+           "[-1, 1]^3 (density field with the 3-sigma cut)",
     "c5": "serving: Poisson arrivals, 70% loss+gradient jobs / 30% 200-iteration Adam reconstructions "
           "(8 views per iteration); CT (cone, C2 geometry scaled to the side) and PET (288x329x63 "
           "arc-corrected) 50:50; admission by a 150 GB HBM budget; continuous batching vs a "
@@ -318,9 +320,10 @@ def run_ours(args):
     ctx = rgrt.Context(local)
     t_auto = None
     if args.tile == "auto":
-        # tile shape from the autotuner (forward + adjoint on 12 of the views), outside the timing
+        # tile shape from the autotuner (forward + adjoint over all views: the
+        # sort's pass count depends on the total number of tiles), outside the timing
         ga = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
-        tw, th, t_auto = rgrt.autotune_tile(ctx, ga, gd, max_views=12)
+        tw, th, t_auto = rgrt.autotune_tile(ctx, ga, gd, max_views=0)
         ga.close()
     else:
         tw, th = (int(x) for x in args.tile.split("x"))
@@ -733,6 +736,81 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+FLOP_PER_PAIR_VOX = 30   # per kept (voxel, Gaussian) pair: delta, P delta, the form, scale, value, sum
+
+
+def run_vox(args):
+    """Voxelisation of the cone-beam workload's Gaussians: voxels/s."""
+    import torch
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    G, _ = synth.workload_c2(0)
+    G = _params(G)
+    n = 256
+    h = 2.0 / n
+    vol = dict(origin=(-1 + h / 2,) * 3, size=(h, h, h), dims=(n, n, n))
+    ctx = rgrt.Context(0)
+    gs = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).cuda() for k in ("mu", "ls", "q", "rho")])
+    out = torch.empty((n, n, n), device="cuda")
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        rgrt.gaussians_voxelize(ctx, gs, vol, out)
+    torch.cuda.synchronize()
+    ctx.prof_enable(True)
+    ctx.prof_reset()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = rgrt.launch_count()
+    for k in range(args.steps):
+        if flush is not None:
+            flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        rgrt.gaussians_voxelize(ctx, gs, vol, out)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = rgrt.launch_count() - l0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    nk, kms = ctx.prof_get("k_voxelize")
+    nb, bms = ctx.prof_get("vox_bin")
+    ctx.prof_enable(False)
+    # kept pairs, counted analytically: voxels inside each Gaussian's 3-sigma
+    # ellipsoid = (4/3) pi 27 sqrt(det Sigma) / h^3 (the grid is fine against sigma)
+    s = np.exp(G["ls"].astype(np.float64))
+    pairs = float(np.sum(4.0 / 3.0 * math.pi * 27.0 * np.prod(s, axis=1)) / h ** 3)
+    per = kms / max(nk, 1)
+    achieved = pairs * FLOP_PER_PAIR_VOX / (per / 1e3) / 1e12
+    peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # end to end: the volume read back to pinned host memory every call
+    host = torch.empty((n, n, n)).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(3, args.steps // 2)):
+        rgrt.gaussians_voxelize(ctx, gs, vol, out)
+        host.copy_(out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(3, args.steps // 2)
+    line = dict(metric="voxels/s", value=n ** 3 / (ms / 1e3), unit="voxels/s", n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOADS["vox"], voxels=n ** 3, gaussians=int(G["mu"].shape[0]),
+                            l2=("flushed between timed calls (256 MiB write outside the events)"
+                                if flush is not None else "not flushed")),
+                kernels=dict(vox_bin=dict(launches=nb, ms=bms), k_voxelize=dict(launches=nk, ms=kms)),
+                pairs_kept_per_step=pairs,
+                roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                              traffic=None, kernel="k_voxelize", kernel_ms=per,
+                              note="30 FLOP per kept (voxel, Gaussian) pair, pairs counted analytically"),
+                gpu_launches=launches,
+                e2e=dict(value=n ** 3 / e2e_s, unit="voxels/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=4 * n ** 3))
+    if clk:
+        line["clocks"] = clk
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -741,6 +819,8 @@ def main():
         run_c4(args)
     elif args.workload == "c5":
         run_c5(args)
+    elif args.workload == "vox":
+        run_vox(args)
     else:
         run_ours(args)
 

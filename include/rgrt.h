@@ -201,6 +201,24 @@ int loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const f
               const rgrt_adam *hp, float *loss_out, float *g_mu3, float *g_logscale3,
               float *g_quat4, float *g_rho, void *stream);
 
+/* ---- voxelisation ---------------------------------------------------- */
+
+/* Regular voxel grid: voxel (i, j, k) has its centre at
+ * origin + (i size[0], j size[1], k size[2]); dims = (nx, ny, nz). */
+typedef struct {
+    double origin[3];
+    double size[3];      /* > 0 */
+    int32_t dims[3];     /* > 0, each <= 65535 x 8 */
+} rgrt_volume_desc;
+
+/* The reconstructed volume: out[k][j][i] = sum over Gaussians of
+ * rho exp(-(x - mu)^T Sigma^-1 (x - mu) / 2) at voxel centre x (the integrand
+ * of Eq. 4 with the Gaussians of Eq. 2), with the projector's cut (a Gaussian
+ * counts where that exponent's argument m <= 9).  out: nx ny nz floats, host
+ * or device.  RGRT_E_INVAL for a bad grid, RGRT_E_NOMEM over the budget. */
+int gaussians_voxelize(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_volume_desc *vol, float *out,
+                       void *stream);
+
 /* ---- batched scans ---------------------------------------------------- */
 
 typedef struct rgrt_batch rgrt_batch;
@@ -234,9 +252,10 @@ int rgrt_batch_loss_step(rgrt_batch *b, const float *const *y, int loss, const r
 int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans);
 
 /* Tile-shape autotuner: times project_forward + project_backward of g on
- * `desc` (CT: an evenly spaced subset of max_views views; max_views <= 0 keeps
- * all) for the tile shapes 16x16, 16x8, 8x8 and 32x8, and returns the
- * fastest (and its time in ms for the subset). */
+ * `desc` (an evenly spaced subset of max_views views; max_views <= 0 keeps
+ * all -- the sort's pass count depends on the total number of tiles, so a
+ * subset can favour small tiles) for the tile shapes 16x16, 16x8, 8x8 and
+ * 32x8, and returns the fastest (and its time in ms). */
 int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc, int max_views,
                        int *tile_w, int *tile_h, double *ms_out);
 

@@ -414,7 +414,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
 }
 
 template <bool CONE, bool STATS>
-__global__ void __launch_bounds__(256, 3) k_forward(DevGeom g, const float4 *__restrict__ rec,
+__global__ void __launch_bounds__(256, 4) k_forward(DevGeom g, const float4 *__restrict__ rec,
                                                     const float4 *__restrict__ crec,
                                                     const uint32_t *__restrict__ gids,
                                                     const uint2 *__restrict__ ranges,

@@ -34,9 +34,9 @@ def test_two_gloo_ranks_max_time_and_independent_scans():
     import torch.multiprocessing as mp
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    ctx = mp.get_context("spawn")      # no fork of a process that already runs threads
+    mgr = ctx.Manager()
     out = mgr.dict()
-    ctx = mp.get_context("spawn")
     procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
     for p in procs:
         p.start()
