@@ -56,6 +56,9 @@ WORKLOADS = {
     "c4-small": "batching, small scans: 64 cone-beam CT scans (Gaussians log-uniform 1k-20k, views "
                 "U{16..64}, detector side U{64,96,128}), fwd+bwd (L2 + Adam) as one graph-captured step; "
                 "against 64 plain steps",
+    "recon": "reconstruction quality: the 50,000 Gaussians of the cone-beam CT workload fitted (L2 + Adam) "
+             "to the exact line integrals of their 12-ellipsoid phantom over 180 views x 256^2; PSNR of the "
+             "voxelised volume (128^3) against the phantom's density",
     "vox": "voxelisation: the 50,000 Gaussians of the cone-beam CT workload on a 256^3 grid of "
            "[-1, 1]^3 (density field with the 3-sigma cut)",
     "c5": "serving: Poisson arrivals, 70% loss+gradient jobs / 30% 200-iteration Adam reconstructions "
@@ -76,6 +79,7 @@ def parse():
     ap.add_argument("--jobs", type=int, default=48, help="c5: jobs per run")
     ap.add_argument("--slots", type=int, default=4, help="c5: slots of the continuous server")
     ap.add_argument("--rate", type=float, default=200.0, help="c5: arrival rate (jobs/s)")
+    ap.add_argument("--iters", type=int, default=300, help="recon: optimisation steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fitted", action="store_true", help="skip the fitted-state timing")
@@ -811,6 +815,50 @@ def run_vox(args):
     print(json.dumps(line), flush=True)
 
 
+def run_recon(args):
+    """Reconstruction quality and speed: Adam on the exact phantom projections,
+    PSNR of the voxelised Gaussians every 50 steps."""
+    import torch
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    ph = synth.ellipsoid_phantom(12, seed=1000, semi=(0.05, 0.6), dens=(0.1, 1.0))   # the C2 phantom
+    G, gd = synth.workload_c2(0)
+    G = _params(G)
+    y = torch.from_numpy(synth.phantom_projection(ph, *synth.detector_rays(gd)).astype(np.float32)).cuda()
+    vol = synth.voxel_grid(128)
+    ref = synth.phantom_volume(ph, vol)
+    ctx = rgrt.Context(0)
+    geom = rgrt.Geometry(ctx, gd)
+    gs = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).cuda() for k in ("mu", "ls", "q", "rho")])
+    hp = rgrt.adam_params()
+    lo = torch.zeros(1, device="cuda")
+    curve = []
+    stream = torch.cuda.current_stream()
+    ms_total = 0.0
+    for it in range(args.iters + 1):
+        if it % 50 == 0 or it == args.iters:
+            V = rgrt.gaussians_voxelize(ctx, gs, vol)
+            curve.append(dict(step=it, loss=float(lo.item()) if it else None, psnr_db=synth.psnr(V, ref)))
+        if it == args.iters:
+            break
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rgrt.loss_step(ctx, gs, geom, y, rgrt.RGRT_LOSS_L2, hp, it + 1, lo)
+        b.record(stream)
+        b.synchronize()
+        ms_total += a.elapsed_time(b)
+    R = synth.num_rays(gd)
+    line = dict(metric=METRIC, value=R * args.iters / (ms_total / 1e3), unit=UNIT, n_gpus=1, steps=args.iters,
+                warmup=0, ms_per_step=ms_total / args.iters, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOADS["recon"], rays_per_step=R, gaussians=int(G["mu"].shape[0]),
+                            voxels=int(np.prod(vol["dims"])), l2="not flushed"),
+                recon=dict(psnr_db_start=curve[0]["psnr_db"], psnr_db_end=curve[-1]["psnr_db"], curve=curve,
+                           note="PSNR against the phantom density at voxel centres, peak = max density"),
+                e2e=None)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -821,6 +869,8 @@ def main():
         run_c5(args)
     elif args.workload == "vox":
         run_vox(args)
+    elif args.workload == "recon":
+        run_recon(args)
     else:
         run_ours(args)
 

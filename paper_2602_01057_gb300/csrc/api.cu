@@ -1022,6 +1022,80 @@ int loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, const f
     return RGRT_OK;
 }
 
+int gaussians_voxelize(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_volume_desc *vol, float *out,
+                       void *stream)
+{
+    TRY(check_ctx(ctx));
+    if (!g || !vol || !out) return fail(RGRT_E_INVAL, "null argument");
+    if (g->ctx != ctx) return fail(RGRT_E_INVAL, "Gaussians of another context");
+    for (int a = 0; a < 3; a++) {
+        if (vol->dims[a] <= 0 || vol->dims[a] > 65535 * 8)
+            return fail(RGRT_E_INVAL, "volume dimension %d out of range (%d)", a, vol->dims[a]);
+        if (!(vol->size[a] > 0.0) || !std::isfinite(vol->size[a]) || !std::isfinite(vol->origin[a]))
+            return fail(RGRT_E_INVAL, "voxel size must be positive and finite, origin finite");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    VolDev v;
+    v.ox = (float)vol->origin[0]; v.oy = (float)vol->origin[1]; v.oz = (float)vol->origin[2];
+    v.sx = (float)vol->size[0]; v.sy = (float)vol->size[1]; v.sz = (float)vol->size[2];
+    v.nx = vol->dims[0]; v.ny = vol->dims[1]; v.nz = vol->dims[2];
+    v.bx = (v.nx + 7) / 8; v.by = (v.ny + 7) / 8; v.bz = (v.nz + 3) / 4;
+    const int64_t nb = (int64_t)v.bx * v.by * v.bz;
+    if (nb >= 0x7fffffffLL) return fail(RGRT_E_INVAL, "too many voxel bricks (%lld)", (long long)nb);
+    const size_t nvox = (size_t)v.nx * v.ny * v.nz;
+    void *dout;
+    bool back;
+    TRY(stage_output(ctx, ctx->stage_out[0], out, sizeof(float) * nvox, &dout, &back));
+    const int64_t N = g->n;
+    if (N == 0) {
+        CK(cudaMemsetAsync(dout, 0, sizeof(float) * nvox, s));
+    } else {
+        TRY(build_records(ctx, g, s));
+        TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)N));
+        TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)N));
+        TRY(ensure(ctx, ctx->rect, sizeof(uint4) * (size_t)N));
+        TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems(N)));
+        TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
+        TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)nb));
+        {
+            PROF("vox_bin");
+            CK(launch_vox_count(g->crec, N, v, (uint32_t *)ctx->cnt.p, (uint4 *)ctx->rect.p, s));
+            CK(launch_scan((uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p, N,
+                           (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
+        }
+        CK(cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const unsigned long long K = *ctx->h_total;
+        if (K >= 0xffffffffull)
+            return fail(RGRT_E_CAPACITY, "%llu (brick, Gaussian) entries (more than 2^32)", K);
+        TRY(ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)(K ? K : 1)));
+        TRY(ensure(ctx, ctx->vals, sizeof(uint32_t) * (size_t)(K ? K : 1)));
+        TRY(ensure(ctx, ctx->keys_alt, sizeof(uint32_t) * (size_t)(K ? K : 1)));
+        TRY(ensure(ctx, ctx->vals_alt, sizeof(uint32_t) * (size_t)(K ? K : 1)));
+        TRY(ensure(ctx, ctx->sort_tmp, sizeof(uint32_t) * sort_tmp_elems((uint32_t)(K ? K : 1))));
+        uint32_t *keys = (uint32_t *)ctx->keys.p, *vals = (uint32_t *)ctx->vals.p;
+        {
+            PROF("vox_bin");
+            CK(launch_vox_emit(N, v, (const uint32_t *)ctx->cnt.p, (const uint32_t *)ctx->off.p,
+                               (const uint4 *)ctx->rect.p, keys, vals, (uint32_t)K, s));
+            if (K > 0)
+                CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
+                               (uint32_t)K, ceil_log2((uint64_t)nb) > 0 ? ceil_log2((uint64_t)nb) : 1,
+                               (uint32_t *)ctx->sort_tmp.p, s));
+            CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)nb, s));
+            CK(launch_vox_ranges(keys, (uint32_t)K, (uint2 *)ctx->ranges.p, (uint32_t)nb, s));
+        }
+        ctx->bin_valid = false;   // the shared scratch now holds brick lists
+        PROF("k_voxelize");
+        CK(launch_voxelize(g->rec, g->crec, vals, (const uint2 *)ctx->ranges.p, v, (float *)dout, s));
+    }
+    if (back) {
+        CK(cudaMemcpyAsync(out, dout, sizeof(float) * nvox, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return RGRT_OK;
+}
+
 int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *stream)
 {
     TRY(check_ctx(ctx));

@@ -140,4 +140,21 @@ cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_ra
                                 const float4 *rec, const uint32_t *gids, const uint2 *ranges,
                                 const float *dLdI, float4 *grad, cudaStream_t s);
 
+// ---- voxelisation (voxel.cu) ----------------------------------------------
+// voxel (i, j, k) centre = (ox + i sx, oy + j sy, oz + k sz); bricks of
+// 8 x 8 x 4 voxels, bx x by x bz of them
+struct VolDev {
+    float ox, oy, oz, sx, sy, sz;
+    int nx, ny, nz, bx, by, bz;
+};
+// per Gaussian: number of bricks its K-sigma box touches and their range
+cudaError_t launch_vox_count(const float4 *crec, int64_t n, const VolDev &v, uint32_t *cnt, uint4 *bbox,
+                             cudaStream_t s);
+cudaError_t launch_vox_emit(int64_t n, const VolDev &v, const uint32_t *cnt, const uint32_t *off,
+                            const uint4 *bbox, uint32_t *keys, uint32_t *vals, uint32_t cap, cudaStream_t s);
+// ranges[b] = [first, last + 1) of brick b in the sorted keys (zeroed first)
+cudaError_t launch_vox_ranges(const uint32_t *keys, uint32_t nk, uint2 *ranges, uint32_t nb, cudaStream_t s);
+cudaError_t launch_voxelize(const float4 *rec, const float4 *crec, const uint32_t *gids, const uint2 *ranges,
+                            const VolDev &v, float *out, cudaStream_t s);
+
 }  // namespace rgrt

@@ -41,6 +41,10 @@ class GeomDesc(ctypes.Structure):
     ]
 
 
+class VolumeDesc(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3), ("dims", ctypes.c_int32 * 3)]
+
+
 class Adam(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in (
         "lr_mu", "lr_logscale", "lr_quat", "lr_rho", "beta1", "beta2", "eps", "kappa",
@@ -68,6 +72,7 @@ _EXPORTS = {
                   ctypes.c_int),
     "loss_grad": ([_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), _VP, _VP, _VP, _VP, _VP, _VP],
                   ctypes.c_int),
+    "gaussians_voxelize": ([_VP, _VP, ctypes.POINTER(VolumeDesc), _VP, _VP], ctypes.c_int),
     "rgrt_batch_create": ([_VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "rgrt_batch_destroy": ([_VP], ctypes.c_int),
     "rgrt_batch_forward": ([_VP, _VP, _VP], ctypes.c_int),
@@ -416,6 +421,19 @@ def loss_grad(ctx, gauss, geom, y, loss=RGRT_LOSS_L2, hp: Adam | None = None, lo
     _check(lib().loss_grad(ctx.h, gauss.h, geom.h, _ptr(y), int(loss), ctypes.byref(hp), _ptr(loss_out),
                            _ptr(g_mu), _ptr(g_ls), _ptr(g_q), _ptr(g_rho), _stream(stream)))
     return loss_out
+
+
+def gaussians_voxelize(ctx, gauss, vol: dict, out=None, stream=None):
+    """Density field on the grid vol = dict(origin, size, dims=(nx, ny, nz));
+    out: [nz, ny, nx] float32 (host numpy or device tensor; a new host array
+    when None)."""
+    d = VolumeDesc((ctypes.c_double * 3)(*vol["origin"]), (ctypes.c_double * 3)(*vol["size"]),
+                   (ctypes.c_int32 * 3)(*(int(x) for x in vol["dims"])))
+    if out is None:
+        nx, ny, nz = (int(x) for x in vol["dims"])
+        out = np.zeros((nz, ny, nx), np.float32)
+    _check(lib().gaussians_voxelize(ctx.h, gauss.h, ctypes.byref(d), _ptr(out), _stream(stream)))
+    return out
 
 
 def debug_records(ctx, gauss):

@@ -180,6 +180,88 @@ def num_rays(g: dict) -> int:
 
 
 # ---------------------------------------------------------------------------
+# ground truth of the phantoms: detector rays, line integrals, voxel grids
+# ---------------------------------------------------------------------------
+
+def detector_rays(g: dict):
+    """(o, d, t_a, t_b) in FP64 of every ray of a CT geometry (output order
+    [view][row][col]), d unit: parallel o = u e_u + v e_v, d = e_w, t in
+    [t_a, t_b]; cone o = S = -dso e_w, d towards the pixel D = S + dsd e_w +
+    u e_u + v e_v, t in [0, |D - S|]; e_w = (cos th, sin th, 0),
+    e_u = (-sin th, cos th, 0), e_v = z, u_i = (i - (W-1)/2) pitch_u."""
+    V, H, W = int(g["n_views"]), int(g["n_rows"]), int(g["n_cols"])
+    th = np.asarray(g["angles"], np.float64)
+    ew = np.stack([np.cos(th), np.sin(th), np.zeros_like(th)], 1)[:, None, None, :]
+    eu = np.stack([-np.sin(th), np.cos(th), np.zeros_like(th)], 1)[:, None, None, :]
+    ev = np.array([0.0, 0.0, 1.0])
+    u = ((np.arange(W) - 0.5 * (W - 1)) * g["pitch_u"])[None, None, :, None]
+    v = ((np.arange(H) - 0.5 * (H - 1)) * g["pitch_v"])[None, :, None, None]
+    if g["kind"] == "parallel":
+        o = u * eu + v * ev
+        d = np.broadcast_to(ew, o.shape)
+        ta = np.full(o.shape[:3], float(g["t_a"]))
+        tb = np.full(o.shape[:3], float(g["t_b"]))
+    elif g["kind"] == "cone":
+        S = -g["dso"] * ew
+        D = S + g["dsd"] * ew + u * eu + v * ev
+        dv = D - S
+        L = np.linalg.norm(dv, axis=-1)
+        o = np.broadcast_to(S, D.shape)
+        d = dv / L[..., None]
+        ta, tb = np.zeros_like(L), L
+    else:
+        raise ValueError("detector_rays covers the CT geometries")
+    return (o.reshape(-1, 3), d.reshape(-1, 3), ta.reshape(-1), tb.reshape(-1))
+
+
+def phantom_projection(ph: dict, o, d, ta, tb) -> np.ndarray:
+    """Exact line integrals of the ellipsoid phantom (additive densities):
+    sum_k D_k |{t in [t_a, t_b]: o + t d inside ellipsoid k}|, d unit, from the
+    roots of the quadratic |A^-1 R^T (o + t d - c)|^2 = 1."""
+    o = np.asarray(o, np.float64)
+    d = np.asarray(d, np.float64)
+    out = np.zeros(o.shape[0])
+    for a, r, c, dens in zip(ph["axes"], ph["rot"], ph["centre"], ph["density"]):
+        p = ((o - c) @ r) / a
+        q = (d @ r) / a
+        A = np.sum(q * q, axis=1)
+        B = np.sum(p * q, axis=1)
+        C = np.sum(p * p, axis=1) - 1.0
+        disc = B * B - A * C
+        hit = disc > 0
+        sq = np.sqrt(np.where(hit, disc, 0.0))
+        t1 = (-B - sq) / A
+        t2 = (-B + sq) / A
+        lo = np.maximum(t1, ta)
+        hi = np.minimum(t2, tb)
+        out += dens * np.where(hit, np.maximum(hi - lo, 0.0), 0.0)
+    return out
+
+
+def voxel_grid(n: int, half: float = 1.0) -> dict:
+    """n^3 voxel centres covering [-half, half]^3."""
+    h = 2.0 * half / n
+    return dict(origin=(-half + h / 2,) * 3, size=(h, h, h), dims=(n, n, n))
+
+
+def phantom_volume(ph: dict, vol: dict) -> np.ndarray:
+    """The phantom's density at the voxel centres, [nz, ny, nx]."""
+    nx, ny, nz = (int(x) for x in vol["dims"])
+    x = vol["origin"][0] + vol["size"][0] * np.arange(nx)
+    y = vol["origin"][1] + vol["size"][1] * np.arange(ny)
+    z = vol["origin"][2] + vol["size"][2] * np.arange(nz)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    return _phantom_density(ph, pts).reshape(nz, ny, nx)
+
+
+def psnr(vol: np.ndarray, ref: np.ndarray) -> float:
+    """Peak signal-to-noise ratio (dB) of vol against ref, peak = max(ref)."""
+    mse = float(np.mean((np.asarray(vol, np.float64) - ref) ** 2))
+    return 10.0 * math.log10(float(ref.max()) ** 2 / max(mse, 1e-300))
+
+
+# ---------------------------------------------------------------------------
 # explicit ray sets
 # ---------------------------------------------------------------------------
 
