@@ -211,9 +211,50 @@ static double og_phi(double wa, double wb)
     return 0.5 * (erf(wb) - erf(wa));
 }
 
+/*
+ * Kernel of the primitives.  0: the Gaussian of Eq. 2.  1: the Epanechnikov
+ * kernel named in section 2 as an alternative for ray tracing, read here as
+ * rho (1 - m(x) / kappa^2)_+ with m(x) the Mahalanobis distance squared of
+ * Eq. 2's covariance and kappa^2 = 7, so that the normalised kernel has
+ * covariance Sigma (the Epanechnikov kernel on the unit 3-ball has variance
+ * 1/7 per axis).  Selected by or_set_kernel for every following call.
+ */
+#define OG_KAPPA2 7.0
+static int og_kern = 0;
+
+void or_set_kernel(int kernel) { og_kern = kernel; }
+
 typedef struct {
     double A, B, C, m, wa, wb, phi, K, f;  /* K = rho sqrt(2pi/A) e^{-m/2} */
+    /* Epanechnikov: clipped interval [s0, s1] around the line's closest point
+     * to mu (s = t + B/A); ea, eb: the ends are the segment's own */
+    double s0, s1, c;
+    int ea, eb;
 } og_pairval;
+
+/* Epanechnikov along the line: with c = 1 - m / kappa^2 the integrand is
+ * rho (c - A s^2 / kappa^2) for |s| <= a = sqrt(kappa^2 c / A), so the
+ * integral over [s0, s1] is rho [c s - A s^3 / (3 kappa^2)] between them */
+static void og_eval_epan(double ta, double tb, double rho, og_pairval *r)
+{
+    r->c = 1.0 - r->m / OG_KAPPA2;
+    r->s0 = r->s1 = 0.0;
+    r->ea = r->eb = 0;
+    r->K = 0.0;
+    r->f = 0.0;
+    if (!(r->m < OG_KAPPA2)) return;
+    const double a = sqrt(OG_KAPPA2 * r->c / r->A);
+    const double sa = ta + r->B / r->A, sb = tb + r->B / r->A;
+    r->ea = sa > -a;
+    r->eb = sb < a;
+    r->s0 = r->ea ? sa : -a;
+    r->s1 = r->eb ? sb : a;
+    if (!(r->s1 > r->s0)) { r->s0 = r->s1 = 0.0; r->ea = r->eb = 0; return; }
+    const double F1 = r->c * r->s1 - r->A * r->s1 * r->s1 * r->s1 / (3.0 * OG_KAPPA2);
+    const double F0 = r->c * r->s0 - r->A * r->s0 * r->s0 * r->s0 / (3.0 * OG_KAPPA2);
+    r->K = F1 - F0;            /* value per unit rho */
+    r->f = rho * r->K;
+}
 
 static void og_eval(const double o[3], const double d[3], double ta, double tb,
                     const double mu[3], double P[3][3], double rho, og_pairval *r)
@@ -228,6 +269,10 @@ static void og_eval(const double o[3], const double d[3], double ta, double tb,
     r->B = d[0] * Pdel[0] + d[1] * Pdel[1] + d[2] * Pdel[2];
     r->C = del[0] * Pdel[0] + del[1] * Pdel[1] + del[2] * Pdel[2];
     r->m = r->C - r->B * r->B / r->A;                              /* Eq. 9 */
+    if (og_kern == 1) {
+        og_eval_epan(ta, tb, rho, r);
+        return;
+    }
     double s2A = sqrt(2.0 * r->A);
     r->wa = (r->A * ta + r->B) / s2A;
     r->wb = (r->A * tb + r->B) / s2A;
@@ -244,6 +289,31 @@ static void og_pair_grad(const double o[3], const double d[3], double ta, double
 {
     const double A = r->A, B = r->B;
     double del[3] = { o[0] - mu[0], o[1] - mu[1], o[2] - mu[2] };
+    if (og_kern == 1) {
+        /* Leibniz: the clipped ends at +-a carry a zero integrand; the
+         * segment's own ends move with B and A through s = t + B/A */
+        if (!(r->s1 > r->s0)) return;
+        const double L = r->s1 - r->s0, k2 = OG_KAPPA2;
+        const double phi1 = r->eb ? rho * (r->c - A * r->s1 * r->s1 / k2) : 0.0;
+        const double phi0 = r->ea ? rho * (r->c - A * r->s0 * r->s0 / k2) : 0.0;
+        const double fC = -rho * L / k2;
+        const double fB = rho * (2.0 * B / A) * L / k2 + (phi1 - phi0) / A;
+        const double fA = -rho * ((B * B) / (A * A) * L
+                                  + (r->s1 * r->s1 * r->s1 - r->s0 * r->s0 * r->s0) / 3.0) / k2
+                          - (phi1 - phi0) * B / (A * A);
+        double Pd[3], Pdel[3];
+        for (int a = 0; a < 3; a++) {
+            Pd[a] = P[a][0] * d[0] + P[a][1] * d[1] + P[a][2] * d[2];
+            Pdel[a] = P[a][0] * del[0] + P[a][1] * del[1] + P[a][2] * del[2];
+        }
+        for (int a = 0; a < 3; a++) gm[a] += wgt * (-fB * Pd[a] - 2.0 * fC * Pdel[a]);
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                gP[a][b] += wgt * (fA * d[a] * d[b] + fB * 0.5 * (d[a] * del[b] + del[a] * d[b])
+                                   + fC * del[a] * del[b]);
+        *grho += wgt * r->K;
+        return;
+    }
     double ea = exp(-r->wa * r->wa), eb = exp(-r->wb * r->wb);
     if (!isfinite(r->wa)) ea = 0.0;
     if (!isfinite(r->wb)) eb = 0.0;
@@ -760,7 +830,8 @@ void or_voxelize(const double *origin, const double *size, const int32_t *dims, 
                     double md = 0.0;
                     for (int a = 0; a < 3; a++)
                         for (int b = 0; b < 3; b++) md += d[a] * P[g][a][b] * d[b];
-                    const double f = rho[g] * exp(-0.5 * md);
+                    const double f = og_kern == 1 ? rho[g] * (md < OG_KAPPA2 ? 1.0 - md / OG_KAPPA2 : 0.0)
+                                                  : rho[g] * exp(-0.5 * md);
                     const int64_t x = ((int64_t)kz * ny + j) * nx + i;
                     og_accum(f, md, cut2, band, V + x, Vlo + x, Vhi + x);
                 }

@@ -105,7 +105,18 @@ def _geom(g):
     return g if isinstance(g, Geometry) else Geometry(g)
 
 
+KERNELS = {"gaussian": 0, "epanechnikov": 1}
+KAPPA2 = 7.0   # Epanechnikov support: Mahalanobis distance squared < 7
+
+
+def _set_kernel(kernel):
+    lib().or_set_kernel(ctypes.c_int(KERNELS[kernel]))
+
+
 def _gauss(G):
+    """Parameter arrays of a Gaussian set; selects its kernel (G["kernel"],
+    default "gaussian") for the call that follows."""
+    _set_kernel(G.get("kernel", "gaussian"))
     mu = _f32(G["mu"], (-1, 3))
     n = mu.shape[0]
     return n, mu, _f32(G["ls"], (n, 3)), _f32(G["q"], (n, 4)), _f32(G["rho"], (n,))
@@ -123,16 +134,18 @@ CUT2 = 9.0          # pairs with m <= 3^2 count (the 3-sigma reading of "negligi
 BAND = 9.0e-4       # |m - 9| <= 1e-4 * 9: ambiguous between FP32 and FP64
 
 
-def pair(o, d, ta, tb, mu, ls, q, rho):
+def pair(o, d, ta, tb, mu, ls, q, rho, kernel="gaussian"):
     """(value, m, A, B, C) of one Gaussian on one ray (no cut-off)."""
+    _set_kernel(kernel)
     out = np.zeros(5)
     lib().or_pair(_p(_f64(o)), _p(_f64(d)), ctypes.c_double(ta), ctypes.c_double(tb),
                   _p(_f32(mu)), _p(_f32(ls)), _p(_f32(q)), ctypes.c_float(rho), _p(out))
     return out
 
 
-def pair_grad(o, d, ta, tb, mu, ls, q, rho):
+def pair_grad(o, d, ta, tb, mu, ls, q, rho, kernel="gaussian"):
     """d value / d(mu[3], l[3], q[4], rho) of one pair (no cut-off)."""
+    _set_kernel(kernel)
     out = np.zeros(11)
     lib().or_pair_grad(_p(_f64(o)), _p(_f64(d)), ctypes.c_double(ta), ctypes.c_double(tb),
                        _p(_f32(mu)), _p(_f32(ls)), _p(_f32(q)), ctypes.c_float(rho), _p(out))
