@@ -65,6 +65,10 @@ extern "C" {
 #define RGRT_LOSS_L2 0       /* L = 1/2 sum (I - y)^2 */
 #define RGRT_LOSS_POISSON 1  /* L = sum (k I + e - y log(k I + e)), k = kappa, e = eps */
 
+/* kernel of the primitives (gaussians_set_kernel) */
+#define RGRT_KERNEL_GAUSSIAN 0      /* rho exp(-m/2), Eq. 2; pairs with m <= 9 count */
+#define RGRT_KERNEL_EPANECHNIKOV 1  /* rho (1 - m/7)_+: compact support, covariance Sigma */
+
 #define RGRT_GEOM_CT_PARALLEL 0
 #define RGRT_GEOM_CT_CONE 1
 #define RGRT_GEOM_PET_RING 2
@@ -137,6 +141,16 @@ int rgrt_ctx_destroy(rgrt_ctx *ctx);
 int gaussians_create(rgrt_ctx *ctx, int64_t n, const float *mu3, const float *logscale3,
                      const float *quat4, const float *rho, int flags, rgrt_gauss **out);
 int gaussians_destroy(rgrt_gauss *g);
+/* Select the kernel of the primitives (RGRT_KERNEL_*; default Gaussian).
+ * Section 2 names the Epanechnikov kernel as an alternative that ray tracing
+ * can use: rho (1 - m(x)/kappa^2)_+ with m(x) the Mahalanobis distance
+ * squared under Sigma and kappa^2 = 7 (its normalised form has covariance
+ * Sigma); its line integral is rho (4 kappa/3) c^{3/2} / sqrt(A),
+ * c = 1 - m/kappa^2, on a line, and a polynomial over a finite segment.
+ * Every projector and voxeliser call honours it except the batch calls,
+ * which reject non-Gaussian sets.  RGRT_E_INVAL for an unknown kernel. */
+int gaussians_set_kernel(rgrt_gauss *g, int kernel);
+
 /* Copy the current parameters out (host or device pointers; null skips). */
 int gaussians_get(rgrt_gauss *g, float *mu3, float *logscale3, float *quat4, float *rho, void *stream);
 /* Overwrite the parameters (host or device pointers; null keeps the old). */
@@ -166,6 +180,17 @@ int geometry_destroy(rgrt_geom *g);
 int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
                       const float *t2, rgrt_geom **out);
 int64_t geometry_num_rays(const rgrt_geom *g);
+
+/* Measurement model of the losses (the attenuation, scatter and randoms that
+ * the paper's future-work section plans to model in the pipeline): per ray a
+ * multiplicative factor mult[r] (attenuation, detector efficiency) and an
+ * additive background add[r] (scatter + randoms, in counts), both
+ * geometry_num_rays floats, host or device, copied; null = none (1 / 0).
+ * loss_step, loss_grad and the batch calls then use the prediction
+ * mult I + add (L2) or the mean kappa mult I + add + eps (Poisson), with
+ * dL/dI carrying the factor mult.  The projector calls are unaffected.  Set
+ * them before creating a batch that uses the geometry. */
+int geometry_set_corrections(rgrt_geom *g, const float *mult, const float *add);
 
 /* ---- projector (Eqs. 4, 11, 12) ------------------------------------- */
 

@@ -357,17 +357,23 @@ def tile_lists_fp32(geom, G, tile_w, tile_h):
 # losses and Adam (numpy, FP64)
 # ---------------------------------------------------------------------------
 
-def loss_l2(I, y):
-    """L = 1/2 sum (I - y)^2, dL/dI = I - y."""
-    r = np.asarray(I, np.float64) - np.asarray(y, np.float64)
-    return 0.5 * float(np.sum(r * r)), r
+def loss_l2(I, y, mult=None, add=None):
+    """L = 1/2 sum (m I + a - y)^2, dL/dI = m (m I + a - y); m = mult (default 1),
+    a = add (default 0): the measurement model's per-ray factor and background."""
+    m = 1.0 if mult is None else np.asarray(mult, np.float64)
+    a = 0.0 if add is None else np.asarray(add, np.float64)
+    r = m * np.asarray(I, np.float64) + a - np.asarray(y, np.float64)
+    return 0.5 * float(np.sum(r * r)), m * r
 
 
-def loss_poisson(I, y, kappa, eps):
-    """L = sum (kappa I + eps - y log(kappa I + eps)), dL/dI = kappa (1 - y/(kappa I + eps))."""
-    lam = kappa * np.asarray(I, np.float64) + eps
+def loss_poisson(I, y, kappa, eps, mult=None, add=None):
+    """L = sum (lam - y log lam), lam = kappa m I + a + eps,
+    dL/dI = kappa m (1 - y/lam); m = mult (default 1), a = add (default 0)."""
+    m = 1.0 if mult is None else np.asarray(mult, np.float64)
+    a = 0.0 if add is None else np.asarray(add, np.float64)
+    lam = kappa * m * np.asarray(I, np.float64) + a + eps
     y = np.asarray(y, np.float64)
-    return float(np.sum(lam - y * np.log(lam))), kappa * (1.0 - y / lam)
+    return float(np.sum(lam - y * np.log(lam))), kappa * m * (1.0 - y / lam)
 
 
 def adam(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

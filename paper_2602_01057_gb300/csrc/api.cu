@@ -416,7 +416,7 @@ int run_forward_rays(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, 
     return for_ray_ranges(ctx, g, geom, s, false, [&](int b0, int nb) -> int {
         PROF("k_rays_forward");
         CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
-                               (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, s));
+                               (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, g->kernel, s));
         return RGRT_OK;
     });
 }
@@ -449,7 +449,7 @@ int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float
         dg.v0 = v0;
         PROF("k_forward");
         CK(launch_forward(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
-                          out, st, s));
+                          out, st, g->kernel, s));
         return RGRT_OK;
     });
 }
@@ -471,7 +471,7 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
             PROF("k_rays_adjoint");
             CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
                                    (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, dLdI,
-                                   (float4 *)ctx->grad.p, s));
+                                   (float4 *)ctx->grad.p, g->kernel, s));
             return RGRT_OK;
         }));
         PROF("k_param_chain");
@@ -484,7 +484,7 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
         dg.v0 = v0;
         PROF("k_adjoint");
         CK(launch_adjoint(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
-                          dLdI, (float4 *)ctx->grad.p, s));
+                          dLdI, (float4 *)ctx->grad.p, g->kernel, s));
         return RGRT_OK;
     }));
     PROF("k_param_chain");
@@ -683,6 +683,16 @@ int gaussians_destroy(rgrt_gauss *g)
 
 int64_t gaussians_count(const rgrt_gauss *g) { return g ? g->n : -1; }
 
+int gaussians_set_kernel(rgrt_gauss *g, int kernel)
+{
+    if (!g) return fail(RGRT_E_INVAL, "null Gaussians");
+    if (kernel != RGRT_KERNEL_GAUSSIAN && kernel != RGRT_KERNEL_EPANECHNIKOV)
+        return fail(RGRT_E_INVAL, "unknown kernel %d", kernel);
+    g->kernel = kernel;
+    g->version++;
+    return RGRT_OK;
+}
+
 int gaussians_get(rgrt_gauss *g, float *mu3, float *ls3, float *q4, float *rho, void *stream)
 {
     if (!g) return fail(RGRT_E_INVAL, "null Gaussians");
@@ -807,6 +817,8 @@ int geometry_destroy(rgrt_geom *g)
     rgrt_ctx *c = g->ctx;
     cudaSetDevice(c->device);
     if (c->bin_geom == g) c->bin_valid = false;
+    dev_free(c, g->d_mult, sizeof(float) * (size_t)g->n_rays);
+    dev_free(c, g->d_add, sizeof(float) * (size_t)g->n_rays);
     if (g->rays) {
         dev_free(c, g->d_ro, sizeof(float4) * (size_t)g->n_rays);
         dev_free(c, g->d_rd, sizeof(float4) * (size_t)g->n_rays);
@@ -871,6 +883,28 @@ int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const floa
 
 int64_t geometry_num_rays(const rgrt_geom *g) { return g ? g->n_rays : -1; }
 
+static int set_ray_array(rgrt_ctx *ctx, float **dst, const float *src, int64_t n)
+{
+    const size_t bytes = sizeof(float) * (size_t)n;
+    if (!src) {
+        dev_free(ctx, *dst, bytes);
+        *dst = nullptr;
+        return RGRT_OK;
+    }
+    if (!*dst) TRY(dev_alloc(ctx, (void **)dst, bytes));
+    CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyDefault));
+    return RGRT_OK;
+}
+
+int geometry_set_corrections(rgrt_geom *g, const float *mult, const float *add)
+{
+    if (!g) return fail(RGRT_E_INVAL, "null geometry");
+    TRY(check_ctx(g->ctx));
+    TRY(set_ray_array(g->ctx, &g->d_mult, mult, g->n_rays));
+    TRY(set_ray_array(g->ctx, &g->d_add, add, g->n_rays));
+    return RGRT_OK;
+}
+
 int project_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out_I,
                     void *stream)
 {
@@ -934,6 +968,7 @@ static int run_loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *ge
     {
         PROF("k_loss");
         CK(launch_loss(loss, (float *)ctx->I.p, (const float *)dy, R, hp->kappa, hp->poisson_eps,
+                       geom->d_mult, geom->d_add,
                        (float *)ctx->dLdI.p, (double *)ctx->partial.p, nblk, (float *)ctx->loss.p, s));
     }
     if (N > 0) TRY(run_backward(ctx, g, geom, (float *)ctx->dLdI.p, gm, gl, gq, gr, s));
@@ -1087,7 +1122,7 @@ int gaussians_voxelize(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_volume_des
         }
         ctx->bin_valid = false;   // the shared scratch now holds brick lists
         PROF("k_voxelize");
-        CK(launch_voxelize(g->rec, g->crec, vals, (const uint2 *)ctx->ranges.p, v, (float *)dout, s));
+        CK(launch_voxelize(g->rec, g->crec, vals, (const uint2 *)ctx->ranges.p, v, (float *)dout, g->kernel, s));
     }
     if (back) {
         CK(cudaMemcpyAsync(out, dout, sizeof(float) * nvox, cudaMemcpyDeviceToHost, s));

@@ -242,8 +242,8 @@ int enqueue_step(rgrt_batch *b, const float *const *y, int loss, const rgrt_adam
     BTRY(enqueue_forward(b, s));
     for (int i = 0; i < b->n; i++) {
         BatchScan &x = b->sc[i];
-        BK(launch_loss(loss, x.I, y[i], x.R, hp->kappa, hp->poisson_eps, x.dLdI, x.partial, x.nblk,
-                       b->d_loss + i, s));
+        BK(launch_loss(loss, x.I, y[i], x.R, hp->kappa, hp->poisson_eps, x.geom->d_mult, x.geom->d_add,
+                       x.dLdI, x.partial, x.nblk, b->d_loss + i, s));
         BK(cudaMemsetAsync(x.grad, 0, sizeof(float4) * GRAD_F4 * (size_t)std::max<int64_t>(x.N, 1), s));
     }
     BK(cudaMemsetAsync(b->d_queue + 1, 0, sizeof(uint32_t), s));
@@ -344,6 +344,10 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g, const rg
         if (geom[i]->rays) {
             delete b;
             return report_error(RGRT_E_INVAL, "explicit-ray geometries are not batched");
+        }
+        if (g[i]->kernel != RGRT_KERNEL_GAUSSIAN) {
+            delete b;
+            return report_error(RGRT_E_INVAL, "batches take Gaussian-kernel sets only");
         }
         const DevGeom &dg = geom[i]->dg;
         const bool cone = dg.kind == 1;

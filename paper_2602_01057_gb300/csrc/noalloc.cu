@@ -236,6 +236,6 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
     // tiles without entries keep the zero range: clear before filling
     NA_CK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)T, s));
     NA_CK(launch_ranges(keys, (uint32_t)K, ranges, T, s));
-    NA_CK(launch_forward(dg, V, rec, crec, vals, ranges, out_I, nullptr, s));
+    NA_CK(launch_forward(dg, V, rec, crec, vals, ranges, out_I, nullptr, RGRT_KERNEL_GAUSSIAN, s));
     return RGRT_OK;
 }

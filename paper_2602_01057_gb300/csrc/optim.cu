@@ -80,22 +80,31 @@ __global__ void k_param_chain(const float *__restrict__ mu, const float *__restr
 constexpr int LOSS_BS = 256;
 constexpr int LOSS_MAXBLK = 2048;
 
+// mult / add (optional, per ray): the measurement model's multiplicative
+// factor (attenuation, detector efficiency) and additive background (scatter,
+// randoms): L2 compares mult I + add with y, Poisson takes the mean
+// kappa mult I + add + eps.
 __global__ void k_loss(int kind, const float *__restrict__ I, const float *__restrict__ y, int64_t n,
-                       float kappa, float eps, float *__restrict__ dLdI, double *partial)
+                       float kappa, float eps, const float *__restrict__ mult,
+                       const float *__restrict__ add, float *__restrict__ dLdI, double *partial)
 {
     __shared__ double sh[LOSS_BS / 32];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float Ii = I[i], yi = y[i];
+        const float Ii = I[i], yi = y[i];
+        const float mi = mult ? mult[i] : 1.0f;
+        const float mI = mult ? mi * Ii : Ii;
         if (kind == 0) {
-            float r = Ii - yi;
+            float r = mI - yi;
+            if (add) r += add[i];
             s += 0.5 * (double)r * (double)r;
-            dLdI[i] = r;
+            dLdI[i] = mult ? mi * r : r;
         } else {
-            float lam = kappa * Ii + eps;
+            float lam = kappa * mI + eps;
+            if (add) lam += add[i];
             s += (double)lam - (double)yi * log((double)lam);
-            dLdI[i] = kappa * (1.0f - yi / lam);
+            dLdI[i] = mult ? kappa * mi * (1.0f - yi / lam) : kappa * (1.0f - yi / lam);
         }
     }
 #pragma unroll
@@ -157,10 +166,10 @@ int loss_blocks(int64_t n)
 }
 
 cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, float kappa,
-                        float eps, float *dLdI, double *partial, int nblk, float *loss_out,
-                        cudaStream_t s)
+                        float eps, const float *mult, const float *add, float *dLdI, double *partial,
+                        int nblk, float *loss_out, cudaStream_t s)
 {
-    k_loss<<<nblk, LOSS_BS, 0, s>>>(kind, I, y, n, kappa, eps, dLdI, partial);
+    k_loss<<<nblk, LOSS_BS, 0, s>>>(kind, I, y, n, kappa, eps, mult, add, dLdI, partial);
     k_loss_final<<<1, 32, 0, s>>>(partial, nblk, loss_out);
     count_launches(2);
     return cudaGetLastError();

@@ -103,9 +103,83 @@ __device__ __forceinline__ int tr_reduce(float *v, int lane)
     return ok ? p : N;
 }
 
-// general-path value: K = rho sqrt(2pi/A) e^{-m/2}; returns K Phi
+// Kernel of the primitives: 0 = the Gaussian of Eq. 2; 1 = Epanechnikov,
+// rho (1 - m / kappa^2)_+ with kappa^2 = 7 (the support whose normalised
+// kernel has covariance Sigma).  Per kernel, in the view-space form:
+//   QSCALE  factor of Q/A in the exponent argument (arg = QSCALE Q / A):
+//           -log2(e)/2 for the Gaussian (arg feeds ex2), -1/kappa^2 for
+//           Epanechnikov (c = 1 + arg is the kernel's profile factor);
+//   FAC     alpha = rho FAC: the line integral per unit alpha is
+//           A^-1/2 e^{-m/2} (FAC = sqrt(2 pi)) or A^-1/2 c^{3/2}
+//           (FAC = 4 kappa / 3);
+//   SKIP    K^2 of the per-warp skip boxes (a margin over the support);
+//   BALL    radius, in sigma_max, beyond which a segment end has no effect.
+template <int KER> struct Kern;
+template <> struct Kern<0> {
+    static constexpr float QSCALE = -0.721347520444481703f;
+    static constexpr float FAC = 2.50662827463100050f;
+    static constexpr float SKIP = 9.2f;
+    static constexpr float BALL = 8.66f;   // (3 + 4 sqrt 2): erf(w) == +-1 beyond
+};
+template <> struct Kern<1> {
+    static constexpr float KAPPA2 = 7.0f;
+    static constexpr float QSCALE = -1.0f / 7.0f;
+    static constexpr float FAC = 3.52766841475278f;   // 4 sqrt(7) / 3
+    static constexpr float SKIP = 7.2f;
+    static constexpr float BALL = 2.66f;              // sqrt(7) (1 + 0.5%)
+};
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Epanechnikov on the general path: the integrand along the line is
+// rho (c - A s^2 / kappa^2) for |s| <= a = sqrt(kappa^2 c / A), s measured
+// from the Mahalanobis-closest point t* = -B/A; over [s0, s1] = the segment
+// clipped to [-a, a] the integral is rho [c s - A s^3 / (3 kappa^2)] between
+// them.  ea / eb: the lower / upper end is the segment's own (not +-a).
+struct EpanSeg {
+    float c, s0, s1;
+    bool ea, eb, any;
+};
+
+__device__ __forceinline__ EpanSeg epan_seg(const PairGeo &q)
+{
+    constexpr float K2 = Kern<1>::KAPPA2;
+    EpanSeg e;
+    e.c = 1.0f - q.m * (1.0f / K2);
+    e.any = false;
+    e.ea = e.eb = false;
+    e.s0 = e.s1 = 0.0f;
+    if (!(e.c > 0.0f)) return e;
+    const float a = sqrtf(K2 * e.c) * q.rA;
+    const float sh = q.B * q.iA;
+    const float sa = q.ta + sh, sb = q.tb + sh;
+    e.ea = sa > -a;
+    e.eb = sb < a;
+    e.s0 = e.ea ? sa : -a;
+    e.s1 = e.eb ? sb : a;
+    e.any = e.s1 > e.s0;
+    return e;
+}
+
+__device__ __forceinline__ float epan_F(const EpanSeg &e, float A, float s)
+{
+    return s * (e.c - A * s * s * (1.0f / (3.0f * Kern<1>::KAPPA2)));
+}
+
+// general-path value of one pair (rho times the kernel's line integral over
+// the segment): Gaussian K Phi with K = rho sqrt(2pi/A) e^{-m/2}
+template <int KER>
 __device__ __forceinline__ float general_value(const PairGeo &q, float rho)
 {
+    if (KER == 1) {
+        const EpanSeg e = epan_seg(q);
+        return e.any ? rho * (epan_F(e, q.A, e.s1) - epan_F(e, q.A, e.s0)) : 0.0f;
+    }
     const float E = __expf(-0.5f * q.m);
     const float K = rho * SQRT2PI * q.rA * E;
     const float sc = q.rA * SQRT_HALF;
@@ -115,41 +189,68 @@ __device__ __forceinline__ float general_value(const PairGeo &q, float rho)
     return K * phi;
 }
 
-// general-path gradient of one pair: dmu[3], G_P[6], drho (times dL/dI)
+// general-path gradient of one pair: dmu[3], G_P[6], drho (times dL/dI).
+// From the partials fA, fB, fC of the value in A, B, C and st, its
+// derivative for a shift of both segment ends:
+//   d mu = -(I - d d^T)(fB P d + 2 fC P p) - d st,
+//   G_P = fA d d^T + fB sym(d p^T) + fC p p^T.
+template <int KER>
 __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, float rho, float gw,
                                              float *val)
 {
-    const float E = __expf(-0.5f * q.m);
-    const float K = rho * SQRT2PI * q.rA * E;
-    const float sc = q.rA * SQRT_HALF;
-    const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
-    float phi = 1.0f, dPhiB = 0.0f, dPhiA = 0.0f;
-    if (!(wa <= -W_SAT && wb >= W_SAT)) {
-        phi = 0.5f * (erff(wb) - erff(wa));
-        const float ea = __expf(-wa * wa), eb = __expf(-wb * wb);
-        dPhiB = (eb - ea) * q.rA * INV_SQRT2PI;
-        const float tA = 2.0f * q.A;
-        const float r32 = rsqrtf(tA) / tA;  // (2A)^-3/2
-        // an infinite end contributes nothing (its Gaussian factor is 0)
-        const float xa = isinf(q.ta) ? 0.0f : ea * (q.A * q.ta - q.B);
-        const float xb = isinf(q.tb) ? 0.0f : eb * (q.A * q.tb - q.B);
-        dPhiA = (xb - xa) * INV_SQRTPI * r32;
+    float fA, fB, fC, st, frho;
+    if (KER == 1) {
+        // Leibniz: the clipped ends +-a carry a zero integrand; the segment's
+        // own ends move with B and A through s = t + B/A
+        constexpr float iK2 = 1.0f / Kern<1>::KAPPA2;
+        const EpanSeg e = epan_seg(q);
+        if (!e.any) {
+#pragma unroll
+            for (int k = 0; k < 10; k++) val[k] = 0.0f;
+            return;
+        }
+        const float L = e.s1 - e.s0;
+        const float phi1 = e.eb ? rho * (e.c - q.A * e.s1 * e.s1 * iK2) : 0.0f;
+        const float phi0 = e.ea ? rho * (e.c - q.A * e.s0 * e.s0 * iK2) : 0.0f;
+        const float bA = q.B * q.iA;
+        fC = -rho * L * iK2;
+        fB = 2.0f * rho * bA * L * iK2 + (phi1 - phi0) * q.iA;
+        fA = -rho * (bA * bA * L + (e.s1 * e.s1 * e.s1 - e.s0 * e.s0 * e.s0) * (1.0f / 3.0f)) * iK2
+             - (phi1 - phi0) * bA * q.iA;
+        st = phi1 - phi0;
+        frho = epan_F(e, q.A, e.s1) - epan_F(e, q.A, e.s0);
+    } else {
+        const float E = __expf(-0.5f * q.m);
+        const float K = rho * SQRT2PI * q.rA * E;
+        const float sc = q.rA * SQRT_HALF;
+        const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
+        float phi = 1.0f, dPhiB = 0.0f, dPhiA = 0.0f;
+        if (!(wa <= -W_SAT && wb >= W_SAT)) {
+            phi = 0.5f * (erff(wb) - erff(wa));
+            const float ea = __expf(-wa * wa), eb = __expf(-wb * wb);
+            dPhiB = (eb - ea) * q.rA * INV_SQRT2PI;
+            const float tA = 2.0f * q.A;
+            const float r32 = rsqrtf(tA) / tA;  // (2A)^-3/2
+            // an infinite end contributes nothing (its Gaussian factor is 0)
+            const float xa = isinf(q.ta) ? 0.0f : ea * (q.A * q.ta - q.B);
+            const float xb = isinf(q.tb) ? 0.0f : eb * (q.A * q.tb - q.B);
+            dPhiA = (xb - xa) * INV_SQRTPI * r32;
+        }
+        const float f = K * phi;
+        fC = -0.5f * f;
+        fB = f * q.B * q.iA + K * dPhiB;
+        fA = -0.5f * f * q.iA * (1.0f + q.B * q.B * q.iA) + K * dPhiA;
+        st = K * q.A * dPhiB;
+        frho = SQRT2PI * q.rA * E * phi;
     }
-    const float f = K * phi;
-    const float fC = -0.5f * f;
-    const float fB = f * q.B * q.iA + K * dPhiB;
-    const float fA = -0.5f * f * q.iA * (1.0f + q.B * q.B * q.iA) + K * dPhiA;
     // gradient w.r.t. the recentred delta: fB P d + 2 fC P delta
     const float gx = fB * q.Pdx + 2.0f * fC * q.Ppx;
     const float gy = fB * q.Pdy + 2.0f * fC * q.Ppy;
     const float gz = fB * q.Pdz + 2.0f * fC * q.Ppz;
     const float dg = ray.dx * gx + ray.dy * gy + ray.dz * gz;
-    const float st = K * q.A * dPhiB;  // d f / d(segment shift)
-    // d mu = -(I - d d^T) grad - d * st
     val[0] = gw * (-(gx - ray.dx * dg) - ray.dx * st);
     val[1] = gw * (-(gy - ray.dy * dg) - ray.dy * st);
     val[2] = gw * (-(gz - ray.dz * dg) - ray.dz * st);
-    // symmetric gradient w.r.t. P: fA d d^T + fB sym(d p^T) + fC p p^T
     const float hB = 0.5f * fB;
     val[3] = gw * (fA * ray.dx * ray.dx + 2.0f * hB * ray.dx * q.px + fC * q.px * q.px);
     val[4] = gw * (fA * ray.dx * ray.dy + hB * (ray.dx * q.py + q.px * ray.dy) + fC * q.px * q.py);
@@ -157,7 +258,7 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
     val[6] = gw * (fA * ray.dy * ray.dy + 2.0f * hB * ray.dy * q.py + fC * q.py * q.py);
     val[7] = gw * (fA * ray.dy * ray.dz + hB * (ray.dy * q.pz + q.py * ray.dz) + fC * q.py * q.pz);
     val[8] = gw * (fA * ray.dz * ray.dz + 2.0f * hB * ray.dz * q.pz + fC * q.pz * q.pz);
-    val[9] = gw * (SQRT2PI * q.rA * E * phi);
+    val[9] = gw * frho;
 }
 
 

@@ -35,11 +35,8 @@
 namespace rgrt {
 namespace {
 
-constexpr float SKIP_K2 = 9.2f;   // skip boxes: a little wider than the 3-sigma cut
-constexpr float SAT_BALL = 8.66f; // (3 + 4 sqrt 2) sigma_max
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
 constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
-constexpr float NEG_HALF_LOG2E = -0.721347520444481703f;   // -log2(e)/2
 constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
 constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
 constexpr int NG = 10;            // general path: dmu[3], G_P[6], drho
@@ -94,7 +91,7 @@ __device__ __forceinline__ void to_frame(const float *X, const float *eu, const 
 }
 
 // gather one record and turn it into its view-space form for frame F
-template <bool CONE>
+template <bool CONE, int KER>
 __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, uint32_t gid,
                                             const float4 *__restrict__ rec,
                                             const float4 *__restrict__ crec, VRec &out)
@@ -121,8 +118,8 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         float suu = quad_form(Sg, eu, eu), svv = quad_form(Sg, ev, ev), sww = quad_form(Sg, ew, ew);
         float suw = quad_form(Sg, eu, ew), svw = quad_form(Sg, ev, ew);
         float lo, hi;
-        if (cone_interval(SKIP_K2, g.dsd, mu_u, D, suu, suw, sww, lo, hi)) { ulo = lo; uhi = hi; }
-        if (cone_interval(SKIP_K2, g.dsd, mu_v, D, svv, svw, sww, lo, hi)) { vlo = lo; vhi = hi; }
+        if (cone_interval(Kern<KER>::SKIP, g.dsd, mu_u, D, suu, suw, sww, lo, hi)) { ulo = lo; uhi = hi; }
+        if (cone_interval(Kern<KER>::SKIP, g.dsd, mu_v, D, svv, svw, sww, lo, hi)) { vlo = lo; vhi = hi; }
         const float iD = 1.0f / D;
         const float u0 = g.dsd * mu_u * iD, v0 = g.dsd * mu_v * iD;
         // A(du, dv) = d~^T P' d~, d~ = (u0 + du, v0 + dv, dsd)
@@ -138,28 +135,28 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         const float Muu = guv * cu1 + guw * cu2;
         const float Muv = guv * cv1 + guw * cv2;
         const float Mvv = gvu * cv0 + gvw * cv2;
-        const float k = NEG_HALF_LOG2E;
+        const float k = Kern<KER>::QSCALE;
         out.c0 = make_float4(u0, v0, k * Muu, 2.0f * k * Muv);
         out.c1 = make_float4(k * Mvv, A0, 2.0f * au, 2.0f * av);
-        out.c2 = make_float4(Pf[0], 2.0f * Pf[1], Pf[3], rho * SQRT2PI);
+        out.c2 = make_float4(Pf[0], 2.0f * Pf[1], Pf[3], rho * Kern<KER>::FAC);
         // both segment ends (source, detector plane) beyond the 8.66-sigma ball
-        sat = D >= SAT_BALL * smax && (g.dsd - D) >= SAT_BALL * smax;
+        sat = D >= Kern<KER>::BALL * smax && (g.dsd - D) >= Kern<KER>::BALL * smax;
     } else {
-        float hu = sqrtf(SKIP_K2 * quad_form(Sg, eu, eu));
-        float hv = sqrtf(SKIP_K2 * quad_form(Sg, ev, ev));
+        float hu = sqrtf(Kern<KER>::SKIP * quad_form(Sg, eu, eu));
+        float hv = sqrtf(Kern<KER>::SKIP * quad_form(Sg, ev, ev));
         ulo = mu_u - hu; uhi = mu_u + hu; vlo = mu_v - hv; vhi = mu_v + hv;
         const float iA = 1.0f / Pf[5];
         const float rA = sqrtf(iA);
         // c = du e_v - dv e_u: M_uu = S'_vv, M_uv = -S'_uv, M_vv = S'_uu
-        const float k = NEG_HALF_LOG2E * iA;
+        const float k = Kern<KER>::QSCALE * iA;
         out.c0 = make_float4(mu_u, mu_v, k * Sf[3], -2.0f * k * Sf[1]);
         out.c1 = make_float4(k * Sf[0], iA, rA, 0.0f);
-        out.c2 = make_float4(0.0f, 0.0f, 0.0f, rho * SQRT2PI * rA);
+        out.c2 = make_float4(0.0f, 0.0f, 0.0f, rho * Kern<KER>::FAC * rA);
         if (g.pet) {
             float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
-            sat = rxy + SAT_BALL * smax <= sqrtf(g.radius2);
+            sat = rxy + Kern<KER>::BALL * smax <= sqrtf(g.radius2);
         } else {
-            sat = mu_w - SAT_BALL * smax >= g.t_a && mu_w + SAT_BALL * smax <= g.t_b;
+            sat = mu_w - Kern<KER>::BALL * smax >= g.t_a && mu_w + Kern<KER>::BALL * smax <= g.t_b;
         }
     }
     out.bb = make_float4(ulo, uhi, vlo, vhi);
@@ -264,14 +261,14 @@ struct ChunkLists {
     uint8_t gen[8][CH];
 };
 
-template <bool CONE>
+template <bool CONE, int KER>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
                                            uint32_t base, uint32_t stride, int cnt,
                                            const float4 *rec, const float4 *crec, VRec *sv,
                                            const float4 *wbox, int nw, uint32_t *msk)
 {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        prep_record<CONE>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i]);
+        prep_record<CONE, KER>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i]);
         const float4 bb = sv[i].bb;
         uint32_t m = 0;
         for (int w = 0; w < nw; w++) {
@@ -312,25 +309,38 @@ __device__ __forceinline__ void warp_box(const TileCtx &c, float4 *wbox)
 }
 
 // view-space value of one pair (without the |d~| factor of cone beam);
-// returns arg = -m log2(e)/2
-template <bool CONE>
+// returns arg = QSCALE m (Gaussian: -m log2(e)/2; Epanechnikov: -m/kappa^2)
+template <bool CONE, int KER>
 __device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float &arg)
 {
     const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
     const float du = u - c0.x, dv = v - c0.y;
     const float q = du * (c0.z * du + c0.w * dv) + c1.x * dv * dv;
+    float rA = 1.0f;
     if (CONE) {
         const float A = c1.y + du * (c1.z + c2.x * du + c2.y * dv) + dv * (c1.w + c2.z * dv);
-        const float rA = rsqrt_approx(A);
+        rA = rsqrt_approx(A);
         arg = q * (rA * rA);
-        return c2.w * rA * ex2_approx(arg);
+    } else {
+        arg = q;
     }
-    arg = q;
-    return c2.w * ex2_approx(arg);
+    if (KER == 1) {
+        const float c = 1.0f + arg;                      // 1 - m / kappa^2
+        const float pc = c > 0.0f ? c * sqrt_approx(c) : 0.0f;
+        return c2.w * rA * pc;
+    }
+    return c2.w * rA * ex2_approx(arg);
+}
+
+// the pair counts (Gaussian: m <= 9; Epanechnikov: inside the support)
+template <int KER>
+__device__ __forceinline__ bool vs_keep(float arg)
+{
+    return KER == 1 ? arg > -1.0f : arg >= CUT_ARG;
 }
 
 // forward integration of tile `tile` of geometry g (one ray per thread)
-template <bool CONE, bool STATS>
+template <bool CONE, bool STATS, int KER>
 __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -364,7 +374,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     const uint32_t nch = (nlist + CH - 1) / CH;
     for (uint32_t ch = 0; ch < nch; ch++) {
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
-        prep_chunk<CONE>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk);
+        prep_chunk<CONE, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk);
         __syncthreads();
         int nvs, ngen;
         build_lists(cnt, msk, lists, w, lane, nvs, ngen);
@@ -372,17 +382,17 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         for (; k + 1 < nvs; k += 2) {
             const int j0 = lists.vs[w][k], j1 = lists.vs[w][k + 1];
             float a0, a1;
-            const float v0 = vs_value<CONE>(sv[j0], u, v, a0);
-            const float v1 = vs_value<CONE>(sv[j1], u, v, a1);
-            acc_vs += a0 >= CUT_ARG ? v0 : 0.0f;
-            acc_vs += a1 >= CUT_ARG ? v1 : 0.0f;
-            if (STATS) n_kept += (a0 >= CUT_ARG) + (a1 >= CUT_ARG);
+            const float v0 = vs_value<CONE, KER>(sv[j0], u, v, a0);
+            const float v1 = vs_value<CONE, KER>(sv[j1], u, v, a1);
+            acc_vs += vs_keep<KER>(a0) ? v0 : 0.0f;
+            acc_vs += vs_keep<KER>(a1) ? v1 : 0.0f;
+            if (STATS) n_kept += vs_keep<KER>(a0) + vs_keep<KER>(a1);
         }
         if (k < nvs) {
             float a0;
-            const float v0 = vs_value<CONE>(sv[lists.vs[w][k]], u, v, a0);
-            acc_vs += a0 >= CUT_ARG ? v0 : 0.0f;
-            if (STATS) n_kept += a0 >= CUT_ARG;
+            const float v0 = vs_value<CONE, KER>(sv[lists.vs[w][k]], u, v, a0);
+            acc_vs += vs_keep<KER>(a0) ? v0 : 0.0f;
+            if (STATS) n_kept += vs_keep<KER>(a0);
         }
         if (ngen > 0) {
             const Ray ray = make_ray<CONE>(g, F, u, v);
@@ -390,7 +400,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                 const VRec &r = sv[lists.gen[w][k2]];
                 PairGeo q;
                 pair_geo(ray, r, q);
-                const float val = general_value(q, r.g0.w);
+                const float val = general_value<KER>(q, r.g0.w);
                 acc_gen += q.m <= PAIR_CUT2 ? val : 0.0f;
                 if (STATS) n_kept += q.m <= PAIR_CUT2;
             }
@@ -413,14 +423,14 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     }
 }
 
-template <bool CONE, bool STATS>
+template <bool CONE, bool STATS, int KER>
 __global__ void __launch_bounds__(256, 4) k_forward(DevGeom g, const float4 *__restrict__ rec,
                                                     const float4 *__restrict__ crec,
                                                     const uint32_t *__restrict__ gids,
                                                     const uint2 *__restrict__ ranges,
                                                     float *__restrict__ out, Stats *stats)
 {
-    forward_tile<CONE, STATS>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
+    forward_tile<CONE, STATS, KER>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
 }
 
 // symmetric 3x3 (packed 00 01 02 11 12 22) back to world: G = E G' E^T
@@ -460,7 +470,7 @@ __device__ __forceinline__ void cross_acc(const float *a, const float *b, float 
 //   dL/dmu' = -2 sum dL/dQ (S' c) x d~      (Q = c^T S' c, c = d~ x (S - mu'))
 //   dL/drho = sqrt(2 pi) Sw
 // out16 = (dmu[3], drho, G_P[6], G_S[6]) in world coordinates.
-template <bool CONE>
+template <bool CONE, int KER>
 __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, const float4 *rec,
                                            uint32_t gid, const float *s, float *out16)
 {
@@ -468,7 +478,7 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
     const float4 r0 = __ldg(r), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
     const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
     const float m[3] = { r0.x, r0.y, r0.z };
-    const float alpha = r0.w * SQRT2PI;
+    const float alpha = r0.w * Kern<KER>::FAC;
     const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
     float Sf[6];
     to_frame(Sh, eu, ev, ew, Sf);
@@ -536,7 +546,7 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
     out16[0] = dmuf[0] * eu[0] + dmuf[1] * ev[0] + dmuf[2] * ew[0];
     out16[1] = dmuf[0] * eu[1] + dmuf[1] * ev[1] + dmuf[2] * ew[1];
     out16[2] = dmuf[0] * eu[2] + dmuf[1] * ev[2] + dmuf[2] * ew[2];
-    out16[3] = SQRT2PI * Sw;
+    out16[3] = Kern<KER>::FAC * Sw;
     from_frame(GPf, eu, ev, ew, out16 + 4);
     from_frame(GSf, eu, ev, ew, out16 + 10);
 }
@@ -552,7 +562,7 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
 // 8-column groups that none of their boxes touches are skipped.  Within a row
 // the Q and A quadratics are evaluated in Horner form in du with the dv terms
 // hoisted.
-template <bool CONE, int TW>
+template <bool CONE, int TW, int KER>
 __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -602,7 +612,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
         uint32_t gid = 0;
         if (active) {
             gid = __ldg(gids + k);
-            prep_record<CONE>(g, F, gid, rec, crec, r);
+            prep_record<CONE, KER>(g, F, gid, rec, crec, r);
         } else {
             r.bb = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
             r.g2 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
@@ -673,9 +683,21 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                         iA = iAc;
                         arg = qv;
                     }
-                    const float wv = arg >= CUT_ARG ? gl_row[i] * rA * ex2_approx(arg) : 0.0f;
-                    const float h = 0.5f * wv * iA;
-                    const float gA = h * (arg * M_PER_ARG - 1.0f);
+                    float wv, h, gA;
+                    if (KER == 1) {
+                        // f = alpha A^-1/2 c^3/2, c = 1 - Q/(kappa^2 A): -dL/dQ / alpha =
+                        // 1.5 w rA iA sqrt(c) / kappa^2, dL/dA / alpha = w rA iA sqrt(c) (1.5 - 2c)
+                        const float c = 1.0f + arg;
+                        const float sc = c > 0.0f ? sqrt_approx(c) : 0.0f;
+                        const float t = gl_row[i] * rA * sc;
+                        wv = t * c;
+                        h = (1.5f / Kern<1>::KAPPA2) * t * iA;
+                        gA = t * iA * (1.5f - 2.0f * c);
+                    } else {
+                        wv = arg >= CUT_ARG ? gl_row[i] * rA * ex2_approx(arg) : 0.0f;
+                        h = 0.5f * wv * iA;
+                        gA = h * (arg * M_PER_ARG - 1.0f);
+                    }
                     const float hd = h * du, gd = gA * du;
                     H0 += h; H1 += hd; H2 += hd * du;
                     G0 += gA; G1 += gd; G2 += gd * du;
@@ -700,7 +722,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 if (!CONE) s[6] = s[11];   // parallel layout: [SQ.. (5), SA, Sw]
 #pragma unroll
                 for (int q = 0; q < NV_CONE; q++) any |= s[q] != 0.0f;
-                if (any) view_chain<CONE>(g, F, rec, gid, s, o);
+                if (any) view_chain<CONE, KER>(g, F, rec, gid, s, o);
             }
         }
         if (__any_sync(0xffffffffu, active && !vs)) {
@@ -721,7 +743,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                         // sgl holds dL/dI |d~|; the general form wants dL/dI
                         const float gw = CONE ? gw0 * rsqrtf(u * u + vj * vj + g.dsd * g.dsd) : gw0;
                         float pv[NG];
-                        general_grad(ray, q, r.g0.w, gw, pv);
+                        general_grad<KER>(ray, q, r.g0.w, gw, pv);
 #pragma unroll
                         for (int qq = 0; qq < NG; qq++) val[qq] += pv[qq];
                     }
@@ -745,7 +767,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
     }
 }
 
-template <bool CONE, int TW>
+template <bool CONE, int TW, int KER>
 __global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
                                                  const float4 *__restrict__ crec,
                                                  const uint32_t *__restrict__ gids,
@@ -753,7 +775,7 @@ __global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__r
                                                  const float *__restrict__ dLdI,
                                                  float4 *__restrict__ grad)
 {
-    adjoint_tile<CONE, TW>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
+    adjoint_tile<CONE, TW, KER>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
 }
 
 // Persistent forms over a batch of scans: every CTA takes (scan, tile) work
@@ -790,7 +812,7 @@ __global__ void __launch_bounds__(256, 3) k_forward_persistent(const ScanDesc *_
     int scan;
     while (next_item(d, nscan, total, queue, item, scan)) {
         const ScanDesc &sd = d[scan];
-        forward_tile<CONE, false>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+        forward_tile<CONE, false, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
                                   sd.out, nullptr);
     }
 }
@@ -803,7 +825,7 @@ __global__ void __launch_bounds__(ADJ_BS) k_adjoint_persistent(const ScanDesc *_
     int scan;
     while (next_item(d, nscan, total, queue, item, scan)) {
         const ScanDesc &sd = d[scan];
-        adjoint_tile<CONE, TW>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+        adjoint_tile<CONE, TW, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
                                sd.dLdI, sd.grad);
     }
 }
@@ -865,39 +887,44 @@ int persistent_grid(bool forward, bool cone, int tile_w, int tile_threads)
 
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, float *out, Stats *stats,
-                           cudaStream_t s)
+                           int ker, cudaStream_t s)
 {
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
     int bs = g.tile_w * g.tile_h;
-    if (g.kind == 1) {
-        if (stats) k_forward<true, true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
-        else k_forward<true, false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+#define RGRT_FWD(C, S, K) k_forward<C, S, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats)
+    if (ker == 1) {
+        if (g.kind == 1) { if (stats) RGRT_FWD(true, true, 1); else RGRT_FWD(true, false, 1); }
+        else { if (stats) RGRT_FWD(false, true, 1); else RGRT_FWD(false, false, 1); }
     } else {
-        if (stats) k_forward<false, true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
-        else k_forward<false, false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+        if (g.kind == 1) { if (stats) RGRT_FWD(true, true, 0); else RGRT_FWD(true, false, 0); }
+        else { if (stats) RGRT_FWD(false, true, 0); else RGRT_FWD(false, false, 0); }
     }
+#undef RGRT_FWD
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, const float *dLdI,
-                           float4 *grad, cudaStream_t s)
+                           float4 *grad, int ker, cudaStream_t s)
 {
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
     const int bs = ADJ_BS;
-#define RGRT_ADJ(CONE, TW) k_adjoint<CONE, TW><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
-    if (g.kind == 1) {
-        if (g.tile_w == 8) RGRT_ADJ(true, 8);
-        else if (g.tile_w == 16) RGRT_ADJ(true, 16);
-        else RGRT_ADJ(true, 32);
-    } else {
-        if (g.tile_w == 8) RGRT_ADJ(false, 8);
-        else if (g.tile_w == 16) RGRT_ADJ(false, 16);
-        else RGRT_ADJ(false, 32);
+#define RGRT_ADJ(CONE, TW, K) k_adjoint<CONE, TW, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
+#define RGRT_ADJ_K(K)                                         \
+    if (g.kind == 1) {                                        \
+        if (g.tile_w == 8) RGRT_ADJ(true, 8, K);              \
+        else if (g.tile_w == 16) RGRT_ADJ(true, 16, K);       \
+        else RGRT_ADJ(true, 32, K);                           \
+    } else {                                                  \
+        if (g.tile_w == 8) RGRT_ADJ(false, 8, K);             \
+        else if (g.tile_w == 16) RGRT_ADJ(false, 16, K);      \
+        else RGRT_ADJ(false, 32, K);                          \
     }
+    if (ker == 1) { RGRT_ADJ_K(1) } else { RGRT_ADJ_K(0) }
+#undef RGRT_ADJ_K
 #undef RGRT_ADJ
     count_launches(1);
     return cudaGetLastError();

@@ -291,6 +291,7 @@ __device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int6
 }
 
 // one ray per thread; blocks b0 .. b0 + gridDim.x - 1
+template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ ro,
                                                      const float4 *__restrict__ rd, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
         for (int i = 0; i < cnt; i++) {
             PairGeo q;
             pair_geo(ray, sr[i], q);
-            if (q.m <= PAIR_CUT2) acc += general_value(q, sr[i].g0.w);
+            if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w);
         }
     }
     if (valid) out[r] = acc;
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
 
 // one ray per thread; per Gaussian a transposed warp reduction of the pair
 // gradients and one atomic per component per warp
+template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ ro,
                                                      const float4 *__restrict__ rd, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
             if (!__any_sync(0xffffffffu, act)) continue;
             float v[NG_RAYS];
             if (act) {
-                general_grad(ray, q, sr[i].g0.w, w, v);
+                general_grad<KER>(ray, q, sr[i].g0.w, w, v);
             } else {
 #pragma unroll
                 for (int k = 0; k < NG_RAYS; k++) v[k] = 0.0f;
@@ -406,20 +408,22 @@ cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, i
 
 cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
                                 const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                float *out, cudaStream_t s)
+                                float *out, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    k_rays_forward<<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
+    if (ker == 1) k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
+    else k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
                                 const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, cudaStream_t s)
+                                const float *dLdI, float4 *grad, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    k_rays_adjoint<<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+    if (ker == 1) k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+    else k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
     count_launches(1);
     return cudaGetLastError();
 }

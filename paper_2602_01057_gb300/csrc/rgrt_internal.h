@@ -75,12 +75,13 @@ size_t sort_tmp_elems(uint32_t n);
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                         uint32_t n, int bits, uint32_t *tmp, cudaStream_t s);
 
+// ker: kernel of the primitives (RGRT_KERNEL_GAUSSIAN / RGRT_KERNEL_EPANECHNIKOV)
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, float *out, Stats *stats,
-                           cudaStream_t s);
+                           int ker, cudaStream_t s);
 cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
                            const uint32_t *gids, const uint2 *ranges, const float *dLdI,
-                           float4 *grad, cudaStream_t s);
+                           float4 *grad, int ker, cudaStream_t s);
 // one scan of a batch, as the persistent kernels see it
 struct ScanDesc {
     DevGeom g;
@@ -107,8 +108,8 @@ cudaError_t launch_param_chain(const float *mu, const float *ls, const float *q,
                                int64_t n, const float4 *grad, float *g_mu, float *g_ls,
                                float *g_q, float *g_rho, cudaStream_t s);
 cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, float kappa,
-                        float eps, float *dLdI, double *partial, int nblk, float *loss_out,
-                        cudaStream_t s);
+                        float eps, const float *mult, const float *add, float *dLdI, double *partial,
+                        int nblk, float *loss_out, cudaStream_t s);
 int loss_blocks(int64_t n);
 // Adam; bc_dev (optional) supplies the bias corrections (1 - beta^t) from
 // device memory instead of bc1, bc2; skip (optional) leaves everything
@@ -135,10 +136,10 @@ cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, i
                              cudaStream_t s);
 cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
                                 const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                float *out, cudaStream_t s);
+                                float *out, int ker, cudaStream_t s);
 cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
                                 const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, cudaStream_t s);
+                                const float *dLdI, float4 *grad, int ker, cudaStream_t s);
 
 // ---- voxelisation (voxel.cu) ----------------------------------------------
 // voxel (i, j, k) centre = (ox + i sx, oy + j sy, oz + k sz); bricks of
@@ -155,6 +156,6 @@ cudaError_t launch_vox_emit(int64_t n, const VolDev &v, const uint32_t *cnt, con
 // ranges[b] = [first, last + 1) of brick b in the sorted keys (zeroed first)
 cudaError_t launch_vox_ranges(const uint32_t *keys, uint32_t nk, uint2 *ranges, uint32_t nb, cudaStream_t s);
 cudaError_t launch_voxelize(const float4 *rec, const float4 *crec, const uint32_t *gids, const uint2 *ranges,
-                            const VolDev &v, float *out, cudaStream_t s);
+                            const VolDev &v, float *out, int ker, cudaStream_t s);
 
 }  // namespace rgrt

@@ -55,6 +55,7 @@ struct rgrt_gauss {
     float4 *rec = nullptr, *crec = nullptr;
     float *adam_m = nullptr, *adam_v = nullptr;
     unsigned long long version = 1;
+    int kernel = RGRT_KERNEL_GAUSSIAN;   // kernel of the primitives
     size_t bytes = 0;
 };
 
@@ -68,6 +69,8 @@ struct rgrt_geom {
     bool rays = false;
     float4 *d_ro = nullptr, *d_rd = nullptr;
     int n_blocks = 0;
+    // measurement model per ray (optional): multiplicative factor, additive background
+    float *d_mult = nullptr, *d_add = nullptr;
     int tiles_per_view = 0;
     size_t bytes = 0;
 };

@@ -104,6 +104,7 @@ __global__ void k_vox_ranges(const uint32_t *__restrict__ keys, uint32_t nk, uin
     if (i == nk - 1 || keys[i + 1] != b) ranges[b].y = i + 1;
 }
 
+template <int KER>
 __global__ void __launch_bounds__(VB) k_voxelize(const float4 *__restrict__ rec,
                                                  const float4 *__restrict__ crec,
                                                  const uint32_t *__restrict__ gids,
@@ -151,9 +152,16 @@ __global__ void __launch_bounds__(VB) k_voxelize(const float4 *__restrict__ rec,
             const float t0 = g1.x * dx + g1.y * dy + g1.z * dz;
             const float t1 = g1.y * dx + g1.w * dy + g2.x * dz;
             const float t2 = g1.z * dx + g2.x * dy + g2.y * dz;
-            const float arg = (dx * t0 + dy * t1 + dz * t2) * NEG_HALF_LOG2E_V;
-            const float f = g0.w * ex2_fast(arg);
-            acc += arg >= VOX_CUT_ARG ? f : 0.0f;
+            const float md = dx * t0 + dy * t1 + dz * t2;
+            if (KER == 1) {
+                // Epanechnikov: rho (1 - m / kappa^2)_+, kappa^2 = 7
+                const float c = 1.0f - md * (1.0f / 7.0f);
+                acc += c > 0.0f ? g0.w * c : 0.0f;
+            } else {
+                const float arg = md * NEG_HALF_LOG2E_V;
+                const float f = g0.w * ex2_fast(arg);
+                acc += arg >= VOX_CUT_ARG ? f : 0.0f;
+            }
         }
     }
     if (i < v.nx && j < v.ny && k < v.nz) out[((int64_t)k * v.ny + j) * v.nx + i] = acc;
@@ -188,11 +196,12 @@ cudaError_t launch_vox_ranges(const uint32_t *keys, uint32_t nk, uint2 *ranges, 
 }
 
 cudaError_t launch_voxelize(const float4 *rec, const float4 *crec, const uint32_t *gids, const uint2 *ranges,
-                            const VolDev &v, float *out, cudaStream_t s)
+                            const VolDev &v, float *out, int ker, cudaStream_t s)
 {
     const int64_t nb = (int64_t)v.bx * v.by * v.bz;
     if (nb <= 0) return cudaSuccess;
-    k_voxelize<<<(unsigned)nb, VB, 0, s>>>(rec, crec, gids, ranges, v, out);
+    if (ker == 1) k_voxelize<1><<<(unsigned)nb, VB, 0, s>>>(rec, crec, gids, ranges, v, out);
+    else k_voxelize<0><<<(unsigned)nb, VB, 0, s>>>(rec, crec, gids, ranges, v, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -19,6 +19,8 @@ from . import build as _build
 RGRT_OK = 0
 RGRT_COPY, RGRT_BORROW = 0, 1
 RGRT_LOSS_L2, RGRT_LOSS_POISSON = 0, 1
+RGRT_KERNEL_GAUSSIAN, RGRT_KERNEL_EPANECHNIKOV = 0, 1
+KERNELS = {"gaussian": RGRT_KERNEL_GAUSSIAN, "epanechnikov": RGRT_KERNEL_EPANECHNIKOV}
 _KIND = {"parallel": 0, "cone": 1, "pet": 2}
 
 
@@ -59,10 +61,12 @@ _EXPORTS = {
     "gaussians_create": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_int,
                           ctypes.POINTER(_VP)], ctypes.c_int),
     "gaussians_destroy": ([_VP], ctypes.c_int),
+    "gaussians_set_kernel": ([_VP, ctypes.c_int], ctypes.c_int),
     "gaussians_get": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gaussians_set": ([_VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "gaussians_count": ([_VP], ctypes.c_int64),
     "geometry_set": ([_VP, ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], ctypes.c_int),
+    "geometry_set_corrections": ([_VP, _VP, _VP], ctypes.c_int),
     "geometry_set_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_destroy": ([_VP], ctypes.c_int),
     "geometry_num_rays": ([_VP], ctypes.c_int64),
@@ -242,6 +246,12 @@ class Gaussians:
         except Exception:
             pass
 
+    def set_kernel(self, kernel):
+        """"gaussian" or "epanechnikov" (or an RGRT_KERNEL_* code)."""
+        k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        _check(lib().gaussians_set_kernel(self.h, k))
+        return self
+
     def get(self, mu=None, ls=None, q=None, rho=None, stream=None):
         _check(lib().gaussians_get(self.h, _ptr(mu), _ptr(ls), _ptr(q), _ptr(rho), _stream(stream)))
 
@@ -296,6 +306,13 @@ class Geometry:
         self.ctx = ctx
         self.desc = d
         self.n_rays = int(lib().geometry_num_rays(h))
+
+    def set_corrections(self, mult=None, add=None):
+        """Per-ray measurement model of the losses: mult I + add (see the C header)."""
+        mult = _f32c(mult) if mult is not None else None
+        add = _f32c(add) if add is not None else None
+        _check(lib().geometry_set_corrections(self.h, _ptr(mult), _ptr(add)))
+        return self
 
     def close(self):
         if self.h:

@@ -383,3 +383,43 @@ def test_view_subset_geometry_bit_exact(rg, ctx, torch, oracle, name):
         want = full.reshape(V, H, W)[idx].reshape(-1)
     np.testing.assert_array_equal(part, want)
     assert fwd_err(part, oracle.forward(sub, G)) < FWD_TOL
+
+
+@pytest.mark.parametrize("loss", ["l2", "poisson"])
+def test_loss_with_measurement_model(rg, ctx, torch, oracle, loss):
+    """geometry_set_corrections: per-ray factor (attenuation) and background
+    (scatter + randoms) in the loss; loss and gradient against the oracle."""
+    G, gd = case("cone_small")
+    R = synth.num_rays(gd)
+    rng = np.random.default_rng(8)
+    mult = rng.uniform(0.3, 1.0, R).astype(np.float32)
+    add = rng.uniform(0.0, 0.2, R).astype(np.float32)
+    ref_fwd = oracle.forward(gd, G)
+    I_true = oracle.forward(gd, synth.perturbed(G, 78, pos_std=0.01))["I"]
+    if loss == "l2":
+        y = (mult * I_true + add).astype(np.float32)
+        kappa, eps = 1.0, 0.0
+        L_ref, dLdI = oracle.loss_l2(ref_fwd["I"], y, mult, add)
+        kind = rg.RGRT_LOSS_L2
+    else:
+        kappa, eps = 50.0, 1e-3
+        y = rng.poisson(kappa * mult * I_true + add + eps).astype(np.float32)
+        L_ref, dLdI = oracle.loss_poisson(ref_fwd["I"], y, kappa, eps, mult, add)
+        kind = rg.RGRT_LOSS_POISSON
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    geom = rg.Geometry(ctx, gd).set_corrections(mult, add)
+    n = gs.n
+    outs = [np.zeros(s, np.float32) for s in ((n, 3), (n, 3), (n, 4), (n,))]
+    lo = np.zeros(1, np.float32)
+    rg.loss_grad(ctx, gs, geom, y, kind, rg.adam_params(kappa=kappa, poisson_eps=eps), lo, *outs)
+    assert float(lo[0]) == pytest.approx(L_ref, rel=1e-5)
+    ref = oracle.backward(gd, G, dLdI)
+    got = dict(zip(("mu", "ls", "q", "rho"), outs))
+    for k in ("mu", "ls", "q", "rho"):
+        assert grad_err(got, ref, k) < GRAD_TOL, k
+    # clearing the corrections restores the plain loss
+    geom.set_corrections(None, None)
+    rg.loss_grad(ctx, gs, geom, y, kind, rg.adam_params(kappa=kappa, poisson_eps=eps), lo)
+    L_plain = (oracle.loss_l2(ref_fwd["I"], y) if loss == "l2"
+               else oracle.loss_poisson(ref_fwd["I"], y, kappa, eps))[0]
+    assert float(lo[0]) == pytest.approx(L_plain, rel=1e-5)

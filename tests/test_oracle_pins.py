@@ -412,6 +412,30 @@ def test_losses_finite_differences(oracle):
             assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-6)
 
 
+def test_losses_with_measurement_model(oracle):
+    """Per-ray factor and background: finite differences, and a factor /
+    background that reduce to the plain losses on rescaled data."""
+    rng = np.random.default_rng(6)
+    I = rng.uniform(0.5, 2.0, 40)
+    y = rng.poisson(30.0, 40).astype(np.float64)
+    m = rng.uniform(0.2, 0.9, 40)
+    a = rng.uniform(0.5, 3.0, 40)
+    for lossf in (lambda v: oracle.loss_poisson(v, y, 20.0, 1e-9, m, a),
+                  lambda v: oracle.loss_l2(v, y / 20.0, m, a)):
+        L, g = lossf(I)
+        for k in range(0, 40, 5):
+            e = np.zeros(40); e[k] = 1e-6
+            fd = (lossf(I + e)[0] - lossf(I - e)[0]) / 2e-6
+            assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-6)
+    # m I + a with m = 1, a = 0 is the plain loss; Poisson with m and a equals the
+    # plain Poisson loss of the predicted mean (m I + a / kappa)
+    assert oracle.loss_l2(I, y, np.ones(40), np.zeros(40))[0] == oracle.loss_l2(I, y)[0]
+    Lm, gm = oracle.loss_poisson(I, y, 20.0, 1e-9, m, a)
+    Lp, gp = oracle.loss_poisson(m * I + a / 20.0, y, 20.0, 1e-9)
+    assert Lm == pytest.approx(Lp, rel=1e-12)
+    np.testing.assert_allclose(gm, m * gp, rtol=1e-12)
+
+
 def test_adam_matches_torch():
     torch = pytest.importorskip("torch")
     from oracle import oracle as o
