@@ -160,3 +160,23 @@ def test_invalid_rays_rejected(rg, ctx, bad):
         R["o"][200, 1] = np.nan
     with pytest.raises(rg.RgrtError):
         rg.Geometry(ctx, R)
+
+
+def test_fully_3d_pet_lors(rg, ctx, torch, oracle):
+    """Oblique PET segments (ring differences up to 3) as explicit rays."""
+    R = synth.pet_rays_3d(8, 4.0, 400.0, 576, 24, 65, max_ring_diff=3)
+    G, _ = synth.workload_c3(2, n=3000, n_angles=24, n_radial=65, n_planes=15)
+    G["mu"][:, 2] *= 0.25            # keep the activity within the 8 rings' axial field
+    I, gs, geom = gpu_fwd(torch, rg, ctx, G, R)
+    ref = oracle.forward_list(R["o"], R["d"], R["t"], G)
+    assert ref["pairs"] > 10000
+    assert fwd_err(I, ref) < FWD_TOL
+    w = synth.random_weights(I.size, 35).astype(np.float32)
+    n = gs.n
+    outs = [torch.empty(s, device="cuda") for s in ((n, 3), (n, 3), (n, 4), (n,))]
+    rg.project_backward(ctx, gs, geom, torch.from_numpy(w).cuda(), *outs)
+    torch.cuda.synchronize()
+    got = dict(zip(("mu", "ls", "q", "rho"), (o.cpu().numpy() for o in outs)))
+    gref = oracle.backward_list(R["o"], R["d"], R["t"], G, w.astype(np.float64))
+    for k in ("mu", "ls", "q", "rho"):
+        assert grad_err(got, gref, k) < GRAD_TOL, k

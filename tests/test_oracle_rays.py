@@ -117,3 +117,24 @@ def test_rays_missing_everything_are_zero(oracle):
     t = np.tile([[-np.inf, np.inf]], (10, 1))
     out = oracle.forward_list(o, d, t, G)
     assert np.all(out["I"] == 0.0) and out["pairs"] == 0
+
+
+def test_pet_3d_direct_planes_are_the_ring_sinogram(oracle):
+    """The ring-difference-0 LORs of the 3-D PET generator are the direct
+    planes (plane 2r) of the 2-D ring geometry with half the ring pitch."""
+    n_rings, pitch, n_ang, n_rad = 6, 4.0, 12, 41
+    R = synth.pet_rays_3d(n_rings, pitch, 400.0, 576, n_ang, n_rad, max_ring_diff=2)
+    G = synth.gaussians_uniform(40, 33, half_box=60.0, log_sigma=math.log(5.0))
+    G["mu"][:, 2] *= 0.15
+    g2 = synth.geom_pet(n_ang, n_rad, 2 * n_rings - 1, 400.0, 576, pitch / 2)
+    ref = oracle.forward(g2, G)["I"].reshape(2 * n_rings - 1, n_ang, n_rad)
+    ix = R["index"]
+    sel = ix[:, 0] == ix[:, 1]
+    got = oracle.forward_list(R["o"][sel], R["d"][sel], R["t"][sel], G)["I"]
+    want = ref[2 * ix[sel, 0], ix[sel, 2], ix[sel, 3]]
+    assert np.count_nonzero(want) > 100
+    np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-6 * np.abs(want).max())
+    # every ring pair within the difference appears once per (angle, radial)
+    n_pairs = sum(1 for a in range(n_rings) for b in range(n_rings) if abs(a - b) <= 2)
+    assert R["o"].shape[0] == n_pairs * n_ang * n_rad
+    assert len({tuple(r) for r in ix.tolist()}) == ix.shape[0]
