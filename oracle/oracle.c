@@ -226,6 +226,9 @@ void or_set_kernel(int kernel) { og_kern = kernel; }
 
 typedef struct {
     double A, B, C, m, wa, wb, phi, K, f;  /* K = rho sqrt(2pi/A) e^{-m/2} */
+    /* exponent of the value: m, or m' of the time-of-flight weighted form,
+     * and the weight's normalisation factor (1 without time of flight) */
+    double mv, sc;
     /* Epanechnikov: clipped interval [s0, s1] around the line's closest point
      * to mu (s = t + B/A); ea, eb: the ends are the segment's own */
     double s0, s1, c;
@@ -256,8 +259,17 @@ static void og_eval_epan(double ta, double tb, double rho, og_pairval *r)
     r->f = rho * r->K;
 }
 
+/*
+ * Time of flight (the paper's future-work section plans TOF PET): a ray may
+ * carry a Gaussian weight N(t; t_c, sigma_T^2) along itself (tau = 1 /
+ * sigma_T^2; tau = 0: none).  The weighted integrand exp(-(A t^2 + 2 B t +
+ * C)/2) N(t) is again of the form of Eq. 7 with A' = A + tau, B' = B - tau t_c,
+ * C' = C + tau t_c^2 and the factor sqrt(tau / 2 pi); the pair still counts by
+ * its spatial m (the 3-sigma cut).
+ */
 static void og_eval(const double o[3], const double d[3], double ta, double tb,
-                    const double mu[3], double P[3][3], double rho, og_pairval *r)
+                    const double mu[3], double P[3][3], double rho, double tc, double tau,
+                    og_pairval *r)
 {
     double del[3] = { o[0] - mu[0], o[1] - mu[1], o[2] - mu[2] };
     double Pd[3], Pdel[3];
@@ -269,15 +281,26 @@ static void og_eval(const double o[3], const double d[3], double ta, double tb,
     r->B = d[0] * Pdel[0] + d[1] * Pdel[1] + d[2] * Pdel[2];
     r->C = del[0] * Pdel[0] + del[1] * Pdel[1] + del[2] * Pdel[2];
     r->m = r->C - r->B * r->B / r->A;                              /* Eq. 9 */
+    r->mv = r->m;
+    r->sc = 1.0;
     if (og_kern == 1) {
         og_eval_epan(ta, tb, rho, r);
         return;
+    }
+    double scale = 1.0;
+    if (tau > 0.0) {
+        r->A += tau;
+        r->B -= tau * tc;
+        r->C += tau * tc * tc;
+        r->mv = r->C - r->B * r->B / r->A;
+        scale = sqrt(tau / (2.0 * OG_PI));
+        r->sc = scale;
     }
     double s2A = sqrt(2.0 * r->A);
     r->wa = (r->A * ta + r->B) / s2A;
     r->wb = (r->A * tb + r->B) / s2A;
     r->phi = og_phi(r->wa, r->wb);
-    r->K = rho * sqrt(2.0 * OG_PI / r->A) * exp(-0.5 * r->m);      /* Eq. 11 */
+    r->K = scale * rho * sqrt(2.0 * OG_PI / r->A) * exp(-0.5 * r->mv);      /* Eq. 11 */
     r->f = r->K * r->phi;
 }
 
@@ -334,7 +357,8 @@ static void og_pair_grad(const double o[3], const double d[3], double ta, double
         for (int b = 0; b < 3; b++)
             gP[a][b] += wgt * (fA * d[a] * d[b] + fB * 0.5 * (d[a] * del[b] + del[a] * d[b])
                                + fC * del[a] * del[b]);
-    *grho += wgt * (rho != 0.0 ? r->f / rho : sqrt(2.0 * OG_PI / A) * exp(-0.5 * r->m) * r->phi);
+    *grho += wgt * (rho != 0.0 ? r->f / rho
+                               : r->sc * sqrt(2.0 * OG_PI / A) * exp(-0.5 * r->mv) * r->phi);
 }
 
 /* dL/dP (symmetric) and the parameters -> dL/dl, dL/dq  (P = R diag(e^{-2l}) R^T) */
@@ -493,7 +517,7 @@ void or_pair(const double *o, const double *d, double ta, double tb,
     double Sig[3][3], P[3][3], m3[3] = { mu[0], mu[1], mu[2] };
     og_cov(ls, q, Sig, P);
     og_pairval r;
-    og_eval(o, d, ta, tb, m3, P, rho, &r);
+    og_eval(o, d, ta, tb, m3, P, rho, 0.0, 0.0, &r);
     out[0] = r.f; out[1] = r.m; out[2] = r.A; out[3] = r.B; out[4] = r.C;
 }
 
@@ -504,7 +528,7 @@ void or_pair_grad(const double *o, const double *d, double ta, double tb,
     double Sig[3][3], P[3][3], m3[3] = { mu[0], mu[1], mu[2] };
     og_cov(ls, q, Sig, P);
     og_pairval r;
-    og_eval(o, d, ta, tb, m3, P, rho, &r);
+    og_eval(o, d, ta, tb, m3, P, rho, 0.0, 0.0, &r);
     double gm[3] = { 0, 0, 0 }, gP[3][3] = { { 0 } }, grho = 0.0, gl[3], gq[4];
     og_pair_grad(o, d, ta, tb, m3, P, rho, 1.0, &r, gm, gP, &grho);
     og_chain(ls, q, gP, gl, gq);
@@ -584,7 +608,7 @@ void or_forward(const og_geom *g, int64_t n, const float *mu, const float *ls, c
                     double o[3], d[3], ta, tb;
                     og_ray(g, v, j, i, o, d, &ta, &tb);
                     og_pairval r;
-                    og_eval(o, d, ta, tb, m3, P[k], rho[k], &r);
+                    og_eval(o, d, ta, tb, m3, P[k], rho[k], 0.0, 0.0, &r);
                     int64_t x = og_index(g, v, j, i);
                     og_accum(r.f, r.m, cut2, band, I + x, Ilo + x, Ihi + x);
                     if (r.m <= cut2) npair++;
@@ -613,7 +637,7 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
         for (int64_t k = 0; k < n; k++) {
             double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
             og_pairval pv;
-            og_eval(o, d, ta, tb, m3, P[k], rho[k], &pv);
+            og_eval(o, d, ta, tb, m3, P[k], rho[k], 0.0, 0.0, &pv);
             og_accum(pv.f, pv.m, cut2, band, &s, &slo, &shi);
         }
         I[r] = s; Ilo[r] = slo; Ihi[r] = shi;
@@ -630,11 +654,11 @@ typedef struct {
 } og_gradacc;
 
 static void og_grad_pair(og_gradacc *a, const double o[3], const double d[3], double ta, double tb,
-                         const double m3[3], double P[3][3], double rho, double w, double cut2,
-                         double band, const float *ls, const float *q)
+                         double tc, double tau, const double m3[3], double P[3][3], double rho,
+                         double w, double cut2, double band, const float *ls, const float *q)
 {
     og_pairval r;
-    og_eval(o, d, ta, tb, m3, P, rho, &r);
+    og_eval(o, d, ta, tb, m3, P, rho, tc, tau, &r);
     if (!(r.m <= cut2 + band) || w == 0.0) return;
     if (r.m <= cut2 - band) {
         og_pair_grad(o, d, ta, tb, m3, P, rho, w, &r, a->gm, a->gP, &a->grho);
@@ -708,7 +732,7 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
                     og_ray(g, v, j, i, o, d, &ta, &tb);
-                    og_grad_pair(&acc, o, d, ta, tb, m3, P, rho[k], dLdI[og_index(g, v, j, i)], cut2,
+                    og_grad_pair(&acc, o, d, ta, tb, 0.0, 0.0, m3, P, rho[k], dLdI[og_index(g, v, j, i)], cut2,
                                  band, ls + 3 * k, q + 4 * k);
                 }
         }
@@ -722,18 +746,27 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
  * d[3r..3r+2] (any nonzero length; normalised here), over t in
  * [t[2r], t[2r+1]] measured along the unit direction (+-inf allowed).
  * Every (ray, Gaussian) pair is evaluated: the plain definition, Eqs. 7-12
- * with the cut m <= cut2 and the band bracket as above.
+ * with the cut m <= cut2 and the band bracket as above.  tof (may be null):
+ * per ray the time-of-flight centre and width (Gaussian kernel only).
  */
-static void og_list_ray(const double *o, const double *d, const double *t, int64_t r,
-                        double oo[3], double dd[3], double *ta, double *tb)
+static void og_list_ray(const double *o, const double *d, const double *t, const double *tof, int64_t r,
+                        double oo[3], double dd[3], double *ta, double *tb, double *tc, double *tau)
 {
     double len = sqrt(d[3 * r] * d[3 * r] + d[3 * r + 1] * d[3 * r + 1] + d[3 * r + 2] * d[3 * r + 2]);
     for (int c = 0; c < 3; c++) { oo[c] = o[3 * r + c]; dd[c] = d[3 * r + c] / len; }
     *ta = t[2 * r];
     *tb = t[2 * r + 1];
+    /* time of flight: tof[2r] = centre t_c, tof[2r + 1] = sigma_T (<= 0 or inf: none) */
+    *tc = 0.0;
+    *tau = 0.0;
+    if (tof && tof[2 * r + 1] > 0.0 && isfinite(tof[2 * r + 1])) {
+        *tc = tof[2 * r];
+        *tau = 1.0 / (tof[2 * r + 1] * tof[2 * r + 1]);
+    }
 }
 
-void or_forward_list(int64_t nr, const double *o, const double *d, const double *t, int64_t n,
+void or_forward_list(int64_t nr, const double *o, const double *d, const double *t, const double *tof,
+                     int64_t n,
                      const float *mu, const float *ls, const float *q, const float *rho, double cut2,
                      double band, int nthreads, double *I, double *Ilo, double *Ihi, int64_t *pairs)
 {
@@ -743,12 +776,12 @@ void or_forward_list(int64_t nr, const double *o, const double *d, const double 
     int64_t npair = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : npair)
     for (int64_t r = 0; r < nr; r++) {
-        double oo[3], dd[3], ta, tb, s = 0.0, slo = 0.0, shi = 0.0;
-        og_list_ray(o, d, t, r, oo, dd, &ta, &tb);
+        double oo[3], dd[3], ta, tb, tc, tau, s = 0.0, slo = 0.0, shi = 0.0;
+        og_list_ray(o, d, t, tof, r, oo, dd, &ta, &tb, &tc, &tau);
         for (int64_t k = 0; k < n; k++) {
             double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
             og_pairval pv;
-            og_eval(oo, dd, ta, tb, m3, P[k], rho[k], &pv);
+            og_eval(oo, dd, ta, tb, m3, P[k], rho[k], tc, tau, &pv);
             og_accum(pv.f, pv.m, cut2, band, &s, &slo, &shi);
             if (pv.m <= cut2) npair++;
         }
@@ -758,7 +791,8 @@ void or_forward_list(int64_t nr, const double *o, const double *d, const double 
     free(P);
 }
 
-void or_backward_list(int64_t nr, const double *o, const double *d, const double *t, int64_t n,
+void or_backward_list(int64_t nr, const double *o, const double *d, const double *t, const double *tof,
+                      int64_t n,
                       const float *mu, const float *ls, const float *q, const float *rho, double cut2,
                       double band, const double *dLdI, int nthreads, double *g_mu, double *g_ls,
                       double *g_q, double *g_rho, double *lohi)
@@ -772,9 +806,10 @@ void or_backward_list(int64_t nr, const double *o, const double *d, const double
         og_gradacc acc;
         memset(&acc, 0, sizeof(acc));
         for (int64_t r = 0; r < nr; r++) {
-            double oo[3], dd[3], ta, tb;
-            og_list_ray(o, d, t, r, oo, dd, &ta, &tb);
-            og_grad_pair(&acc, oo, dd, ta, tb, m3, P, rho[k], dLdI[r], cut2, band, ls + 3 * k, q + 4 * k);
+            double oo[3], dd[3], ta, tb, tc, tau;
+            og_list_ray(o, d, t, tof, r, oo, dd, &ta, &tb, &tc, &tau);
+            og_grad_pair(&acc, oo, dd, ta, tb, tc, tau, m3, P, rho[k], dLdI[r], cut2, band, ls + 3 * k,
+                         q + 4 * k);
         }
         og_grad_finish(&acc, k, ls + 3 * k, q + 4 * k, g_mu, g_ls, g_q, g_rho, lohi);
     }

@@ -240,30 +240,43 @@ def _ray_arrays(o, d, t):
     return o, d, t
 
 
-def forward_list(o, d, t, G, cut2=CUT2, band=BAND, nthreads=0):
+def _tof(tof, nr):
+    if tof is None:
+        return None
+    tof = _f64(tof).reshape(-1, 2)
+    assert tof.shape[0] == nr
+    return tof
+
+
+def forward_list(o, d, t, G, cut2=CUT2, band=BAND, nthreads=0, tof=None):
     """FP64 projection of explicit rays (o[R,3], d[R,3] any length, t[R,2]
-    along the unit direction): dict(I, I_lo, I_hi, pairs); every pair evaluated."""
+    along the unit direction; tof[R,2] = time-of-flight centre and width, or
+    None): dict(I, I_lo, I_hi, pairs); every pair evaluated."""
     o, d, t = _ray_arrays(o, d, t)
+    tf = _tof(tof, o.shape[0])
     nr = o.shape[0]
     n, mu, ls, q, rho = _gauss(G)
     I = np.zeros(nr); Ilo = np.zeros(nr); Ihi = np.zeros(nr)
     pairs = ctypes.c_int64(0)
-    lib().or_forward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), ctypes.c_int64(n), _p(mu), _p(ls),
+    lib().or_forward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), None if tf is None else _p(tf),
+                          ctypes.c_int64(n), _p(mu), _p(ls),
                           _p(q), _p(rho), ctypes.c_double(cut2), ctypes.c_double(band),
                           ctypes.c_int(nthreads), _p(I), _p(Ilo), _p(Ihi), ctypes.byref(pairs))
     return dict(I=I, I_lo=Ilo, I_hi=Ihi, pairs=int(pairs.value))
 
 
-def backward_list(o, d, t, G, dLdI, cut2=CUT2, band=BAND, nthreads=0):
+def backward_list(o, d, t, G, dLdI, cut2=CUT2, band=BAND, nthreads=0, tof=None):
     """FP64 adjoint for explicit rays; same outputs as backward()."""
     o, d, t = _ray_arrays(o, d, t)
+    tf = _tof(tof, o.shape[0])
     nr = o.shape[0]
     n, mu, ls, q, rho = _gauss(G)
     w = _f64(dLdI).reshape(-1)
     assert w.size == nr
     gm = np.zeros((n, 3)); gl = np.zeros((n, 3)); gq = np.zeros((n, 4)); gr = np.zeros(n)
     lohi = np.zeros((n, 22))
-    lib().or_backward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), ctypes.c_int64(n), _p(mu), _p(ls),
+    lib().or_backward_list(ctypes.c_int64(nr), _p(o), _p(d), _p(t), None if tf is None else _p(tf),
+                           ctypes.c_int64(n), _p(mu), _p(ls),
                            _p(q), _p(rho), ctypes.c_double(cut2), ctypes.c_double(band), _p(w),
                            ctypes.c_int(nthreads), _p(gm), _p(gl), _p(gq), _p(gr), _p(lohi))
 
