@@ -179,6 +179,18 @@ int geometry_destroy(rgrt_geom *g);
  * ray-level form of Eq. 3 (o + t d) with no detector structure. */
 int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
                       const float *t2, rgrt_geom **out);
+
+/* Explicit rays with time of flight (TOF PET, which the paper's future-work
+ * section plans): as geometry_set_rays, plus tof2[2r] = t_c, the centre of
+ * ray r's Gaussian TOF kernel N(t; t_c, sigma_T^2) along the ray (t as in
+ * t2) and tof2[2r + 1] = sigma_T (<= 0 or infinite: no weight for that
+ * ray).  The weighted line integral keeps the closed form of Eqs. 7-12 with
+ * A + 1/sigma_T^2, B - t_c/sigma_T^2, C + t_c^2/sigma_T^2 and the factor
+ * 1/(sqrt(2 pi) sigma_T); a pair still counts by its spatial m <= 9.
+ * Gaussian kernel only (projections of an Epanechnikov set return
+ * RGRT_E_INVAL).  RGRT_E_INVAL also for a NaN width or centre. */
+int geometry_set_rays_tof(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
+                          const float *t2, const float *tof2, rgrt_geom **out);
 int64_t geometry_num_rays(const rgrt_geom *g);
 
 /* Measurement model of the losses (the attenuation, scatter and randoms that

@@ -411,11 +411,13 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
 int run_forward_rays(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float *out,
                      cudaStream_t s)
 {
+    if (geom->d_tof && g->kernel != RGRT_KERNEL_GAUSSIAN)
+        return fail(RGRT_E_INVAL, "time of flight takes the Gaussian kernel");
     TRY(build_records(ctx, g, s));
     ctx->last_keys = 0;
     return for_ray_ranges(ctx, g, geom, s, false, [&](int b0, int nb) -> int {
         PROF("k_rays_forward");
-        CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
+        CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
                                (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, g->kernel, s));
         return RGRT_OK;
     });
@@ -467,9 +469,11 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
                  ctx->bin_version == g->version;
     if (!reuse) TRY(build_records(ctx, g, s));
     if (geom->rays) {
+        if (geom->d_tof && g->kernel != RGRT_KERNEL_GAUSSIAN)
+            return fail(RGRT_E_INVAL, "time of flight takes the Gaussian kernel");
         TRY(for_ray_ranges(ctx, g, geom, s, reuse, [&](int b0, int nb) -> int {
             PROF("k_rays_adjoint");
-            CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->n_rays, b0, nb, g->rec,
+            CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
                                    (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, dLdI,
                                    (float4 *)ctx->grad.p, g->kernel, s));
             return RGRT_OK;
@@ -822,6 +826,7 @@ int geometry_destroy(rgrt_geom *g)
     if (g->rays) {
         dev_free(c, g->d_ro, sizeof(float4) * (size_t)g->n_rays);
         dev_free(c, g->d_rd, sizeof(float4) * (size_t)g->n_rays);
+        dev_free(c, g->d_tof, sizeof(float2) * (size_t)g->n_rays);
     } else {
         dev_free(c, g->d_tables, g->bytes);
     }
@@ -831,6 +836,12 @@ int geometry_destroy(rgrt_geom *g)
 
 int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
                       const float *t2, rgrt_geom **out)
+{
+    return geometry_set_rays_tof(ctx, n_rays, o3, d3, t2, nullptr, out);
+}
+
+int geometry_set_rays_tof(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
+                          const float *t2, const float *tof2, rgrt_geom **out)
 {
     TRY(check_ctx(ctx));
     if (!out) return fail(RGRT_E_INVAL, "null output");
@@ -851,7 +862,10 @@ int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const floa
     const size_t nb = sizeof(float4) * (size_t)n_rays;
     int r = dev_alloc(ctx, (void **)&g->d_ro, nb);
     if (r == RGRT_OK) r = dev_alloc(ctx, (void **)&g->d_rd, nb);
-    const void *po = nullptr, *pd = nullptr, *pt = nullptr;
+    const void *po = nullptr, *pd = nullptr, *pt = nullptr, *pf = nullptr;
+    if (r == RGRT_OK && tof2) r = dev_alloc(ctx, (void **)&g->d_tof, sizeof(float2) * (size_t)n_rays);
+    if (r == RGRT_OK && tof2)
+        r = stage_input(ctx, ctx->stage_in[3], tof2, 2 * sizeof(float) * (size_t)n_rays, s, &pf);
     if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[0], o3, 3 * sizeof(float) * (size_t)n_rays, s, &po);
     if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[1], d3, 3 * sizeof(float) * (size_t)n_rays, s, &pd);
     if (r == RGRT_OK) r = stage_input(ctx, ctx->stage_in[2], t2, 2 * sizeof(float) * (size_t)n_rays, s, &pt);
@@ -860,20 +874,21 @@ int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const floa
         uint32_t bad = 0;
         cudaError_t e = cudaMemsetAsync(ctx->total.p, 0, sizeof(uint32_t), s);
         if (e == cudaSuccess)
-            e = launch_rays_prep((const float *)po, (const float *)pd, (const float *)pt, n_rays, g->d_ro,
-                                 g->d_rd, (uint32_t *)ctx->total.p, s);
+            e = launch_rays_prep((const float *)po, (const float *)pd, (const float *)pt, (const float *)pf,
+                                 n_rays, g->d_ro, g->d_rd, g->d_tof, (uint32_t *)ctx->total.p, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, ctx->total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess)
             r = fail(RGRT_E_CUDA, "preparing rays: %s", cudaGetErrorString(e));
         else if (bad)
-            r = fail(RGRT_E_INVAL, "a ray has a non-finite origin, a zero or non-finite direction, or "
-                                   "a segment with t_a > t_b or NaN");
+            r = fail(RGRT_E_INVAL, "a ray has a non-finite origin, a zero or non-finite direction, "
+                                   "a segment with t_a > t_b or NaN, or a NaN time of flight");
     }
-    for (int k = 0; k < 3; k++) release(ctx, ctx->stage_in[k]);  // staged copies are not kept
+    for (int k = 0; k < 4; k++) release(ctx, ctx->stage_in[k]);  // staged copies are not kept
     if (r != RGRT_OK) {
         if (g->d_ro) dev_free(ctx, g->d_ro, nb);
         if (g->d_rd) dev_free(ctx, g->d_rd, nb);
+        if (g->d_tof) dev_free(ctx, g->d_tof, sizeof(float2) * (size_t)n_rays);
         delete g;
         return r;
     }

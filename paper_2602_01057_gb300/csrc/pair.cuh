@@ -25,6 +25,7 @@ struct PairGeo {
     float Pdx, Pdy, Pdz;   // P d
     float Ppx, Ppy, Ppz;   // P delta
     float A, B, C, rA, iA, m;
+    float sh;              // shift of the ray parameter to the recentred origin
 };
 
 // general path: A, B, C, m of Eq. 7/9 with delta re-based at the foot of the
@@ -36,6 +37,7 @@ __device__ __forceinline__ void pair_geo(const Ray &r, const Rec &s, PairGeo &q)
     float tau = r.dx * ex + r.dy * ey + r.dz * ez;
     q.px = ex - tau * r.dx; q.py = ey - tau * r.dy; q.pz = ez - tau * r.dz;
     q.ta = r.ta + tau; q.tb = r.tb + tau;
+    q.sh = tau;
     const float P00 = s.g1.x, P01 = s.g1.y, P02 = s.g1.z, P11 = s.g1.w, P12 = s.g2.x, P22 = s.g2.y;
     q.Pdx = P00 * r.dx + P01 * r.dy + P02 * r.dz;
     q.Pdy = P01 * r.dx + P11 * r.dy + P12 * r.dz;
@@ -173,15 +175,40 @@ __device__ __forceinline__ float epan_F(const EpanSeg &e, float A, float s)
 
 // general-path value of one pair (rho times the kernel's line integral over
 // the segment): Gaussian K Phi with K = rho sqrt(2pi/A) e^{-m/2}
+// Time of flight (explicit rays, Gaussian kernel): a weight N(t; t_c,
+// sigma_T^2) along the ray, tau = 1/sigma_T^2 (0: none), t_c in the ray's
+// parameter.  The weighted integrand keeps the form of Eq. 7 with
+// A' = A + tau, B' = B - tau t_c, C' = C + tau t_c^2 and the factor
+// sqrt(tau / 2 pi); tof_geo returns the primed pair (t_c moved to the
+// recentred origin like the segment) and that factor.
+__device__ __forceinline__ float tof_geo(const PairGeo &q, float tc_ray, float tau, PairGeo &qp,
+                                         float &tc)
+{
+    qp = q;
+    tc = tc_ray + q.sh;
+    qp.A = q.A + tau;
+    qp.B = q.B - tau * tc;
+    qp.C = q.C + tau * tc * tc;
+    qp.rA = rsqrtf(qp.A);
+    qp.iA = qp.rA * qp.rA;
+    qp.m = qp.C - qp.B * qp.B * qp.iA;
+    return sqrtf(tau) * INV_SQRT2PI;
+}
+
 template <int KER>
-__device__ __forceinline__ float general_value(const PairGeo &q, float rho)
+__device__ __forceinline__ float general_value(const PairGeo &q0, float rho, float tc_ray = 0.0f,
+                                               float tau = 0.0f)
 {
     if (KER == 1) {
-        const EpanSeg e = epan_seg(q);
-        return e.any ? rho * (epan_F(e, q.A, e.s1) - epan_F(e, q.A, e.s0)) : 0.0f;
+        const EpanSeg e = epan_seg(q0);
+        return e.any ? rho * (epan_F(e, q0.A, e.s1) - epan_F(e, q0.A, e.s0)) : 0.0f;
     }
+    PairGeo qt;
+    float tc, scale = 1.0f;
+    if (tau > 0.0f) scale = tof_geo(q0, tc_ray, tau, qt, tc);
+    const PairGeo &q = tau > 0.0f ? qt : q0;
     const float E = __expf(-0.5f * q.m);
-    const float K = rho * SQRT2PI * q.rA * E;
+    const float K = scale * rho * SQRT2PI * q.rA * E;
     const float sc = q.rA * SQRT_HALF;
     const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
     float phi = 1.0f;
@@ -195,10 +222,16 @@ __device__ __forceinline__ float general_value(const PairGeo &q, float rho)
 //   d mu = -(I - d d^T)(fB P d + 2 fC P p) - d st,
 //   G_P = fA d d^T + fB sym(d p^T) + fC p p^T.
 template <int KER>
-__device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, float rho, float gw,
-                                             float *val)
+__device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q0, float rho, float gw,
+                                             float *val, float tc_ray = 0.0f, float tau = 0.0f)
 {
     float fA, fB, fC, st, frho;
+    PairGeo qt;
+    float tc = 0.0f, scale = 1.0f;
+    if (KER == 0 && tau > 0.0f) scale = tof_geo(q0, tc_ray, tau, qt, tc);
+    // the partials below are taken in the primed pair; A', B', C' move with
+    // A, B, C one for one, and t_c shifts with the segment
+    const PairGeo &q = (KER == 0 && tau > 0.0f) ? qt : q0;
     if (KER == 1) {
         // Leibniz: the clipped ends +-a carry a zero integrand; the segment's
         // own ends move with B and A through s = t + B/A
@@ -221,7 +254,7 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
         frho = epan_F(e, q.A, e.s1) - epan_F(e, q.A, e.s0);
     } else {
         const float E = __expf(-0.5f * q.m);
-        const float K = rho * SQRT2PI * q.rA * E;
+        const float K = scale * rho * SQRT2PI * q.rA * E;
         const float sc = q.rA * SQRT_HALF;
         const float wa = (q.A * q.ta + q.B) * sc, wb = (q.A * q.tb + q.B) * sc;
         float phi = 1.0f, dPhiB = 0.0f, dPhiA = 0.0f;
@@ -241,7 +274,8 @@ __device__ __forceinline__ void general_grad(const Ray &ray, const PairGeo &q, f
         fB = f * q.B * q.iA + K * dPhiB;
         fA = -0.5f * f * q.iA * (1.0f + q.B * q.B * q.iA) + K * dPhiA;
         st = K * q.A * dPhiB;
-        frho = SQRT2PI * q.rA * E * phi;
+        if (tau > 0.0f) st += tau * (2.0f * fC * tc - fB);   // d f / d t_c
+        frho = scale * SQRT2PI * q.rA * E * phi;
     }
     // gradient w.r.t. the recentred delta: fB P d + 2 fC P delta
     const float gx = fB * q.Pdx + 2.0f * fC * q.Ppx;

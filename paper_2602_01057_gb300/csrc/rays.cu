@@ -42,8 +42,8 @@ __device__ __forceinline__ float norm2(float3 a) { return a.x * a.x + a.y * a.y 
 // normalise d, re-base o at the point of the line nearest the world origin
 // (FP64, once per ray), shift the segment accordingly; flag invalid rays
 __global__ void k_rays_prep(const float *__restrict__ o3, const float *__restrict__ d3,
-                            const float *__restrict__ t2, int64_t n, float4 *ro, float4 *rd,
-                            uint32_t *bad)
+                            const float *__restrict__ t2, const float *__restrict__ tof2, int64_t n,
+                            float4 *ro, float4 *rd, float2 *tof, uint32_t *bad)
 {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -53,16 +53,27 @@ __global__ void k_rays_prep(const float *__restrict__ o3, const float *__restric
     const double len = sqrt(dx * dx + dy * dy + dz * dz);
     const bool ok = isfinite(ox) && isfinite(oy) && isfinite(oz) && isfinite(len) && len > 0.0 &&
                     !isnan(ta) && !isnan(tb) && ta <= tb;
-    if (!ok) {
+    double tc = 0.0, sT = 0.0;
+    if (tof2) {
+        tc = tof2[2 * r];
+        sT = tof2[2 * r + 1];
+    }
+    const bool tof_ok = !tof2 || (!isnan(sT) && (!(sT > 0.0) || isinf(sT) || isfinite(tc)));
+    if (!ok || !tof_ok) {
         atomicOr(bad, 1u);
         ro[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         rd[r] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+        if (tof) tof[r] = make_float2(0.0f, 0.0f);
         return;
     }
     const double ux = dx / len, uy = dy / len, uz = dz / len;
     const double s = ox * ux + oy * uy + oz * uz;   // o = o' + s u
     ro[r] = make_float4((float)(ox - s * ux), (float)(oy - s * uy), (float)(oz - s * uz), (float)(ta + s));
     rd[r] = make_float4((float)ux, (float)uy, (float)uz, (float)(tb + s));
+    // time of flight: centre in the re-based parameter, tau = 1 / sigma_T^2
+    // (a width <= 0 or infinite means none)
+    if (tof) tof[r] = sT > 0.0 && !isinf(sT) ? make_float2((float)(tc + s), (float)(1.0 / (sT * sT)))
+                                             : make_float2(0.0f, 0.0f);
 }
 
 // bounding balls (mu, K sigma_max) and per-CTA partial scene boxes
@@ -293,7 +304,8 @@ __device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int6
 // one ray per thread; blocks b0 .. b0 + gridDim.x - 1
 template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ ro,
-                                                     const float4 *__restrict__ rd, int64_t n,
+                                                     const float4 *__restrict__ rd,
+                                                     const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges, float *out)
@@ -302,6 +314,7 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
     const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
     const bool valid = r < n;
     const Ray ray = load_ray(ro, rd, valid ? r : 0);
+    const float2 tf = tof && valid ? __ldg(tof + r) : make_float2(0.0f, 0.0f);
     const uint2 rg = ranges[blockIdx.x];
     float acc = 0.0f;
     for (uint32_t c = rg.x; c < rg.y; c += RCH) {
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
         for (int i = 0; i < cnt; i++) {
             PairGeo q;
             pair_geo(ray, sr[i], q);
-            if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w);
+            if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w, tf.x, tf.y);
         }
     }
     if (valid) out[r] = acc;
@@ -322,7 +335,8 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
 // gradients and one atomic per component per warp
 template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ ro,
-                                                     const float4 *__restrict__ rd, int64_t n,
+                                                     const float4 *__restrict__ rd,
+                                                     const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges,
@@ -334,6 +348,7 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
     const bool valid = r < n;
     const Ray ray = load_ray(ro, rd, valid ? r : 0);
     const float w = valid ? __ldg(dLdI + r) : 0.0f;
+    const float2 tf = tof && valid ? __ldg(tof + r) : make_float2(0.0f, 0.0f);
     const uint2 rg = ranges[blockIdx.x];
     // accumulator slot of general_grad's components: dmu[3], G_P[6], drho
     const int slot[NG_RAYS] = { 0, 1, 2, 4, 5, 6, 7, 8, 9, 3 };
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
             if (!__any_sync(0xffffffffu, act)) continue;
             float v[NG_RAYS];
             if (act) {
-                general_grad<KER>(ray, q, sr[i].g0.w, w, v);
+                general_grad<KER>(ray, q, sr[i].g0.w, w, v, tf.x, tf.y);
             } else {
 #pragma unroll
                 for (int k = 0; k < NG_RAYS; k++) v[k] = 0.0f;
@@ -365,11 +380,11 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
 
 }  // namespace
 
-cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, int64_t n, float4 *ro,
-                             float4 *rd, uint32_t *bad, cudaStream_t s)
+cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, const float *tof2, int64_t n,
+                             float4 *ro, float4 *rd, float2 *tof, uint32_t *bad, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_rays_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o3, d3, t2, n, ro, rd, bad);
+    k_rays_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(o3, d3, t2, tof2, n, ro, rd, tof, bad);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -406,24 +421,27 @@ cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
-                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                float *out, int ker, cudaStream_t s)
+cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, float *out, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    if (ker == 1) k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
-    else k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, out);
+    if (ker == 1) k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, out);
+    else k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
-                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, int ker, cudaStream_t s)
+cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, const float *dLdI, float4 *grad, int ker,
+                                cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    if (ker == 1) k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
-    else k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+    if (ker == 1)
+        k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+    else
+        k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
     count_launches(1);
     return cudaGetLastError();
 }

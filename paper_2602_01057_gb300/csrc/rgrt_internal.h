@@ -121,8 +121,9 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
 // ---- explicit rays (rays.cu) ----------------------------------------------
 // ro[r] = (o', t_a'), rd[r] = (unit d, t_b'), o' re-based at the point of the
 // line nearest the world origin; *bad |= 1 for an invalid ray
-cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, int64_t n, float4 *ro,
-                             float4 *rd, uint32_t *bad, cudaStream_t s);
+// tof2 (nullable): per ray (t_c, sigma_T) -> tof[r] = (t_c re-based, 1/sigma_T^2 or 0)
+cudaError_t launch_rays_prep(const float *o3, const float *d3, const float *t2, const float *tof2, int64_t n,
+                             float4 *ro, float4 *rd, float2 *tof, uint32_t *bad, cudaStream_t s);
 int rays_blocks(int64_t n_rays);       // ray blocks (128 rays each)
 int rays_ball_parts(int64_t n);        // partial scene boxes of the ball pass
 // balls (n float4), partial boxes (2 x parts), scene box (2), block lines
@@ -134,12 +135,14 @@ cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, 
 cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, int64_t b0, int nb,
                              const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
                              cudaStream_t s);
-cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
-                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                float *out, int ker, cudaStream_t s);
-cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, int64_t n_rays, int64_t b0, int nb,
-                                const float4 *rec, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, int ker, cudaStream_t s);
+// tof (nullable, Gaussian kernel only): per ray (t_c, tau)
+cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, float *out, int ker, cudaStream_t s);
+cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, const float *dLdI, float4 *grad, int ker,
+                                cudaStream_t s);
 
 // ---- voxelisation (voxel.cu) ----------------------------------------------
 // voxel (i, j, k) centre = (ox + i sx, oy + j sy, oz + k sz); bricks of

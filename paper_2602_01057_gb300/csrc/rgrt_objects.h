@@ -68,6 +68,7 @@ struct rgrt_geom {
     // explicit rays: per ray (o', t_a') and (unit d, t_b'); ray blocks
     bool rays = false;
     float4 *d_ro = nullptr, *d_rd = nullptr;
+    float2 *d_tof = nullptr;   // explicit rays with time of flight: (t_c, 1/sigma_T^2)
     int n_blocks = 0;
     // measurement model per ray (optional): multiplicative factor, additive background
     float *d_mult = nullptr, *d_add = nullptr;

@@ -67,6 +67,7 @@ _EXPORTS = {
     "gaussians_count": ([_VP], ctypes.c_int64),
     "geometry_set": ([_VP, ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_set_corrections": ([_VP, _VP, _VP], ctypes.c_int),
+    "geometry_set_rays_tof": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_set_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_destroy": ([_VP], ctypes.c_int),
     "geometry_num_rays": ([_VP], ctypes.c_int64),
@@ -285,8 +286,9 @@ def make_desc(d: dict):
 
 class Geometry:
     """A geometry from a description dict: a detector geometry (geometry_set)
-    or, for kind "rays", explicit rays o[R,3], d[R,3], t[R,2] (geometry_set_rays;
-    numpy arrays or contiguous float32 tensors)."""
+    or, for kind "rays", explicit rays o[R,3], d[R,3], t[R,2] and optionally
+    tof[R,2] = (centre, width) (geometry_set_rays[_tof]; numpy arrays or
+    contiguous float32 tensors)."""
 
     def __init__(self, ctx: Context, d: dict):
         h = _VP()
@@ -295,7 +297,12 @@ class Geometry:
             dd = _f32c(d["d"])
             t = _f32c(d["t"])
             n = int(o.shape[0])
-            _check(lib().geometry_set_rays(ctx.h, n, _ptr(o), _ptr(dd), _ptr(t), ctypes.byref(h)))
+            if d.get("tof") is not None:
+                tof = _f32c(d["tof"])
+                _check(lib().geometry_set_rays_tof(ctx.h, n, _ptr(o), _ptr(dd), _ptr(t), _ptr(tof),
+                                                   ctypes.byref(h)))
+            else:
+                _check(lib().geometry_set_rays(ctx.h, n, _ptr(o), _ptr(dd), _ptr(t), ctypes.byref(h)))
             self.tiles_per_view = 0
         else:
             desc, angles = make_desc(d)

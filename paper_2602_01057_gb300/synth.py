@@ -341,6 +341,21 @@ def pet_rays_3d(n_rings: int = 32, ring_pitch: float = 4.0, radius: float = 400.
                 n_rings=n_rings, ring_pitch=ring_pitch)
 
 
+def with_tof(R: dict, n_bins: int, spacing: float, sigma: float) -> dict:
+    """Time-of-flight version of a ray set: every ray repeated n_bins times
+    (ray-major), bin k with the TOF kernel centred at the segment's middle +
+    (k - (n_bins - 1)/2) spacing (along the unit direction) and width sigma."""
+    t = np.asarray(R["t"], np.float64)
+    mid = np.where(np.isfinite(t).all(axis=1), 0.5 * (t[:, 0] + t[:, 1]), 0.0)
+    off = (np.arange(n_bins) - 0.5 * (n_bins - 1)) * spacing
+    out = {k: np.repeat(np.asarray(v), n_bins, axis=0) for k, v in R.items()
+           if isinstance(v, np.ndarray) and v.ndim >= 1 and v.shape[0] == t.shape[0]}
+    out.update({k: v for k, v in R.items() if k not in out})
+    centres = (mid[:, None] + off[None, :]).reshape(-1)
+    out["tof"] = np.stack([centres, np.full(centres.size, sigma)], 1).astype(np.float32)
+    return out
+
+
 def rays_random(n: int, seed: int, radius: float = 1.0, seg: float | None = None) -> dict:
     """Incoherent rays: lines through uniform points of the ball of the given
     radius along uniform directions (unnormalised: length U(0.5, 2)), the

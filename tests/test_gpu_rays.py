@@ -180,3 +180,41 @@ def test_fully_3d_pet_lors(rg, ctx, torch, oracle):
     gref = oracle.backward_list(R["o"], R["d"], R["t"], G, w.astype(np.float64))
     for k in ("mu", "ls", "q", "rho"):
         assert grad_err(got, gref, k) < GRAD_TOL, k
+
+
+def test_time_of_flight(rg, ctx, torch, oracle):
+    """TOF rays (3-D PET LORs, 9 TOF bins each) against the oracle, forward
+    and adjoint; the TOF bins of a LOR sum to its plain projection."""
+    R0 = synth.pet_rays_3d(6, 4.0, 400.0, 576, 12, 49, max_ring_diff=2)
+    G, _ = synth.workload_c3(3, n=1500, n_angles=12, n_radial=49, n_planes=11)
+    G["mu"][:, 2] *= 0.2
+    R = synth.with_tof(R0, 9, 40.0, 30.0)            # 40 mm bins, 30 mm kernel width
+    I, gs, geom = gpu_fwd(torch, rg, ctx, G, R)
+    ref = oracle.forward_list(R["o"], R["d"], R["t"], G, tof=R["tof"])
+    assert fwd_err(I, ref) < FWD_TOL
+    w = synth.random_weights(I.size, 37).astype(np.float32)
+    n = gs.n
+    outs = [torch.empty(s, device="cuda") for s in ((n, 3), (n, 3), (n, 4), (n,))]
+    rg.project_backward(ctx, gs, geom, torch.from_numpy(w).cuda(), *outs)
+    torch.cuda.synchronize()
+    got = dict(zip(("mu", "ls", "q", "rho"), (o.cpu().numpy() for o in outs)))
+    gref = oracle.backward_list(R["o"], R["d"], R["t"], G, w.astype(np.float64), tof=R["tof"])
+    for k in ("mu", "ls", "q", "rho"):
+        assert grad_err(got, gref, k) < GRAD_TOL, k
+    # dense TOF bins (spacing below the width) sum to the plain projection
+    Rd = synth.with_tof(R0, 81, 10.0, 20.0)
+    Id, _, _ = gpu_fwd(torch, rg, ctx, G, Rd)
+    plain, _, _ = gpu_fwd(torch, rg, ctx, G, R0)
+    summed = Id.reshape(-1, 81).sum(axis=1) * 10.0
+    assert np.linalg.norm(summed - plain) / np.linalg.norm(plain) < 1e-5
+
+
+def test_time_of_flight_takes_the_gaussian_kernel(rg, ctx, torch):
+    R = synth.with_tof(synth.rays_random(200, 38, radius=0.5, seg=0.4), 3, 0.1, 0.1)
+    G = synth.gaussians_uniform(50, 39, half_box=0.5, log_sigma=math.log(0.1))
+    geom = rg.Geometry(ctx, R)
+    gs = rg.Gaussians(ctx, *[torch.from_numpy(np.ascontiguousarray(G[k])).cuda() for k in ("mu", "ls", "q", "rho")])
+    gs.set_kernel("epanechnikov")
+    out = torch.empty(geom.n_rays, device="cuda")
+    with pytest.raises(rg.RgrtError):
+        rg.project_forward(ctx, gs, geom, out)
