@@ -340,6 +340,7 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     TRY(ensure(ctx, ctx->part, sizeof(float4) * 2 * (size_t)parts));
     TRY(ensure(ctx, ctx->scene, sizeof(float4) * 2));
     TRY(ensure(ctx, ctx->blk, sizeof(float4) * 2 * (size_t)T));
+    TRY(ensure(ctx, ctx->wblk, sizeof(float4) * 8 * (size_t)T));
     TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)T));
     TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)T));
     TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)T));
@@ -349,7 +350,7 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
         PROF("rays_bin");
         CK(launch_rays_bin(geom->d_ro, geom->d_rd, geom->n_rays, g->rec, N, (float4 *)ctx->ball.p,
                            (float4 *)ctx->part.p, (float4 *)ctx->scene.p, (float4 *)ctx->blk.p,
-                           (uint32_t *)ctx->cnt.p, s));
+                           (float4 *)ctx->wblk.p, (uint32_t *)ctx->cnt.p, s));
     }
     ctx->h_cnt.resize((size_t)T);
     CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * (size_t)T,
@@ -418,6 +419,7 @@ int run_forward_rays(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, 
     return for_ray_ranges(ctx, g, geom, s, false, [&](int b0, int nb) -> int {
         PROF("k_rays_forward");
         CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
+                               (const float4 *)ctx->ball.p, (const float4 *)ctx->wblk.p,
                                (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, g->kernel, s));
         return RGRT_OK;
     });
@@ -474,6 +476,7 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
         TRY(for_ray_ranges(ctx, g, geom, s, reuse, [&](int b0, int nb) -> int {
             PROF("k_rays_adjoint");
             CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
+                                   (const float4 *)ctx->ball.p, (const float4 *)ctx->wblk.p,
                                    (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, dLdI,
                                    (float4 *)ctx->grad.p, g->kernel, s));
             return RGRT_OK;
@@ -608,7 +611,7 @@ int rgrt_ctx_destroy(rgrt_ctx *c)
     Buf *bufs[] = { &c->cnt, &c->off, &c->rect, &c->keys, &c->vals, &c->keys_alt, &c->vals_alt,
                     &c->sort_tmp, &c->scan_tmp, &c->ranges, &c->total, &c->I, &c->dLdI, &c->y,
                     &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss, &c->ball, &c->part,
-                    &c->scene, &c->blk };
+                    &c->scene, &c->blk, &c->wblk };
     for (Buf *b : bufs) release(c, *b);
     for (auto &b : c->stage_in) release(c, b);
     for (auto &b : c->stage_out) release(c, b);
@@ -1089,7 +1092,7 @@ int gaussians_voxelize(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_volume_des
     v.ox = (float)vol->origin[0]; v.oy = (float)vol->origin[1]; v.oz = (float)vol->origin[2];
     v.sx = (float)vol->size[0]; v.sy = (float)vol->size[1]; v.sz = (float)vol->size[2];
     v.nx = vol->dims[0]; v.ny = vol->dims[1]; v.nz = vol->dims[2];
-    v.bx = (v.nx + 7) / 8; v.by = (v.ny + 7) / 8; v.bz = (v.nz + 3) / 4;
+    v.bx = (v.nx + 7) / 8; v.by = (v.ny + 7) / 8; v.bz = (v.nz + 15) / 16;
     const int64_t nb = (int64_t)v.bx * v.by * v.bz;
     if (nb >= 0x7fffffffLL) return fail(RGRT_E_INVAL, "too many voxel bricks (%lld)", (long long)nb);
     const size_t nvox = (size_t)v.nx * v.ny * v.nz;

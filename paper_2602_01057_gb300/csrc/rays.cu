@@ -157,7 +157,8 @@ __device__ __forceinline__ bool clip_line(float3 o, float3 d, float4 lo, float4 
 // the scene box
 __global__ void __launch_bounds__(RB) k_ray_blocks(const float4 *__restrict__ ro,
                                                    const float4 *__restrict__ rd, int64_t n,
-                                                   const float4 *__restrict__ scene, float4 *blk)
+                                                   const float4 *__restrict__ scene, float4 *blk,
+                                                   float4 *wblk)
 {
     __shared__ int s_hit[RB];
     __shared__ float s_dev[RB / 32];
@@ -174,6 +175,38 @@ __global__ void __launch_bounds__(RB) k_ray_blocks(const float4 *__restrict__ ro
         hit = clip_line(o, d, lo, hi, t0, t1);
     }
     s_hit[threadIdx.x] = hit;
+    // the same bound per warp (32 rays): used by the integration kernels to
+    // skip, warp by warp, the Gaussians of the block's list that miss it
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const unsigned hb = __ballot_sync(0xffffffffu, hit);
+        float4 wP = make_float4(0.0f, 0.0f, 0.0f, 0.0f), wD = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (hb) {
+            const unsigned up = hb & 0xffff0000u;
+            const int rl = __ffs(up ? up : hb) - 1;
+            const float ax = __shfl_sync(0xffffffffu, o.x, rl), ay = __shfl_sync(0xffffffffu, o.y, rl),
+                        az = __shfl_sync(0xffffffffu, o.z, rl);
+            const float bxx = __shfl_sync(0xffffffffu, d.x, rl), byy = __shfl_sync(0xffffffffu, d.y, rl),
+                        bzz = __shfl_sync(0xffffffffu, d.z, rl);
+            const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+            const float s = (cx - ax) * bxx + (cy - ay) * byy + (cz - az) * bzz;
+            wP = make_float4(ax + s * bxx, ay + s * byy, az + s * bzz, 0.0f);
+            wD = make_float4(bxx, byy, bzz, 1.0f);
+            float dv = 0.0f;
+            if (hit) {
+                const float3 d0 = make_float3(bxx, byy, bzz);
+                const float3 ea = make_float3(o.x + t0 * d.x - wP.x, o.y + t0 * d.y - wP.y, o.z + t0 * d.z - wP.z);
+                const float3 eb = make_float3(o.x + t1 * d.x - wP.x, o.y + t1 * d.y - wP.y, o.z + t1 * d.z - wP.z);
+                dv = sqrtf(fmaxf(norm2(cross3(ea, d0)), norm2(cross3(eb, d0))));
+            }
+            for (int k = 16; k > 0; k >>= 1) dv = fmaxf(dv, __shfl_xor_sync(0xffffffffu, dv, k));
+            wP.w = dv + lo.w;
+        }
+        if (lane == 0) {
+            wblk[2 * ((size_t)blockIdx.x * (RB / 32) + w)] = wP;
+            wblk[2 * ((size_t)blockIdx.x * (RB / 32) + w) + 1] = wD;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int ref = -1;
@@ -279,6 +312,7 @@ __global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict_
 }
 
 __device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec,
+                                            const float4 *__restrict__ ball,
                                             const uint32_t *__restrict__ gids, uint32_t beg, int cnt,
                                             SRec *sr)
 {
@@ -288,8 +322,14 @@ __device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec,
         const float4 r2 = __ldg(r + 2);
         sr[i].g0 = __ldg(r);
         sr[i].g1 = __ldg(r + 1);
-        sr[i].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), 0.0f);
+        sr[i].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), __ldg(ball + gid).w);
     }
+}
+
+// the warp's bound (reference line, deviation) and the test of one staged record
+__device__ __forceinline__ bool warp_hit(const float4 &P, const float4 &D, const SRec &r)
+{
+    return D.w != 0.0f && block_hit(P, D, make_float4(r.g0.x, r.g0.y, r.g0.z, r.g2.w));
 }
 
 __device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int64_t r)
@@ -307,11 +347,15 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
                                                      const float4 *__restrict__ rd,
                                                      const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
+                                                     const float4 *__restrict__ ball,
+                                                     const float4 *__restrict__ wblk,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges, float *out)
 {
     __shared__ SRec sr[RCH];
     const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
+    const size_t wi = (size_t)(b0 + blockIdx.x) * (RB / 32) + (threadIdx.x >> 5);
+    const float4 wP = __ldg(wblk + 2 * wi), wD = __ldg(wblk + 2 * wi + 1);
     const bool valid = r < n;
     const Ray ray = load_ray(ro, rd, valid ? r : 0);
     const float2 tf = tof && valid ? __ldg(tof + r) : make_float2(0.0f, 0.0f);
@@ -320,9 +364,10 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
     for (uint32_t c = rg.x; c < rg.y; c += RCH) {
         const int cnt = (int)min((uint32_t)RCH, rg.y - c);
         __syncthreads();
-        stage_chunk(rec, gids, c, cnt, sr);
+        stage_chunk(rec, ball, gids, c, cnt, sr);
         __syncthreads();
         for (int i = 0; i < cnt; i++) {
+            if (!warp_hit(wP, wD, sr[i])) continue;       // warp-uniform
             PairGeo q;
             pair_geo(ray, sr[i], q);
             if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w, tf.x, tf.y);
@@ -338,10 +383,14 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
                                                      const float4 *__restrict__ rd,
                                                      const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
+                                                     const float4 *__restrict__ ball,
+                                                     const float4 *__restrict__ wblk,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges,
                                                      const float *__restrict__ dLdI, float *grad)
 {
+    const size_t wi = (size_t)(b0 + blockIdx.x) * (RB / 32) + (threadIdx.x >> 5);
+    const float4 wP = __ldg(wblk + 2 * wi), wD = __ldg(wblk + 2 * wi + 1);
     __shared__ SRec sr[RCH];
     const int lane = threadIdx.x & 31;
     const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
@@ -355,9 +404,10 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
     for (uint32_t c = rg.x; c < rg.y; c += RCH) {
         const int cnt = (int)min((uint32_t)RCH, rg.y - c);
         __syncthreads();
-        stage_chunk(rec, gids, c, cnt, sr);
+        stage_chunk(rec, ball, gids, c, cnt, sr);
         __syncthreads();
         for (int i = 0; i < cnt; i++) {
+            if (!warp_hit(wP, wD, sr[i])) continue;       // warp-uniform
             PairGeo q;
             pair_geo(ray, sr[i], q);
             const bool act = valid && w != 0.0f && q.m <= PAIR_CUT2;
@@ -399,13 +449,13 @@ int rays_ball_parts(int64_t n)
 
 cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
                             int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
-                            uint32_t *cnt, cudaStream_t s)
+                            float4 *wblk, uint32_t *cnt, cudaStream_t s)
 {
     const int parts = rays_ball_parts(n);
     k_balls<<<parts, CULL_BS, 0, s>>>(rec, n, ball, part);
     k_scene<<<1, 32, 0, s>>>(part, parts, scene);
     const int T = rays_blocks(n_rays);
-    k_ray_blocks<<<T, RB, 0, s>>>(ro, rd, n_rays, scene, blk);
+    k_ray_blocks<<<T, RB, 0, s>>>(ro, rd, n_rays, scene, blk, wblk);
     k_rays_count<<<T, CULL_BS, 0, s>>>(blk, ball, n, cnt);
     count_launches(4);
     return cudaGetLastError();
@@ -422,26 +472,31 @@ cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, i
 }
 
 cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
-                                const uint2 *ranges, float *out, int ker, cudaStream_t s)
+                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
+                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
+                                float *out, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    if (ker == 1) k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, out);
-    else k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, out);
+    if (ker == 1)
+        k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, ball, wblk, gids, ranges, out);
+    else
+        k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, ball, wblk, gids, ranges, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
-                                const uint2 *ranges, const float *dLdI, float4 *grad, int ker,
-                                cudaStream_t s)
+                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
+                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
+                                const float *dLdI, float4 *grad, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
     if (ker == 1)
-        k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+        k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, ball, wblk, gids, ranges, dLdI,
+                                            (float *)grad);
     else
-        k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
+        k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, ball, wblk, gids, ranges, dLdI,
+                                            (float *)grad);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -2,8 +2,10 @@
 // exp(-m_g(x)/2) with m_g(x) = (x - mu_g)^T P_g (x - mu_g) <= 9 (the cut of
 // the projector), sampled at voxel centres -- the reconstructed volume.
 //
-// The grid is cut into bricks of 8 x 8 x 4 voxels, one CTA of 256 threads per
-// brick, one voxel per thread; each warp holds an 8 x 4 x 1 slab.  Binning:
+// The grid is cut into bricks of 8 x 8 x 16 voxels, one CTA of 256 threads per
+// brick, four voxels along z per thread (the exponent is a quadratic in z:
+// its xy part is computed once per Gaussian and thread); each warp holds an
+// 8 x 4 x 4 block.  Binning:
 // per Gaussian the box mu +- sqrt(K^2 Sigma_aa) (K^2 = 9.0625) gives a voxel
 // range per axis, hence a brick range; counts, exclusive scan, emission of
 // (brick, Gaussian) pairs in Gaussian order, stable radix sort by brick and
@@ -15,15 +17,19 @@
 namespace rgrt {
 namespace {
 
-constexpr int VB = 256;            // threads (voxels) per brick
+constexpr int VB = 256;            // threads per brick
+constexpr int VZ = 4;              // voxels per thread along z
+constexpr int BZ = 4 * VZ;         // brick depth: 8 x 8 x 16 voxels
 constexpr int VCH = 256;           // records per chunk
 constexpr float NEG_HALF_LOG2E_V = -0.721347520444481703f;
 constexpr float VOX_CUT_ARG = -6.49212768400033233f;  // -9 log2(e) / 2
 
+// one Gaussian in shared memory; P carries the exponent's scale k
+// (-log2(e)/2, or -1/kappa^2 for Epanechnikov)
 struct VRecord {
     float4 g0;   // mu, rho
-    float4 g1;   // P00 P01 P02 P11
-    float4 g2;   // P12 P22 hx hy   (h = half-widths of the K-sigma box)
+    float4 g1;   // k P00, 2k P01, k P11, 2k P02
+    float4 g2;   // 2k P12, k P22, hx, hy   (h = half-widths of the K-sigma box)
     float4 g3;   // hz
 };
 
@@ -64,7 +70,7 @@ __global__ void k_vox_count(const float4 *__restrict__ crec, int64_t n, VolDev v
     uint32_t c = 0;
     uint4 b = make_uint4(1u, 0u, 0u, 0u);   // empty
     if (i0 <= i1 && j0 <= j1 && k0 <= k1) {
-        const int bx0 = i0 >> 3, bx1 = i1 >> 3, by0 = j0 >> 3, by1 = j1 >> 3, bz0 = k0 >> 2, bz1 = k1 >> 2;
+        const int bx0 = i0 >> 3, bx1 = i1 >> 3, by0 = j0 >> 3, by1 = j1 >> 3, bz0 = k0 / BZ, bz1 = k1 / BZ;
         c = (uint32_t)((bx1 - bx0 + 1) * (by1 - by0 + 1) * (bz1 - bz0 + 1));
         b = make_uint4((uint32_t)bx0 | ((uint32_t)bx1 << 16), (uint32_t)by0 | ((uint32_t)by1 << 16),
                        (uint32_t)bz0 | ((uint32_t)bz1 << 16), 0u);
@@ -117,16 +123,20 @@ __global__ void __launch_bounds__(VB) k_voxelize(const float4 *__restrict__ rec,
     const int by = (int)((brick / (uint32_t)v.bx) % (uint32_t)v.by);
     const int bz = (int)(brick / ((uint32_t)v.bx * (uint32_t)v.by));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // warp w: x 0..7 (lane & 7), y (w & 1) * 4 + lane >> 3, z (w >> 1) * VZ + 0..VZ-1
     const int i = bx * 8 + (lane & 7);
     const int j = by * 8 + (w & 1) * 4 + (lane >> 3);
-    const int k = bz * 4 + (w >> 1);
-    const float x = v.ox + (float)i * v.sx, y = v.oy + (float)j * v.sy, z = v.oz + (float)k * v.sz;
-    // the warp's slab: centre and half extents
+    const int k0 = bz * BZ + (w >> 1) * VZ;
+    const float x = v.ox + (float)i * v.sx, y = v.oy + (float)j * v.sy, z0 = v.oz + (float)k0 * v.sz;
+    // the warp's block of 8 x 4 x VZ voxels: centre and half extents
     const float i0 = (float)(bx * 8), j0 = (float)(by * 8 + (w & 1) * 4);
-    const float cx = v.ox + (i0 + 3.5f) * v.sx, cy = v.oy + (j0 + 1.5f) * v.sy, cz = z;
-    const float ex = 3.5f * fabsf(v.sx), ey = 1.5f * fabsf(v.sy);
+    const float cx = v.ox + (i0 + 3.5f) * v.sx, cy = v.oy + (j0 + 1.5f) * v.sy;
+    const float cz = z0 + 0.5f * (float)(VZ - 1) * v.sz;
+    const float ex = 3.5f * v.sx, ey = 1.5f * v.sy, ez = 0.5f * (float)(VZ - 1) * v.sz;
     const uint2 rg = ranges[brick];
-    float acc = 0.0f;
+    float acc[VZ];
+#pragma unroll
+    for (int q = 0; q < VZ; q++) acc[q] = 0.0f;
     for (uint32_t c = rg.x; c < rg.y; c += VCH) {
         const int cnt = (int)min((uint32_t)VCH, rg.y - c);
         __syncthreads();
@@ -134,37 +144,46 @@ __global__ void __launch_bounds__(VB) k_voxelize(const float4 *__restrict__ rec,
             const uint32_t gid = __ldg(gids + c + t);
             const float4 *r = rec + REC_F4 * (size_t)gid;
             const float4 c1 = __ldg(crec + CREC_F4 * (size_t)gid + 1), c2 = __ldg(crec + CREC_F4 * (size_t)gid + 2);
-            const float4 r2 = __ldg(r + 2);
+            const float4 r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+            // the exponent's scale folded into P: arg = d^T (k P) d
+            const float kk = KER == 1 ? -1.0f / 7.0f : NEG_HALF_LOG2E_V;
             sr[t].g0 = __ldg(r);
-            sr[t].g1 = __ldg(r + 1);
-            sr[t].g2 = make_float4(r2.x, r2.y, sqrtf(CULL_K2 * c1.x), sqrtf(CULL_K2 * c1.w));
-            sr[t].g3 = make_float4(sqrtf(CULL_K2 * c2.y), 0.0f, 0.0f, 0.0f);
+            sr[t].g1 = make_float4(kk * r1.x, 2.0f * kk * r1.y, kk * r1.w, 2.0f * kk * r1.z);   // P00 2P01 P11 2P02
+            sr[t].g2 = make_float4(2.0f * kk * r2.x, kk * r2.y, sqrtf(CULL_K2 * c1.x), sqrtf(CULL_K2 * c1.w));
+            sr[t].g3 = make_float4(sqrtf(CULL_K2 * c2.y), 0.0f, 0.0f, 0.0f);                       // 2P12 P22 hx hy | hz
         }
         __syncthreads();
         for (int t = 0; t < cnt; t++) {
             const float4 g0 = sr[t].g0, g2 = sr[t].g2;
             const float hz = sr[t].g3.x;
-            // warp-uniform: skip a Gaussian whose box misses this slab
-            if (fabsf(g0.x - cx) > g2.z + ex || fabsf(g0.y - cy) > g2.w + ey || fabsf(g0.z - cz) > hz)
+            // warp-uniform: skip a Gaussian whose box misses this warp's voxels
+            if (fabsf(g0.x - cx) > g2.z + ex || fabsf(g0.y - cy) > g2.w + ey || fabsf(g0.z - cz) > hz + ez)
                 continue;
             const float4 g1 = sr[t].g1;
-            const float dx = x - g0.x, dy = y - g0.y, dz = z - g0.z;
-            const float t0 = g1.x * dx + g1.y * dy + g1.z * dz;
-            const float t1 = g1.y * dx + g1.w * dy + g2.x * dz;
-            const float t2 = g1.z * dx + g2.x * dy + g2.y * dz;
-            const float md = dx * t0 + dy * t1 + dz * t2;
-            if (KER == 1) {
-                // Epanechnikov: rho (1 - m / kappa^2)_+, kappa^2 = 7
-                const float c = 1.0f - md * (1.0f / 7.0f);
-                acc += c > 0.0f ? g0.w * c : 0.0f;
-            } else {
-                const float arg = md * NEG_HALF_LOG2E_V;
-                const float f = g0.w * ex2_fast(arg);
-                acc += arg >= VOX_CUT_ARG ? f : 0.0f;
+            const float dx = x - g0.x, dy = y - g0.y;
+            // arg(dz) = a0 + dz (b0 + c0 dz): the xy terms once, then VZ voxels along z
+            const float a0 = dx * (g1.x * dx + g1.y * dy) + g1.z * dy * dy;
+            const float b0 = g1.w * dx + g2.x * dy;
+            const float c0 = g2.y;
+#pragma unroll
+            for (int q = 0; q < VZ; q++) {
+                const float dz = z0 + (float)q * v.sz - g0.z;
+                const float arg = a0 + dz * (b0 + c0 * dz);
+                if (KER == 1) {
+                    const float cc = 1.0f + arg;                // 1 - m / kappa^2
+                    acc[q] += cc > 0.0f ? g0.w * cc : 0.0f;
+                } else {
+                    const float f = g0.w * ex2_fast(arg);
+                    acc[q] += arg >= VOX_CUT_ARG ? f : 0.0f;
+                }
             }
         }
     }
-    if (i < v.nx && j < v.ny && k < v.nz) out[((int64_t)k * v.ny + j) * v.nx + i] = acc;
+    if (i < v.nx && j < v.ny) {
+#pragma unroll
+        for (int q = 0; q < VZ; q++)
+            if (k0 + q < v.nz) out[((int64_t)(k0 + q) * v.ny + j) * v.nx + i] = acc[q];
+    }
 }
 
 }  // namespace

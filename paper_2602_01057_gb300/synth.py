@@ -293,6 +293,15 @@ def rays_helical(n_views: int, n_rows: int, n_cols: int, pitch: float, dso: floa
                 t=t.astype(np.float32))
 
 
+def _morton2(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Interleave the bits of a (even positions) and b (odd positions)."""
+    code = np.zeros(a.shape, np.int64)
+    for bit in range(16):
+        code |= ((a >> bit) & 1) << (2 * bit)
+        code |= ((b >> bit) & 1) << (2 * bit + 1)
+    return code
+
+
 def pet_rays_3d(n_rings: int = 32, ring_pitch: float = 4.0, radius: float = 400.0, n_crystals: int = 576,
                 n_angles: int = 288, n_radial: int = 329, max_ring_diff: int = 5, arc_mode: int = 0) -> dict:
     """Fully 3-D PET: the LORs between every pair of rings (r1, r2) with
@@ -301,44 +310,40 @@ def pet_rays_3d(n_rings: int = 32, ring_pitch: float = 4.0, radius: float = 400.
     chords).  Ring r sits at z_r = (r - (n_rings - 1)/2) ring_pitch; the LOR
     runs from s e_u - h e_w + z_r1 e_z to s e_u + h e_w + z_r2 e_z,
     h = sqrt(R^2 - s^2), e_u = (cos phi, sin phi, 0), e_w = (sin phi, -cos phi, 0).
-    Rays are ordered in blocks of 16 radial bins x 8 ring pairs of one
-    (ring difference, angle) so that neighbouring rays are close; the returned
-    dict carries each ray's (ring1, ring2, angle, radial) indices."""
+    Order: by ring difference, then angle, then the (ring pair, radial bin)
+    grid of that difference and angle along a Morton curve (radial bits on
+    the even positions), so that any 128 consecutive rays lie close together;
+    the returned dict carries each ray's (ring1, ring2, angle, radial)."""
     c = 0.5 * (n_radial - 1)
     k = np.arange(n_radial) - c
     s = k * (math.pi * radius / n_crystals) if arc_mode == 0 else radius * np.sin(k * math.pi / n_crystals)
     h = np.sqrt(radius * radius - s * s)
     zr = (np.arange(n_rings) - 0.5 * (n_rings - 1)) * ring_pitch
-    pairs = [(r1, r1 + dlt) for dlt in range(-max_ring_diff, max_ring_diff + 1)
-             for r1 in range(n_rings) if 0 <= r1 + dlt < n_rings]
-    pairs.sort(key=lambda p: (p[1] - p[0], p[0]))
-    P = np.array(pairs)
-    diff = P[:, 1] - P[:, 0]
-    out_o, out_d, out_t, idx = [], [], [], []
     phi = math.pi * np.arange(n_angles) / n_angles
-    for dlt in np.unique(diff):
-        sel = np.nonzero(diff == dlt)[0]
+    out_o, out_d, out_t, idx = [], [], [], []
+    ez = np.array([0.0, 0.0, 1.0])
+    for dlt in range(-max_ring_diff, max_ring_diff + 1):
+        r1s = np.array([r for r in range(n_rings) if 0 <= r + dlt < n_rings])
+        if r1s.size == 0:
+            continue
+        pp, kk = np.meshgrid(np.arange(r1s.size), np.arange(n_radial), indexing="ij")
+        order = np.argsort(_morton2(kk.ravel(), pp.ravel()), kind="stable")
+        r1 = r1s[pp.ravel()[order]]
+        r2 = r1 + dlt
+        kq = kk.ravel()[order]
         for j in range(n_angles):
             eu = np.array([math.cos(phi[j]), math.sin(phi[j]), 0.0])
             ew = np.array([math.sin(phi[j]), -math.cos(phi[j]), 0.0])
-            for zb in range(0, sel.size, 8):
-                zs = sel[zb:zb + 8]
-                for rb in range(0, n_radial, 16):
-                    ks = np.arange(rb, min(rb + 16, n_radial))
-                    r1 = P[zs, 0][:, None].repeat(ks.size, 1).ravel()
-                    r2 = P[zs, 1][:, None].repeat(ks.size, 1).ravel()
-                    kk = np.tile(ks, zs.size)
-                    a = s[kk, None] * eu - h[kk, None] * ew + zr[r1, None] * np.array([0, 0, 1.0])
-                    b = s[kk, None] * eu + h[kk, None] * ew + zr[r2, None] * np.array([0, 0, 1.0])
-                    dv = b - a
-                    out_o.append(a)
-                    out_d.append(dv)
-                    out_t.append(np.stack([np.zeros(kk.size), np.linalg.norm(dv, axis=1)], 1))
-                    idx.append(np.stack([r1, r2, np.full(kk.size, j), kk], 1))
-    o = np.concatenate(out_o)
-    return dict(kind="rays", o=o.astype(np.float32), d=np.concatenate(out_d).astype(np.float32),
-                t=np.concatenate(out_t).astype(np.float32), index=np.concatenate(idx).astype(np.int32),
-                n_rings=n_rings, ring_pitch=ring_pitch)
+            a = s[kq, None] * eu - h[kq, None] * ew + zr[r1, None] * ez
+            b = s[kq, None] * eu + h[kq, None] * ew + zr[r2, None] * ez
+            dv = b - a
+            out_o.append(a)
+            out_d.append(dv)
+            out_t.append(np.stack([np.zeros(kq.size), np.linalg.norm(dv, axis=1)], 1))
+            idx.append(np.stack([r1, r2, np.full(kq.size, j), kq], 1))
+    return dict(kind="rays", o=np.concatenate(out_o).astype(np.float32),
+                d=np.concatenate(out_d).astype(np.float32), t=np.concatenate(out_t).astype(np.float32),
+                index=np.concatenate(idx).astype(np.int32), n_rings=n_rings, ring_pitch=ring_pitch)
 
 
 def with_tof(R: dict, n_bins: int, spacing: float, sigma: float) -> dict:
