@@ -87,6 +87,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fitted", action="store_true", help="skip the fitted-state timing")
     ap.add_argument("--tile", default="auto", help="binning tile WxH, or auto (the autotuner)")
+    ap.add_argument("--seed", type=int, default=0, help="c1-c3: workload seed (rank r uses seed + r)")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
     ap.add_argument("--cpu-views", type=int, default=0, help="views in the CPU sample (0 = auto)")
     return ap.parse_args()
@@ -322,7 +323,7 @@ def run_ours(args):
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
     dev = torch.device("cuda", local)
-    G, Gt, gd, loss = workload(args.workload, rank)
+    G, Gt, gd, loss = workload(args.workload, args.seed + rank)
     R = synth.num_rays(gd)
     ctx = rgrt.Context(local)
     t_auto = None
@@ -416,6 +417,7 @@ def run_ours(args):
                 config=dict(workload=WORKLOADS[args.workload], rays_per_step=R,
                             gaussians=int(G["mu"].shape[0]),
                             tile=f"{tw}x{th}" + (" (autotuner)" if t_auto is not None else ""),
+                            seed=args.seed,
                             l2=("flushed between timed steps (256 MiB write outside the events)"
                                 if flush is not None else "not flushed"),
                             parallelism=f"{world} independent scans (one per GPU)"),

@@ -341,10 +341,11 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     TRY(ensure(ctx, ctx->scene, sizeof(float4) * 2));
     TRY(ensure(ctx, ctx->blk, sizeof(float4) * 2 * (size_t)T));
     TRY(ensure(ctx, ctx->wblk, sizeof(float4) * 8 * (size_t)T));
-    TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * (size_t)T));
-    TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * (size_t)T));
-    TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)T));
-    TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems(T)));
+    const size_t TL = (size_t)T * RAYS_WPB;   // one list per warp
+    TRY(ensure(ctx, ctx->cnt, sizeof(uint32_t) * TL));
+    TRY(ensure(ctx, ctx->off, sizeof(uint32_t) * TL));
+    TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * TL));
+    TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems((int64_t)TL)));
     TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
     {
         PROF("rays_bin");
@@ -352,9 +353,8 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
                            (float4 *)ctx->part.p, (float4 *)ctx->scene.p, (float4 *)ctx->blk.p,
                            (float4 *)ctx->wblk.p, (uint32_t *)ctx->cnt.p, s));
     }
-    ctx->h_cnt.resize((size_t)T);
-    CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * (size_t)T,
-                       cudaMemcpyDeviceToHost, s));
+    ctx->h_cnt.resize(TL);
+    CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * TL, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     // list capacity: what the budget leaves (the current list buffer included)
     size_t avail = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
@@ -365,8 +365,13 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     std::vector<std::pair<int, int>> rng;
     uint64_t acc = 0, total = 0;
     int b0 = 0;
+    auto block_count = [&](int b) -> uint64_t {
+        uint64_t c = 0;
+        for (int w = 0; w < RAYS_WPB; w++) c += ctx->h_cnt[(size_t)b * RAYS_WPB + w];
+        return c;
+    };
     for (int b = 0; b < T; b++) {
-        const uint64_t c = ctx->h_cnt[(size_t)b];
+        const uint64_t c = block_count(b);
         if (c > cap)
             return fail(RGRT_E_CAPACITY, "ray block %d lists %llu Gaussians, over the budget", b,
                         (unsigned long long)c);
@@ -382,7 +387,7 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     uint64_t kmax = 0;
     for (auto &r : rng) {
         uint64_t k = 0;
-        for (int b = r.first; b < r.first + r.second; b++) k += ctx->h_cnt[(size_t)b];
+        for (int b = r.first; b < r.first + r.second; b++) k += block_count(b);
         kmax = k > kmax ? k : kmax;
     }
     TRY(ensure(ctx, ctx->vals, sizeof(uint32_t) * (size_t)(kmax > 0 ? kmax : 1)));
@@ -390,10 +395,12 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     for (auto &r : rng) {
         {
             PROF("rays_emit");
-            CK(launch_scan((const uint32_t *)ctx->cnt.p + r.first, (uint32_t *)ctx->off.p, r.second,
-                           (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
-            CK(launch_rays_emit((const float4 *)ctx->blk.p, (const float4 *)ctx->ball.p, N, r.first,
-                                r.second, (const uint32_t *)ctx->off.p, (const uint32_t *)ctx->cnt.p,
+            CK(launch_scan((const uint32_t *)ctx->cnt.p + (size_t)r.first * RAYS_WPB, (uint32_t *)ctx->off.p,
+                           (int64_t)r.second * RAYS_WPB, (unsigned long long *)ctx->total.p,
+                           (unsigned long long *)ctx->scan_tmp.p, s));
+            CK(launch_rays_emit((const float4 *)ctx->blk.p, (const float4 *)ctx->wblk.p,
+                                (const float4 *)ctx->ball.p, N, r.first, r.second,
+                                (const uint32_t *)ctx->off.p, (const uint32_t *)ctx->cnt.p,
                                 (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p, s));
         }
         if (rng.size() == 1) {
@@ -419,7 +426,6 @@ int run_forward_rays(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, 
     return for_ray_ranges(ctx, g, geom, s, false, [&](int b0, int nb) -> int {
         PROF("k_rays_forward");
         CK(launch_rays_forward(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
-                               (const float4 *)ctx->ball.p, (const float4 *)ctx->wblk.p,
                                (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, out, g->kernel, s));
         return RGRT_OK;
     });
@@ -476,7 +482,6 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
         TRY(for_ray_ranges(ctx, g, geom, s, reuse, [&](int b0, int nb) -> int {
             PROF("k_rays_adjoint");
             CK(launch_rays_adjoint(geom->d_ro, geom->d_rd, geom->d_tof, geom->n_rays, b0, nb, g->rec,
-                                   (const float4 *)ctx->ball.p, (const float4 *)ctx->wblk.p,
                                    (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->ranges.p, dLdI,
                                    (float4 *)ctx->grad.p, g->kernel, s));
             return RGRT_OK;

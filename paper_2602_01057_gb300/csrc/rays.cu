@@ -15,9 +15,11 @@
 //    further than dev from L0 (distance to a line is convex along a segment),
 //    so the Gaussian can pair with the block only if
 //        dist(mu, L0) <= K sigma_max + dev;
-//  * per block, a pass over all Gaussians counts and then emits, in ascending
-//    Gaussian order, those passing that test.
-// Integration and adjoint then walk a block's list in shared-memory chunks.
+//  * the same bound is taken per warp (32 rays); per block, a pass over all
+//    Gaussians counts and then emits, in ascending Gaussian order, the ones
+//    that pass the block's test and then a warp's test into that warp's list.
+// Integration and adjoint: every warp walks its own list, 32 records at a
+// time staged in its own slice of shared memory (no barrier across the CTA).
 #include "pair.cuh"
 
 namespace rgrt {
@@ -259,78 +261,122 @@ __device__ __forceinline__ bool block_hit(const float4 P, const float4 D, const 
     return d2 <= __fmul_rn(R, R);
 }
 
+constexpr int WPB = RB / 32;   // warps (and lists) per ray block
+static_assert(WPB == RAYS_WPB, "one list per warp of a ray block");
+
+// per block: how many Gaussians pass the block's bound and then each warp's
+// bound; cnt[WPB b + w] = the length of warp w's list
 __global__ void __launch_bounds__(CULL_BS) k_rays_count(const float4 *__restrict__ blk,
+                                                        const float4 *__restrict__ wblk,
                                                         const float4 *__restrict__ ball, int64_t n,
                                                         uint32_t *cnt)
 {
-    __shared__ uint32_t s_c[CULL_BS / 32];
+    __shared__ uint32_t s_c[WPB][CULL_BS / 32];
     const float4 P = blk[2 * blockIdx.x], D = blk[2 * blockIdx.x + 1];
-    uint32_t c = 0;
+    float4 wP[WPB], wD[WPB];
+#pragma unroll
+    for (int w = 0; w < WPB; w++) {
+        wP[w] = wblk[2 * ((size_t)blockIdx.x * WPB + w)];
+        wD[w] = wblk[2 * ((size_t)blockIdx.x * WPB + w) + 1];
+    }
+    uint32_t c[WPB] = {};
     if (D.w != 0.0f)
-        for (int64_t k = threadIdx.x; k < n; k += CULL_BS) c += block_hit(P, D, __ldg(ball + k));
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+        for (int64_t k = threadIdx.x; k < n; k += CULL_BS) {
+            const float4 bl = __ldg(ball + k);
+            if (!block_hit(P, D, bl)) continue;
+#pragma unroll
+            for (int w = 0; w < WPB; w++) c[w] += wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
+        }
+#pragma unroll
+    for (int w = 0; w < WPB; w++) {
+        uint32_t v = c[w];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_c[w][threadIdx.x >> 5] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < WPB) {
         uint32_t t = 0;
-        for (int j = 0; j < CULL_BS / 32; j++) t += s_c[j];
-        cnt[blockIdx.x] = t;
+        for (int j = 0; j < CULL_BS / 32; j++) t += s_c[threadIdx.x][j];
+        cnt[(size_t)blockIdx.x * WPB + threadIdx.x] = t;
     }
 }
 
-// blocks b0 .. b0 + gridDim.x - 1; off[] relative to the range
+// blocks b0 .. b0 + gridDim.x - 1; off[] (per warp list) relative to the range;
+// every list in ascending Gaussian order
 __global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict__ blk,
+                                                       const float4 *__restrict__ wblk,
                                                        const float4 *__restrict__ ball, int64_t n,
                                                        int64_t b0, const uint32_t *__restrict__ off,
                                                        const uint32_t *__restrict__ cnt,
                                                        uint32_t *gids, uint2 *ranges)
 {
-    __shared__ uint32_t s_w[CULL_BS / 32];
+    __shared__ uint32_t s_w[WPB][CULL_BS / 32];
     const int64_t b = b0 + blockIdx.x;
     const float4 P = blk[2 * b], D = blk[2 * b + 1];
-    const uint32_t beg = off[blockIdx.x], num = cnt[b];
-    if (threadIdx.x == 0) ranges[blockIdx.x] = make_uint2(beg, beg + num);
-    if (D.w == 0.0f || num == 0) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t pos = beg;
+    float4 wP[WPB], wD[WPB];
+    uint32_t beg[WPB], num[WPB], pos[WPB], total_num = 0;
+#pragma unroll
+    for (int w = 0; w < WPB; w++) {
+        wP[w] = wblk[2 * ((size_t)b * WPB + w)];
+        wD[w] = wblk[2 * ((size_t)b * WPB + w) + 1];
+        beg[w] = off[(size_t)blockIdx.x * WPB + w];
+        num[w] = cnt[(size_t)b * WPB + w];
+        pos[w] = beg[w];
+        total_num += num[w];
+    }
+    if (threadIdx.x < WPB)
+        ranges[(size_t)blockIdx.x * WPB + threadIdx.x] = make_uint2(beg[threadIdx.x], beg[threadIdx.x] + num[threadIdx.x]);
+    if (D.w == 0.0f || total_num == 0) return;
+    const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     for (int64_t base = 0; base < n; base += CULL_BS) {
         const int64_t k = base + threadIdx.x;
-        const bool h = k < n && block_hit(P, D, __ldg(ball + k));
-        const uint32_t bal = __ballot_sync(0xffffffffu, h);
-        if (lane == 0) s_w[w] = __popc(bal);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int j = 0; j < CULL_BS / 32; j++) {
-            before += j < w ? s_w[j] : 0u;
-            total += s_w[j];
+        bool h[WPB] = {};
+        if (k < n) {
+            const float4 bl = __ldg(ball + k);
+            if (block_hit(P, D, bl)) {
+#pragma unroll
+                for (int w = 0; w < WPB; w++) h[w] = wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
+            }
         }
-        const uint32_t at = pos + before + __popc(bal & ((1u << lane) - 1u));
-        if (h && at < beg + num) gids[at] = (uint32_t)k;
-        pos += total;
+        uint32_t bal[WPB];
+#pragma unroll
+        for (int w = 0; w < WPB; w++) {
+            bal[w] = __ballot_sync(0xffffffffu, h[w]);
+            if (lane == 0) s_w[w][cw] = __popc(bal[w]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < WPB; w++) {
+            uint32_t before = 0, total = 0;
+            for (int j = 0; j < CULL_BS / 32; j++) {
+                before += j < cw ? s_w[w][j] : 0u;
+                total += s_w[w][j];
+            }
+            const uint32_t at = pos[w] + before + __popc(bal[w] & lt);
+            if (h[w] && at < beg[w] + num[w]) gids[at] = (uint32_t)k;
+            pos[w] += total;
+        }
         __syncthreads();
     }
 }
 
-__device__ __forceinline__ void stage_chunk(const float4 *__restrict__ rec,
-                                            const float4 *__restrict__ ball,
-                                            const uint32_t *__restrict__ gids, uint32_t beg, int cnt,
-                                            SRec *sr)
+// a warp stages up to 32 records of its own list (lane i: entry beg + i)
+__device__ __forceinline__ void stage_warp(const float4 *__restrict__ rec,
+                                           const uint32_t *__restrict__ gids, uint32_t beg, int cnt,
+                                           int lane, SRec *sr)
 {
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint32_t gid = __ldg(gids + beg + i);
+    if (lane < cnt) {
+        const uint32_t gid = __ldg(gids + beg + lane);
         const float4 *r = rec + REC_F4 * (size_t)gid;
         const float4 r2 = __ldg(r + 2);
-        sr[i].g0 = __ldg(r);
-        sr[i].g1 = __ldg(r + 1);
-        sr[i].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), __ldg(ball + gid).w);
+        sr[lane].g0 = __ldg(r);
+        sr[lane].g1 = __ldg(r + 1);
+        sr[lane].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), 0.0f);
     }
+    __syncwarp();
 }
 
-// the warp's bound (reference line, deviation) and the test of one staged record
-__device__ __forceinline__ bool warp_hit(const float4 &P, const float4 &D, const SRec &r)
-{
-    return D.w != 0.0f && block_hit(P, D, make_float4(r.g0.x, r.g0.y, r.g0.z, r.g2.w));
-}
 
 __device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int64_t r)
 {
@@ -341,33 +387,30 @@ __device__ __forceinline__ Ray load_ray(const float4 *ro, const float4 *rd, int6
     return y;
 }
 
-// one ray per thread; blocks b0 .. b0 + gridDim.x - 1
+// one ray per thread; blocks b0 .. b0 + gridDim.x - 1; every warp walks its
+// own list (no barrier across the CTA)
 template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ ro,
                                                      const float4 *__restrict__ rd,
                                                      const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
-                                                     const float4 *__restrict__ ball,
-                                                     const float4 *__restrict__ wblk,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges, float *out)
 {
-    __shared__ SRec sr[RCH];
+    __shared__ SRec sr_all[WPB][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    SRec *sr = sr_all[w];
     const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
-    const size_t wi = (size_t)(b0 + blockIdx.x) * (RB / 32) + (threadIdx.x >> 5);
-    const float4 wP = __ldg(wblk + 2 * wi), wD = __ldg(wblk + 2 * wi + 1);
     const bool valid = r < n;
     const Ray ray = load_ray(ro, rd, valid ? r : 0);
     const float2 tf = tof && valid ? __ldg(tof + r) : make_float2(0.0f, 0.0f);
-    const uint2 rg = ranges[blockIdx.x];
+    const uint2 rg = ranges[(size_t)blockIdx.x * WPB + w];
     float acc = 0.0f;
-    for (uint32_t c = rg.x; c < rg.y; c += RCH) {
-        const int cnt = (int)min((uint32_t)RCH, rg.y - c);
-        __syncthreads();
-        stage_chunk(rec, ball, gids, c, cnt, sr);
-        __syncthreads();
+    for (uint32_t c = rg.x; c < rg.y; c += 32) {
+        const int cnt = (int)min(32u, rg.y - c);
+        __syncwarp();
+        stage_warp(rec, gids, c, cnt, lane, sr);
         for (int i = 0; i < cnt; i++) {
-            if (!warp_hit(wP, wD, sr[i])) continue;       // warp-uniform
             PairGeo q;
             pair_geo(ray, sr[i], q);
             if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w, tf.x, tf.y);
@@ -376,45 +419,41 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
     if (valid) out[r] = acc;
 }
 
-// one ray per thread; per Gaussian a transposed warp reduction of the pair
-// gradients and one atomic per component per warp
+// one ray per thread, warp-private lists; per Gaussian a transposed warp
+// reduction of the pair gradients and one atomic per component per warp
 template <int KER>
 __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ ro,
                                                      const float4 *__restrict__ rd,
                                                      const float2 *__restrict__ tof, int64_t n,
                                                      int64_t b0, const float4 *__restrict__ rec,
-                                                     const float4 *__restrict__ ball,
-                                                     const float4 *__restrict__ wblk,
                                                      const uint32_t *__restrict__ gids,
                                                      const uint2 *__restrict__ ranges,
                                                      const float *__restrict__ dLdI, float *grad)
 {
-    const size_t wi = (size_t)(b0 + blockIdx.x) * (RB / 32) + (threadIdx.x >> 5);
-    const float4 wP = __ldg(wblk + 2 * wi), wD = __ldg(wblk + 2 * wi + 1);
-    __shared__ SRec sr[RCH];
-    const int lane = threadIdx.x & 31;
+    __shared__ SRec sr_all[WPB][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    SRec *sr = sr_all[w];
     const int64_t r = (b0 + blockIdx.x) * (int64_t)RB + threadIdx.x;
     const bool valid = r < n;
     const Ray ray = load_ray(ro, rd, valid ? r : 0);
-    const float w = valid ? __ldg(dLdI + r) : 0.0f;
+    const float wgt = valid ? __ldg(dLdI + r) : 0.0f;
     const float2 tf = tof && valid ? __ldg(tof + r) : make_float2(0.0f, 0.0f);
-    const uint2 rg = ranges[blockIdx.x];
+    const uint2 rg = ranges[(size_t)blockIdx.x * WPB + w];
     // accumulator slot of general_grad's components: dmu[3], G_P[6], drho
     const int slot[NG_RAYS] = { 0, 1, 2, 4, 5, 6, 7, 8, 9, 3 };
-    for (uint32_t c = rg.x; c < rg.y; c += RCH) {
-        const int cnt = (int)min((uint32_t)RCH, rg.y - c);
-        __syncthreads();
-        stage_chunk(rec, ball, gids, c, cnt, sr);
-        __syncthreads();
+    if (!__any_sync(0xffffffffu, wgt != 0.0f)) return;
+    for (uint32_t c = rg.x; c < rg.y; c += 32) {
+        const int cnt = (int)min(32u, rg.y - c);
+        __syncwarp();
+        stage_warp(rec, gids, c, cnt, lane, sr);
         for (int i = 0; i < cnt; i++) {
-            if (!warp_hit(wP, wD, sr[i])) continue;       // warp-uniform
             PairGeo q;
             pair_geo(ray, sr[i], q);
-            const bool act = valid && w != 0.0f && q.m <= PAIR_CUT2;
+            const bool act = valid && wgt != 0.0f && q.m <= PAIR_CUT2;
             if (!__any_sync(0xffffffffu, act)) continue;
             float v[NG_RAYS];
             if (act) {
-                general_grad<KER>(ray, q, sr[i].g0.w, w, v, tf.x, tf.y);
+                general_grad<KER>(ray, q, sr[i].g0.w, wgt, v, tf.x, tf.y);
             } else {
 #pragma unroll
                 for (int k = 0; k < NG_RAYS; k++) v[k] = 0.0f;
@@ -456,47 +495,42 @@ cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, 
     k_scene<<<1, 32, 0, s>>>(part, parts, scene);
     const int T = rays_blocks(n_rays);
     k_ray_blocks<<<T, RB, 0, s>>>(ro, rd, n_rays, scene, blk, wblk);
-    k_rays_count<<<T, CULL_BS, 0, s>>>(blk, ball, n, cnt);
+    k_rays_count<<<T, CULL_BS, 0, s>>>(blk, wblk, ball, n, cnt);
     count_launches(4);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, int64_t b0, int nb,
-                             const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const float4 *ball, int64_t n, int64_t b0,
+                             int nb, const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
                              cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    k_rays_emit<<<nb, CULL_BS, 0, s>>>(blk, ball, n, b0, off, cnt, gids, ranges);
+    k_rays_emit<<<nb, CULL_BS, 0, s>>>(blk, wblk, ball, n, b0, off, cnt, gids, ranges);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
-                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
-                                float *out, int ker, cudaStream_t s)
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, float *out, int ker, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    if (ker == 1)
-        k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, ball, wblk, gids, ranges, out);
-    else
-        k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, ball, wblk, gids, ranges, out);
+    if (ker == 1) k_rays_forward<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, out);
+    else k_rays_forward<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
-                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, int ker, cudaStream_t s)
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, const float *dLdI, float4 *grad, int ker,
+                                cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
     if (ker == 1)
-        k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, ball, wblk, gids, ranges, dLdI,
-                                            (float *)grad);
+        k_rays_adjoint<1><<<nb, RB, 0, s>>>(ro, rd, nullptr, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
     else
-        k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, ball, wblk, gids, ranges, dLdI,
-                                            (float *)grad);
+        k_rays_adjoint<0><<<nb, RB, 0, s>>>(ro, rd, tof, n_rays, b0, rec, gids, ranges, dLdI, (float *)grad);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -132,19 +132,20 @@ int rays_ball_parts(int64_t n);        // partial scene boxes of the ball pass
 cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
                             int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
                             float4 *wblk, uint32_t *cnt, cudaStream_t s);
-// lists of blocks b0 .. b0+nb-1 (ascending Gaussian ids) at offsets off[0..nb)
-cudaError_t launch_rays_emit(const float4 *blk, const float4 *ball, int64_t n, int64_t b0, int nb,
-                             const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
+// per-warp lists (RAYS_WPB per block, ascending Gaussian ids) of blocks
+// b0 .. b0+nb-1 at offsets off[0 .. RAYS_WPB nb); cnt holds RAYS_WPB counts per block
+constexpr int RAYS_WPB = 4;
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const float4 *ball, int64_t n, int64_t b0,
+                             int nb, const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
                              cudaStream_t s);
 // tof (nullable, Gaussian kernel only): per ray (t_c, tau)
 cudaError_t launch_rays_forward(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
-                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
-                                float *out, int ker, cudaStream_t s);
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, float *out, int ker, cudaStream_t s);
 cudaError_t launch_rays_adjoint(const float4 *ro, const float4 *rd, const float2 *tof, int64_t n_rays,
-                                int64_t b0, int nb, const float4 *rec, const float4 *ball,
-                                const float4 *wblk, const uint32_t *gids, const uint2 *ranges,
-                                const float *dLdI, float4 *grad, int ker, cudaStream_t s);
+                                int64_t b0, int nb, const float4 *rec, const uint32_t *gids,
+                                const uint2 *ranges, const float *dLdI, float4 *grad, int ker,
+                                cudaStream_t s);
 
 // ---- voxelisation (voxel.cu) ----------------------------------------------
 // voxel (i, j, k) centre = (ox + i sx, oy + j sy, oz + k sz); bricks of
