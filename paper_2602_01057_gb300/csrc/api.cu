@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <utility>
 #include <map>
 #include <new>
 #include <string>
@@ -181,11 +182,27 @@ void prof_harvest(rgrt_ctx *c)
 
 // ---- pipeline pieces ------------------------------------------------------
 
+// records of the current parameters; total[1] collects the non-finite flag,
+// which the next host read-back of the binning totals checks
 int build_records(rgrt_ctx *ctx, const rgrt_gauss *g, cudaStream_t s)
 {
     if (g->n == 0) return RGRT_OK;
+    TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
+    unsigned long long *bad = (unsigned long long *)ctx->total.p + 1;
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
     PROF("k_records");
-    CK(launch_records(g->mu, g->ls, g->q, g->rho, g->n, g->rec, g->crec, s));
+    CK(launch_records(g->mu, g->ls, g->q, g->rho, g->n, g->rec, g->crec, (uint32_t *)bad, s));
+    return RGRT_OK;
+}
+
+// the binning totals (K) and the non-finite flag, read back together
+int read_totals(rgrt_ctx *ctx, cudaStream_t s, unsigned long long *K)
+{
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_total[1])
+        return fail(RGRT_E_INVAL, "non-finite Gaussian parameters (mu, log-scale, quaternion or rho)");
+    if (K) *K = ctx->h_total[0];
     return RGRT_OK;
 }
 
@@ -223,9 +240,8 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
         CK(launch_scan((uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p, E,
                        (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
     }
-    CK(cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    unsigned long long K = *ctx->h_total;
+    unsigned long long K = 0;
+    TRY(read_totals(ctx, s, &K));
     if (K >= 0xffffffffull)
         return fail(RGRT_E_CAPACITY, "views %d..%d produce %llu tile entries (more than 2^32)", v0,
                     v0 + nv, K);
@@ -248,8 +264,15 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     }
     {
         PROF("radix_sort");
+        bool in_alt = false;
         CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
-                       (uint32_t)K, ceil_log2(T) + 8, (uint32_t *)ctx->sort_tmp.p, s));
+                       (uint32_t)K, ceil_log2(T) + 8, (uint32_t *)ctx->sort_tmp.p, s, &in_alt));
+        if (in_alt) {   // adopt the buffers that hold the result
+            std::swap(ctx->keys, ctx->keys_alt);
+            std::swap(ctx->vals, ctx->vals_alt);
+            keys = (uint32_t *)ctx->keys.p;
+            vals = (uint32_t *)ctx->vals.p;
+        }
     }
     {
         PROF("k_ranges");
@@ -355,7 +378,7 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     }
     ctx->h_cnt.resize(TL);
     CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * TL, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    TRY(read_totals(ctx, s, nullptr));
     // list capacity: what the budget leaves (the current list buffer included)
     size_t avail = ctx->budget > ctx->used ? ctx->budget - ctx->used : 0;
     avail += ctx->vals.bytes;
@@ -1121,9 +1144,8 @@ int gaussians_voxelize(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_volume_des
             CK(launch_scan((uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p, N,
                            (unsigned long long *)ctx->total.p, (unsigned long long *)ctx->scan_tmp.p, s));
         }
-        CK(cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const unsigned long long K = *ctx->h_total;
+        unsigned long long K = 0;
+        TRY(read_totals(ctx, s, &K));
         if (K >= 0xffffffffull)
             return fail(RGRT_E_CAPACITY, "%llu (brick, Gaussian) entries (more than 2^32)", K);
         TRY(ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)(K ? K : 1)));

@@ -149,7 +149,7 @@ int plan(rgrt_batch *b)
         BatchScan &x = b->sc[i];
         DevGeom dg = x.geom->dg;
         dg.v0 = 0;
-        BK(launch_records(x.g->mu, x.g->ls, x.g->q, x.g->rho, x.N, x.g->rec, x.g->crec, s));
+        BK(launch_records(x.g->mu, x.g->ls, x.g->q, x.g->rho, x.N, x.g->rec, x.g->crec, nullptr, s));
         BK(launch_cull(dg, dg.n_views, x.g->crec, x.N, b->cnt, b->rect, s));
         BK(launch_scan(b->cnt, b->off, x.E, b->total, b->stmp, s));
         unsigned long long K = 0;
@@ -213,7 +213,7 @@ int enqueue_binning(rgrt_batch *b, cudaStream_t s)
         BatchScan &x = b->sc[i];
         DevGeom dg = x.geom->dg;
         dg.v0 = 0;
-        BK(launch_records(x.g->mu, x.g->ls, x.g->q, x.g->rho, x.N, x.g->rec, x.g->crec, s));
+        BK(launch_records(x.g->mu, x.g->ls, x.g->q, x.g->rho, x.N, x.g->rec, x.g->crec, nullptr, s));
         BK(launch_cull(dg, dg.n_views, x.g->crec, x.N, b->cnt, b->rect, s));
         BK(launch_scan(b->cnt, b->off, x.E, b->total, b->stmp, s));
         // padding entries keep the all-ones key: they sort last and map to no tile

@@ -191,44 +191,79 @@ __global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int s
 
 // stable scatter: rank of a key = keys with the same digit in earlier rounds
 // of this block + in earlier warps of this round + in lower lanes of its warp
+// Scatter of one radix pass.  A CTA takes a tile of SORT_TILE keys: it ranks
+// them stably by digit inside the tile (rounds in order, warps in order, lanes
+// in order), places keys and values at their tile-local positions in shared
+// memory, and then writes the tile out in that order -- each digit's keys are
+// consecutive there and land consecutively at the digit's global offset, so
+// the global writes are runs rather than single words.
 __global__ void k_sort_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                                uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals, uint32_t n,
-                               int shift, const uint32_t *__restrict__ offs, uint32_t nb)
+                               int shift, const uint32_t *__restrict__ hist,
+                               const uint32_t *__restrict__ offs, uint32_t nb)
 {
-    __shared__ uint32_t run[256];
+    __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
+    __shared__ uint32_t lbase[256], run[256];
     __shared__ uint32_t wc[SORT_BS / 32][256];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    run[t] = offs[(size_t)t * nb + blockIdx.x];
     const uint32_t lt = (1u << lane) - 1u;
-    uint32_t base = blockIdx.x * SORT_TILE;
+    const uint32_t base = blockIdx.x * SORT_TILE;
+    // tile-local start of every digit: exclusive scan of the tile's histogram
+    {
+        const uint32_t c = hist[(size_t)t * nb + blockIdx.x];
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wc[0][w] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int ww = 0; ww < w; ww++) add += wc[0][ww];
+        lbase[t] = add + x - c;
+        run[t] = add + x - c;
+        __syncthreads();
+    }
     for (int r = 0; r < SORT_ROUNDS; r++) {
 #pragma unroll
         for (int ww = 0; ww < SORT_BS / 32; ww++) wc[ww][t] = 0;
         __syncthreads();
-        uint32_t i = base + r * SORT_BS + t;
-        bool valid = i < n;
-        uint32_t key = valid ? keys[i] : 0u;
-        uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt);
+        const uint32_t i = base + r * SORT_BS + t;
+        const bool valid = i < n;
+        const uint32_t key = valid ? keys[i] : 0u;
+        const uint32_t val = valid ? vals[i] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) wc[w][d] = __popc(peers);
         __syncthreads();
         uint32_t acc = run[t];
 #pragma unroll
         for (int ww = 0; ww < SORT_BS / 32; ww++) {
-            uint32_t c = wc[ww][t];
+            const uint32_t c = wc[ww][t];
             wc[ww][t] = acc;
             acc += c;
         }
         run[t] = acc;
         __syncthreads();
         if (valid) {
-            uint32_t dst = wc[w][d] + rank;
-            if (dst >= n) dst = i;  // never taken when the histogram scan is consistent
-            okeys[dst] = key;
-            ovals[dst] = vals[i];
+            const uint32_t at = wc[w][d] + rank;   // tile-local position
+            if (at < SORT_TILE) {
+                sk[at] = key;
+                sv[at] = val;
+            }
         }
         __syncthreads();
+    }
+    const uint32_t cnt = min((uint32_t)SORT_TILE, n - base);
+    for (uint32_t k = t; k < cnt; k += SORT_BS) {
+        const uint32_t key = sk[k];
+        const uint32_t d = (key >> shift) & 255u;
+        uint32_t dst = offs[(size_t)d * nb + blockIdx.x] + (k - lbase[d]);
+        if (dst >= n) dst = base + k;  // never taken when the histogram scan is consistent
+        okeys[dst] = key;
+        ovals[dst] = sv[k];
     }
 }
 
@@ -281,8 +316,9 @@ size_t sort_tmp_elems(uint32_t n)
 }
 
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s)
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt)
 {
+    if (in_alt) *in_alt = false;
     if (n == 0) return cudaSuccess;
     uint32_t nb = (n + SORT_TILE - 1) / SORT_TILE;
     size_t hn = (size_t)256 * nb;
@@ -299,14 +335,18 @@ cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint
         k_sort_hist<<<nb, SORT_BS, 0, s>>>(src_k, n, shift, hist, nb);
         cudaError_t e = launch_scan(hist, offs, (int64_t)hn, stot, stmp, s);
         if (e != cudaSuccess) return e;
-        k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, offs, nb);
+        k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, offs, nb);
         count_launches(2);
         uint32_t *tk = src_k, *tv = src_v;
         src_k = dst_k; src_v = dst_v; dst_k = tk; dst_v = tv;
     }
-    if (src_k != keys) {  // odd pass count: bring the result home
-        cudaMemcpyAsync(keys, src_k, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (src_k != keys) {  // odd pass count: the result sits in the alternate buffers
+        if (in_alt) {
+            *in_alt = true;
+        } else {
+            cudaMemcpyAsync(keys, src_k, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        }
     }
     return cudaGetLastError();
 }

@@ -211,7 +211,7 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
     dg.vtab = dg.utab + W;
 
     NA_CK(cudaMemcpyAsync(d_tab, tab, sizeof(float) * ntab, cudaMemcpyHostToDevice, s));
-    NA_CK(launch_records(mu3, logscale3, quat4, rho, n, rec, crec, s));
+    NA_CK(launch_records(mu3, logscale3, quat4, rho, n, rec, crec, nullptr, s));
     NA_CK(launch_cull(dg, V, crec, n, cnt, rect, s));
     NA_CK(launch_scan(cnt, off, E, total, stmp, s));
     unsigned long long K = 0;

@@ -36,6 +36,11 @@ namespace rgrt {
 namespace {
 
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
+// chunk buffers of the forward: with two, a chunk's records are prepared into
+// one buffer while slower warps still read the other, and a single barrier
+// per chunk suffices -- but the doubled shared memory drops the kernel to 3
+// CTAs per SM and the cone-beam forward measured 2% slower, so one it is
+constexpr int NBUF = 1;
 constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
 constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
 constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
@@ -348,9 +353,9 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const uint2 *__restrict__ ranges,
                                              float *__restrict__ out, Stats *stats)
 {
-    __shared__ VRec sv[CH];
+    __shared__ VRec sv_buf[NBUF][CH];
     __shared__ ChunkLists lists;
-    __shared__ uint32_t msk[CH];
+    __shared__ uint32_t msk_buf[NBUF][CH];
     __shared__ float4 wbox[8];
     __shared__ float Fs[9];
     const TileCtx c = tile_ctx(g, tile);
@@ -374,7 +379,11 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     const uint32_t nch = (nlist + CH - 1) / CH;
     for (uint32_t ch = 0; ch < nch; ch++) {
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
+        VRec *sv = sv_buf[ch % NBUF];
+        uint32_t *msk = msk_buf[ch % NBUF];
         prep_chunk<CONE, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk);
+        // every thread has prepared this chunk and (with two buffers) left the
+        // previous one, whose buffer the next chunk's preparation reuses
         __syncthreads();
         int nvs, ngen;
         build_lists(cnt, msk, lists, w, lane, nvs, ngen);
@@ -406,7 +415,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
             }
         }
         if (STATS) n_eval += nvs + ngen;
-        __syncthreads();
+        if (NBUF == 1) __syncthreads();
     }
     if (c.valid) out[c.out_idx] = acc_gen + L * acc_vs;
     if (STATS) {

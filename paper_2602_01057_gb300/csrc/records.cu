@@ -37,11 +37,17 @@ __device__ __forceinline__ float exp_spec(float x)
 
 __global__ void k_records(const float *__restrict__ mu, const float *__restrict__ ls,
                           const float *__restrict__ q, const float *__restrict__ rho, int64_t n,
-                          float4 *__restrict__ rec, float4 *__restrict__ crec)
+                          float4 *__restrict__ rec, float4 *__restrict__ crec, uint32_t *bad)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     float qw = q[4 * k], qx = q[4 * k + 1], qy = q[4 * k + 2], qz = q[4 * k + 3];
+    // a non-finite parameter (a diverged optimisation, corrupted input) is
+    // reported to the host, which refuses the projection
+    if (bad && !(isfinite(mu[3 * k]) && isfinite(mu[3 * k + 1]) && isfinite(mu[3 * k + 2]) &&
+                 isfinite(ls[3 * k]) && isfinite(ls[3 * k + 1]) && isfinite(ls[3 * k + 2]) &&
+                 isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(rho[k])))
+        atomicOr(bad, 1u);
     float n2 = A(A(A(M(qw, qw), M(qx, qx)), M(qy, qy)), M(qz, qz));
     float w, x, y, z;
     if (!(n2 > 0.0f) || !(n2 < INFINITY)) {
@@ -192,11 +198,11 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
 }  // namespace
 
 cudaError_t launch_records(const float *mu, const float *ls, const float *q, const float *rho,
-                           int64_t n, float4 *rec, float4 *crec, cudaStream_t s)
+                           int64_t n, float4 *rec, float4 *crec, uint32_t *bad, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     int bs = 256;
-    k_records<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(mu, ls, q, rho, n, rec, crec);
+    k_records<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(mu, ls, q, rho, n, rec, crec, bad);
     count_launches(1);
     return cudaGetLastError();
 }

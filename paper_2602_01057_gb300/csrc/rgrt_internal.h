@@ -52,8 +52,9 @@ int validate_geometry(const rgrt_geom_desc *d);
 int report_error(int code, const char *msg);
 
 // ---- launchers (each returns cudaGetLastError of its launch) -------------
+// bad (nullable): set to nonzero when a parameter is not finite
 cudaError_t launch_records(const float *mu, const float *ls, const float *q, const float *rho,
-                           int64_t n, float4 *rec, float4 *crec, cudaStream_t s);
+                           int64_t n, float4 *rec, float4 *crec, uint32_t *bad, cudaStream_t s);
 cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n, uint32_t *cnt,
                         uint2 *rect, cudaStream_t s);
 cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
@@ -72,8 +73,10 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
 // end in (keys, vals) (alt buffers are scratch).  tmp must hold
 // sort_tmp_elems(n) u32.
 size_t sort_tmp_elems(uint32_t n);
+// in_alt (nullable): set when the result is left in (keys_alt, vals_alt)
+// instead of being copied back (an odd number of passes)
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s);
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt = nullptr);
 
 // ker: kernel of the primitives (RGRT_KERNEL_GAUSSIAN / RGRT_KERNEL_EPANECHNIKOV)
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,

@@ -423,3 +423,28 @@ def test_loss_with_measurement_model(rg, ctx, torch, oracle, loss):
     L_plain = (oracle.loss_l2(ref_fwd["I"], y) if loss == "l2"
                else oracle.loss_poisson(ref_fwd["I"], y, kappa, eps))[0]
     assert float(lo[0]) == pytest.approx(L_plain, rel=1e-5)
+
+
+@pytest.mark.parametrize("field", ["mu", "ls", "q", "rho"])
+def test_non_finite_parameters_are_refused(rg, ctx, torch, field):
+    """A NaN or infinite parameter (a diverged optimisation) makes the
+    projector return an error instead of a silently wrong projection; finite
+    parameters set afterwards project again."""
+    G, gd = case("cone_small")
+    bad = {k: np.array(G[k], copy=True) for k in ("mu", "ls", "q", "rho")}
+    if field == "rho":
+        bad["rho"][17] = np.nan
+    else:
+        bad[field][17, 1] = np.inf if field == "ls" else np.nan
+    gs = rg.Gaussians(ctx, *[_dev(torch, bad)[k] for k in ("mu", "ls", "q", "rho")])
+    geom = rg.Geometry(ctx, gd)
+    out = torch.empty(geom.n_rays, device="cuda")
+    with pytest.raises(rg.RgrtError):
+        rg.project_forward(ctx, gs, geom, out)
+    with pytest.raises(rg.RgrtError):
+        rg.loss_step(ctx, gs, geom, np.zeros(geom.n_rays, np.float32), rg.RGRT_LOSS_L2, rg.adam_params(), 1,
+                     np.zeros(1, np.float32))
+    gs.set(*[G[k] for k in ("mu", "ls", "q", "rho")])
+    rg.project_forward(ctx, gs, geom, out)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(out.cpu().numpy()))
