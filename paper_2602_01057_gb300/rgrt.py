@@ -237,9 +237,12 @@ class Gaussians:
         self.ctx = ctx
 
     def close(self):
-        if self.h:
+        # after its context has been closed the handle is only dropped (its
+        # device memory stays allocated until the process ends): destroying it
+        # would reach into the freed context
+        if self.h and self.ctx.h:
             lib().gaussians_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -322,9 +325,12 @@ class Geometry:
         return self
 
     def close(self):
-        if self.h:
+        # after its context has been closed the handle is only dropped (its
+        # device memory stays allocated until the process ends): destroying it
+        # would reach into the freed context
+        if self.h and self.ctx.h:
             lib().geometry_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -386,9 +392,12 @@ class Batch:
         self.h = h
 
     def close(self):
-        if self.h:
+        # after its context has been closed the handle is only dropped (its
+        # device memory stays allocated until the process ends): destroying it
+        # would reach into the freed context
+        if self.h and self.ctx.h:
             lib().rgrt_batch_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
