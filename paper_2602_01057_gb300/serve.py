@@ -35,7 +35,7 @@ from collections import deque
 
 import numpy as np
 
-from . import rgrt
+from . import rgrt, synth
 
 FWD, GRAD, RECON = "fwd", "grad", "recon"
 
@@ -60,7 +60,7 @@ class Job:
 
 
 def num_rays(geom: dict) -> int:
-    return int(geom["n_views"]) * int(geom["n_rows"]) * int(geom["n_cols"])
+    return synth.num_rays(geom)
 
 
 def job_budget(job: Job) -> int:
@@ -76,7 +76,7 @@ def job_budget(job: Job) -> int:
     Plus 64 MiB of slack for tables and small buffers."""
     n = int(job.G["mu"].shape[0])
     r = num_rays(job.geom)
-    v = int(job.geom["n_views"])
+    v = int(job.geom.get("n_views", 1))
     if job.kind == RECON:
         v = min(v, int(job.views_per_iter))
     v = min(v, 64)
@@ -143,6 +143,8 @@ def run_job(job: Job, device: int, budget: int, stream) -> dict:
         g = rgrt.Gaussians(ctx, *(np.ascontiguousarray(job.G[k], dtype=np.float32)
                                   for k in ("mu", "ls", "q", "rho")))
         objs.append(g)
+        if job.G.get("kernel", "gaussian") != "gaussian":
+            g.set_kernel(job.G["kernel"])
         hp = rgrt.adam_params(**(job.hp or {}))
         if job.kind == FWD:
             geom = rgrt.Geometry(ctx, job.geom)
@@ -164,6 +166,8 @@ def run_job(job: Job, device: int, budget: int, stream) -> dict:
                         grad={k: o.cpu().numpy() for k, o in zip(("mu", "ls", "q", "rho"), outs)})
         if job.kind != RECON:
             raise ValueError(f"unknown job kind {job.kind!r}")
+        if job.geom["kind"] == "rays":
+            raise ValueError("reconstruction jobs take detector geometries (mini-batches are views)")
         geoms, order = subset_geometries(job.geom, job.views_per_iter, job.seed)
         ys = subset_measurements(job.geom, job.y, order, job.views_per_iter)
         yd = torch.from_numpy(ys).to(dev)
