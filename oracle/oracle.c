@@ -47,8 +47,19 @@
  *           d = e_w, t in [-sqrt(R^2-s^2), +sqrt(R^2-s^2)].
  *           Arc-corrected: s_k = (k-c) pi R / n_crystals; raw chords:
  *           s_k = R sin((k-c) pi / n_crystals); c = (n_radial-1)/2.
+ *   kind 3  fully 3-D PET: n_rows rings at z_r = (r - (n_rows-1)/2) pitch_v,
+ *           the LORs between rings r1 and r2 = r1 + delta for every ring
+ *           difference |delta| <= max_ring_diff, at the angles and radial
+ *           bins of kind 2.  View v = (2 max_ring_diff + 1) segments x
+ *           n_views angles: segment sg = v / n_views (delta = sg -
+ *           max_ring_diff), angle a = v % n_views.  Row j is the ring pair
+ *           r1 = j + max(0, -delta) (j < n_rows - |delta|; the other rows
+ *           have no LOR and project to 0), at the mid-height
+ *           z_mid = (z_r1 + z_r2)/2.  The LOR runs from
+ *           s e_u - h e_w + z_r1 e_z to s e_u + h e_w + z_r2 e_z, h = sqrt(R^2 - s^2).
  *   Pixel coordinates: u_i = (i - (n_cols-1)/2) pitch_u, v_j likewise.
- *   Output layout: CT [view][row][col]; PET [plane][angle][radial].
+ *   Output layout: CT [view][row][col]; PET [plane][angle][radial];
+ *   3-D PET [segment][angle][ring pair][radial].
  *
  * It also holds an FP32 replica of the culling predicate (records and
  * detector bounding boxes) used only to check that the GPU tile lists are
@@ -67,12 +78,25 @@ typedef struct {
     int32_t kind, n_views, n_rows, n_cols;
     const double *angles;
     double pitch_u, pitch_v, t_a, t_b, dso, dsd, radius;
-    int32_t n_crystals, arc_mode;
+    int32_t n_crystals, arc_mode, max_ring_diff;
 } og_geom;
 
 #define OG_PARALLEL 0
 #define OG_CONE 1
 #define OG_PET 2
+#define OG_PET3D 3
+
+/* number of views: 3-D PET has one per (segment, angle) */
+static int og_nviews(const og_geom *g)
+{
+    return g->kind == OG_PET3D ? g->n_views * (2 * g->max_ring_diff + 1) : g->n_views;
+}
+
+/* 3-D PET: ring difference of view v */
+static int og_delta(const og_geom *g, int v)
+{
+    return v / g->n_views - g->max_ring_diff;
+}
 
 static const double OG_PI = 3.14159265358979323846;
 
@@ -82,7 +106,8 @@ static const double OG_PI = 3.14159265358979323846;
 
 static void og_frame(const og_geom *g, int v, double eu[3], double ev[3], double ew[3])
 {
-    if (g->kind == OG_PET) {
+    if (g->kind == OG_PET || g->kind == OG_PET3D) {
+        if (g->kind == OG_PET3D) v = v % g->n_views;
         double phi = g->angles ? g->angles[v] : (OG_PI * (double)v) / (double)g->n_views;
         double c = cos(phi), s = sin(phi);
         eu[0] = c;  eu[1] = s;  eu[2] = 0.0;
@@ -100,7 +125,7 @@ static void og_frame(const og_geom *g, int v, double eu[3], double ev[3], double
 static double og_u(const og_geom *g, int i)
 {
     double k = (double)i - 0.5 * (double)(g->n_cols - 1);
-    if (g->kind == OG_PET) {
+    if (g->kind == OG_PET || g->kind == OG_PET3D) {
         if (g->arc_mode == 0)
             return k * ((OG_PI * g->radius) / (double)g->n_crystals);
         return g->radius * sin((k * OG_PI) / (double)g->n_crystals);
@@ -113,6 +138,13 @@ static double og_v(const og_geom *g, int j)
     return ((double)j - 0.5 * (double)(g->n_rows - 1)) * g->pitch_v;
 }
 
+/* 3-D PET: mid-height of ring pair j in view v (its segment) */
+static double og_v3(const og_geom *g, int v, int j)
+{
+    int ad = abs(og_delta(g, v));
+    return ((double)j + 0.5 * (double)ad - 0.5 * (double)(g->n_rows - 1)) * g->pitch_v;
+}
+
 static int64_t og_index(const og_geom *g, int v, int j, int i)
 {
     if (g->kind == OG_PET)
@@ -120,12 +152,33 @@ static int64_t og_index(const og_geom *g, int v, int j, int i)
     return ((int64_t)v * g->n_rows + j) * g->n_cols + i;
 }
 
-static void og_ray(const og_geom *g, int v, int j, int i,
-                   double o[3], double d[3], double *ta, double *tb)
+/* the ray of pixel (v, j, i); returns 0 when the pixel has none (3-D PET rows
+ * beyond the segment's ring pairs) */
+static int og_ray(const og_geom *g, int v, int j, int i,
+                  double o[3], double d[3], double *ta, double *tb)
 {
     double eu[3], ev[3], ew[3];
     og_frame(g, v, eu, ev, ew);
     double u = og_u(g, i), w = og_v(g, j);
+    if (g->kind == OG_PET3D) {
+        int delta = og_delta(g, v);
+        if (j >= g->n_rows - abs(delta)) {
+            for (int k = 0; k < 3; k++) { o[k] = 0.0; d[k] = ew[k]; }
+            *ta = *tb = 0.0;
+            return 0;
+        }
+        double h = g->radius * g->radius - u * u;
+        h = h > 0.0 ? sqrt(h) : 0.0;
+        double zm = og_v3(g, v, j), dz = (double)delta * g->pitch_v;
+        double L = sqrt(4.0 * h * h + dz * dz);
+        for (int k = 0; k < 3; k++) {
+            o[k] = u * eu[k] + zm * ev[k];
+            d[k] = (2.0 * h * ew[k] + dz * ev[k]) / L;
+        }
+        *ta = -0.5 * L;
+        *tb = 0.5 * L;
+        return 1;
+    }
     if (g->kind == OG_CONE) {
         double S[3], D[3], L = 0.0;
         for (int k = 0; k < 3; k++) {
@@ -149,6 +202,7 @@ static void og_ray(const og_geom *g, int v, int j, int i,
             *tb = g->t_b;
         }
     }
+    return 1;
 }
 
 static void og_unflatten(const og_geom *g, int64_t idx, int *v, int *j, int *i)
@@ -469,6 +523,41 @@ static void og_bbox(const og_geom *g, int v, const double mu[3], double Sig[3][3
     }
     *i0 = og_lower(utab, g->n_cols, ulo);
     *i1 = og_upper(utab, g->n_cols, uhi);
+    if (g->kind == OG_PET3D) {
+        /* the LOR at (s, z_mid) has z = z_mid + slope w (w along e_w), slope =
+         * dz / (2 h(s)): it meets the ellipsoid only if z_mid lies in
+         * mu_z - slope mu_w +- sqrt(K2 a^T Sigma a), a = e_z - slope e_w; over
+         * the box's s-range the slope spans [dz/2h_max, dz/2h_min] and the
+         * union of those intervals is bounded by its end slopes */
+        int delta = og_delta(g, v), ad = abs(delta);
+        double dz = (double)delta * g->pitch_v;
+        double mu_w = mu[0] * ew[0] + mu[1] * ew[1] + mu[2] * ew[2];
+        double slo_ = ulo < utab[0] ? utab[0] : ulo, shi_ = uhi > utab[g->n_cols - 1] ? utab[g->n_cols - 1] : uhi;
+        double amin = (slo_ <= 0.0 && shi_ >= 0.0) ? 0.0 : fmin(fabs(slo_), fabs(shi_));
+        double amax = fmax(fabs(slo_), fabs(shi_));
+        double R2 = g->radius * g->radius;
+        double hmax = sqrt(fmax(R2 - amin * amin, 0.0)), hmin = sqrt(fmax(R2 - amax * amax, 0.0));
+        int last = g->n_rows - ad - 1;
+        if (!(hmin > 0.0)) {            /* the box reaches the ring's edge: slopes unbounded */
+            *j0 = 0;
+            *j1 = last;
+            return;
+        }
+        double zl = INFINITY, zh = -INFINITY;
+        for (int e = 0; e < 2; e++) {
+            double hh = e ? hmin : hmax;
+            double sl = dz / (2.0 * hh);
+            double a[3] = { -sl * ew[0], -sl * ew[1], 1.0 - sl * ew[2] };
+            double c = mu[2] - sl * mu_w, half = sqrt(K2 * og_quad(Sig, a, a));
+            zl = fmin(zl, c - half);
+            zh = fmax(zh, c + half);
+        }
+        double off = 0.5 * (double)ad - 0.5 * (double)(g->n_rows - 1);
+        double jl = ceil(zl / g->pitch_v - off), jh = floor(zh / g->pitch_v - off);
+        *j0 = jl < 0.0 ? 0 : (jl > last + 1 ? last + 1 : (int)jl);
+        *j1 = jh > last ? last : (jh < -1.0 ? -1 : (int)jh);
+        return;
+    }
     *j0 = og_lower(vtab, g->n_rows, vlo);
     *j1 = og_upper(vtab, g->n_rows, vhi);
 }
@@ -550,7 +639,7 @@ void or_cov(int64_t n, const float *ls, const float *q, double *sig9, double *p9
 
 int64_t or_num_rays(const og_geom *g)
 {
-    return (int64_t)g->n_views * g->n_rows * g->n_cols;
+    return (int64_t)og_nviews(g) * g->n_rows * g->n_cols;
 }
 
 /* rays for flat output indices */
@@ -598,7 +687,7 @@ void or_forward(const og_geom *g, int64_t n, const float *mu, const float *ls, c
     for (int64_t k = 0; k < n; k++) og_cov(ls + 3 * k, q + 4 * k, Sig[k], P[k]);
     int64_t npair = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : npair)
-    for (int v = 0; v < g->n_views; v++) {
+    for (int v = 0; v < og_nviews(g); v++) {
         for (int64_t k = 0; k < n; k++) {
             double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
             int i0 = 0, i1 = g->n_cols - 1, j0 = 0, j1 = g->n_rows - 1;
@@ -606,7 +695,7 @@ void or_forward(const og_geom *g, int64_t n, const float *mu, const float *ls, c
             for (int j = j0; j <= j1; j++)
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
-                    og_ray(g, v, j, i, o, d, &ta, &tb);
+                    if (!og_ray(g, v, j, i, o, d, &ta, &tb)) continue;
                     og_pairval r;
                     og_eval(o, d, ta, tb, m3, P[k], rho[k], 0.0, 0.0, &r);
                     int64_t x = og_index(g, v, j, i);
@@ -632,8 +721,9 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
         int v, j, i;
         og_unflatten(g, idx[r], &v, &j, &i);
         double o[3], d[3], ta, tb;
-        og_ray(g, v, j, i, o, d, &ta, &tb);
+        const int has = og_ray(g, v, j, i, o, d, &ta, &tb);
         double s = 0.0, slo = 0.0, shi = 0.0;
+        if (!has) { I[r] = Ilo[r] = Ihi[r] = 0.0; continue; }
         for (int64_t k = 0; k < n; k++) {
             double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
             og_pairval pv;
@@ -725,13 +815,13 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
         double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
         og_gradacc acc;
         memset(&acc, 0, sizeof(acc));
-        for (int v = 0; v < g->n_views; v++) {
+        for (int v = 0; v < og_nviews(g); v++) {
             int i0 = 0, i1 = g->n_cols - 1, j0 = 0, j1 = g->n_rows - 1;
             if (!brute) og_bbox(g, v, m3, Sig, og_box_k2(cut2, band), ut, vt, &i0, &i1, &j0, &j1);
             for (int j = j0; j <= j1; j++)
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
-                    og_ray(g, v, j, i, o, d, &ta, &tb);
+                    if (!og_ray(g, v, j, i, o, d, &ta, &tb)) continue;
                     og_grad_pair(&acc, o, d, ta, tb, 0.0, 0.0, m3, P, rho[k], dLdI[og_index(g, v, j, i)], cut2,
                                  band, ls + 3 * k, q + 4 * k);
                 }

@@ -46,10 +46,11 @@ class _Geom(ctypes.Structure):
         ("t_a", ctypes.c_double), ("t_b", ctypes.c_double),
         ("dso", ctypes.c_double), ("dsd", ctypes.c_double), ("radius", ctypes.c_double),
         ("n_crystals", ctypes.c_int32), ("arc_mode", ctypes.c_int32),
+        ("max_ring_diff", ctypes.c_int32),
     ]
 
 
-_KIND = {"parallel": 0, "cone": 1, "pet": 2}
+_KIND = {"parallel": 0, "cone": 1, "pet": 2, "pet3d": 3}
 _lib = None
 
 
@@ -93,8 +94,10 @@ class Geometry:
             float(desc.get("t_a", 0.0)), float(desc.get("t_b", 0.0)),
             float(desc.get("dso", 0.0)), float(desc.get("dsd", 0.0)),
             float(desc.get("radius", 0.0)), int(desc.get("n_crystals", 0)),
-            int(desc.get("arc_mode", 0)))
-        self.n_rays = int(desc["n_views"]) * int(desc["n_rows"]) * int(desc["n_cols"])
+            int(desc.get("arc_mode", 0)), int(desc.get("max_ring_diff", 0)))
+        self.n_views = int(desc["n_views"]) * (2 * int(desc.get("max_ring_diff", 0)) + 1
+                                               if desc["kind"] == "pet3d" else 1)
+        self.n_rays = self.n_views * int(desc["n_rows"]) * int(desc["n_cols"])
 
     @property
     def ref(self):
@@ -319,6 +322,8 @@ def cull_fp32(geom, G, tile_w, tile_h):
     """FP32 cull: (pixel box[V, n, 4] = i0, i1, j0, j1; tile rectangle[V, n, 4]
     = tx0, tx1, ty0, ty1; tile count[V, n])."""
     g = _geom(geom)
+    if g.desc["kind"] == "pet3d":
+        raise ValueError("the FP32 cull reference covers the detector geometries of kinds 0-2")
     n, mu, ls, q, rho = _gauss(G)
     V = int(g.desc["n_views"])
     box = np.zeros((V, n, 4), dtype=np.int32)

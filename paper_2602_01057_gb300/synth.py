@@ -154,6 +154,19 @@ def geom_pet(n_angles: int, n_radial: int, n_planes: int, radius: float, n_cryst
                 n_crystals=n_crystals, arc_mode=arc_mode, tile_w=tile[0], tile_h=tile[1])
 
 
+def geom_pet3d(n_angles: int, n_radial: int, n_rings: int, radius: float, n_crystals: int,
+               ring_pitch: float, max_ring_diff: int, arc_mode: int = 0, tile=(16, 16)) -> dict:
+    """Fully 3-D PET sinograms: one view per (ring difference delta in
+    [-max_ring_diff, max_ring_diff], angle), delta-major; row j of a view is
+    the ring pair (min ring j, ring difference delta), rows j >= n_rings -
+    |delta| carry no LOR (their output is 0).  Output [delta][angle][ring
+    pair][radial]."""
+    return dict(kind="pet3d", n_views=n_angles, n_rows=n_rings, n_cols=n_radial,
+                angles=np.zeros(0, dtype=np.float64), pitch_u=0.0, pitch_v=ring_pitch,
+                t_a=0.0, t_b=0.0, dso=0.0, dsd=0.0, radius=radius, n_crystals=n_crystals,
+                arc_mode=arc_mode, max_ring_diff=max_ring_diff, tile_w=tile[0], tile_h=tile[1])
+
+
 def geom_c1(tile=(16, 16)) -> dict:
     return geom_parallel(16, 64, 64, 2.0 / 64, 2.0 / 64, -2.0, 2.0, span=math.pi, tile=tile)
 
@@ -176,7 +189,10 @@ def geom_c3(n_angles: int = 288, n_radial: int = 329, n_planes: int = 63, arc_mo
 def num_rays(g: dict) -> int:
     if g["kind"] == "rays":
         return int(np.asarray(g["o"]).shape[0])
-    return int(g["n_views"]) * int(g["n_rows"]) * int(g["n_cols"])
+    v = int(g["n_views"])
+    if g["kind"] == "pet3d":
+        v *= 2 * int(g["max_ring_diff"]) + 1
+    return v * int(g["n_rows"]) * int(g["n_cols"])
 
 
 # ---------------------------------------------------------------------------
