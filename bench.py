@@ -59,9 +59,12 @@ WORKLOADS = {
     "recon": "reconstruction quality: the 50,000 Gaussians of the cone-beam CT workload fitted (L2 + Adam) "
              "to the exact line integrals of their 12-ellipsoid phantom over 180 views x 256^2; PSNR of the "
              "voxelised volume (128^3) against the phantom's density",
-    "pet3d": "fully 3-D PET fwd+bwd (Poisson NLL + Adam) as explicit rays: 200,000 Gaussians, 32 rings of 576 "
-             "crystals (radius 400 mm, ring pitch 4 mm), ring differences up to 5, 288 angles x 329 radial "
-             "(30.5M LORs)",
+    "pet3d": "fully 3-D PET fwd+bwd (Poisson NLL + Adam) on structured sinograms: 200,000 Gaussians, 32 "
+             "rings of 576 crystals (radius 400 mm, ring pitch 4 mm), ring differences up to 5 (11 segments), "
+             "288 angles x 329 arc-corrected radial bins (30.5M LORs; 33.4M sinogram bins with the rows "
+             "past each segment's last ring pair)",
+    "pet3d-rays": "the LORs of pet3d as explicit rays (geometry_set_rays, no detector structure), fwd+bwd "
+                  "(Poisson NLL + Adam)",
     "vox": "voxelisation: the 50,000 Gaussians of the cone-beam CT workload on a 256^3 grid of "
            "[-1, 1]^3 (density field with the 3-sigma cut)",
     "c5": "serving: Poisson arrivals, 70% loss+gradient jobs / 30% 200-iteration Adam reconstructions "
@@ -111,6 +114,10 @@ def _workload(name, seed):
         G, gd = synth.workload_c3(seed)
         true = synth.perturbed(G, seed + 101, pos_std=1.0)
         return G, true, gd, "poisson"
+    if name == "pet3d":
+        G, _ = synth.workload_c3(seed)
+        true = synth.perturbed(G, seed + 101, pos_std=1.0)
+        return G, true, synth.geom_c3_3d(), "poisson"
     G, gd = synth.workload_c1(seed)
     true = synth.perturbed(G, seed + 101, pos_std=0.01)
     return G, true, gd, "l2"
@@ -154,7 +161,7 @@ def sample_geometry(gd, n_views):
     """The first n_views views of a geometry."""
     sub = dict(gd)
     sub["n_views"] = n_views
-    if gd["kind"] != "pet":
+    if gd["kind"] not in ("pet", "pet3d"):
         sub["angles"] = gd["angles"][:n_views]
     return sub
 
@@ -224,7 +231,7 @@ def gpu_error(rgrt, ctx, G, sub, f, w, g):
 
 
 def auto_views(name):
-    return {"c2": 4, "c3": 4, "c1": 16}[name]
+    return {"c2": 4, "c3": 4, "c1": 16, "pet3d": 1}[name]
 
 
 def run_reference(args):
@@ -865,7 +872,8 @@ def run_recon(args):
 
 
 def run_pet3d(args):
-    """Oblique PET segments through the explicit-ray path: rays/s of a full step."""
+    """The LORs of the 3-D PET workload through the explicit-ray path: rays/s
+    of a full step."""
     import torch
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
@@ -914,7 +922,7 @@ def run_pet3d(args):
     line = dict(metric=METRIC, value=n_rays / (ms / 1e3), unit=UNIT, n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOADS["pet3d"], rays_per_step=n_rays, gaussians=int(G["mu"].shape[0]),
+                config=dict(workload=WORKLOADS["pet3d-rays"], rays_per_step=n_rays, gaussians=int(G["mu"].shape[0]),
                             l2="not flushed: the step's working set is far above L2"),
                 kernels=kernels, keys_per_step=None, gpu_launches=launches, roofline=None,
                 note="explicit-ray path (no detector structure): the binning tests every Gaussian against "
@@ -936,7 +944,7 @@ def main():
         run_vox(args)
     elif args.workload == "recon":
         run_recon(args)
-    elif args.workload == "pet3d":
+    elif args.workload == "pet3d-rays":
         run_pet3d(args)
     else:
         run_ours(args)

@@ -72,6 +72,7 @@ extern "C" {
 #define RGRT_GEOM_CT_PARALLEL 0
 #define RGRT_GEOM_CT_CONE 1
 #define RGRT_GEOM_PET_RING 2
+#define RGRT_GEOM_PET_3D 3
 
 typedef struct rgrt_ctx rgrt_ctx;
 typedef struct rgrt_gauss rgrt_gauss;
@@ -96,13 +97,24 @@ typedef struct rgrt_geom rgrt_geom;
  * with c = (n_cols-1)/2, plane j at z_j = (j - (n_rows-1)/2) pitch_v; the
  * line of response o = s e_u + z e_v, d = e_w runs over the chord
  * t in [-sqrt(radius^2 - s^2), +sqrt(radius^2 - s^2)].
- * Output layout: CT I[view][row][col]; PET I[plane][angle][radial].
+ * PET_3D (fully 3-D sinograms, the oblique LORs of section 3's geometric
+ * flexibility): n_rows rings at z_r = (r - (n_rows-1)/2) pitch_v, the angles
+ * and radial bins of PET_RING, and one view per (ring difference delta in
+ * [-max_ring_diff, max_ring_diff], angle): view = (delta + max_ring_diff)
+ * n_views + angle.  Row j of a view is the ring pair (r1, r2) = (j, j +
+ * delta) for delta >= 0, (j - delta, j) otherwise; the LOR runs from
+ * s e_u - h e_w + z_r1 e_v to s e_u + h e_w + z_r2 e_v, h = sqrt(radius^2 -
+ * s^2).  Rows j >= n_rows - |delta| have no ring pair: their output is 0 and
+ * they take no gradient.
+ * Output layout: CT I[view][row][col]; PET I[plane][angle][radial];
+ * PET_3D I[delta][angle][ring pair][radial]
+ * ((2 max_ring_diff + 1) n_views n_rows n_cols values).
  * tile_w/tile_h: binning tile in pixels (multiples of 8 and 4; 0 = 16).
  */
 typedef struct {
     int32_t kind;        /* RGRT_GEOM_* */
-    int32_t n_views;     /* CT projections / PET sinogram angles */
-    int32_t n_rows;      /* CT detector rows / PET planes */
+    int32_t n_views;     /* CT projections / PET sinogram angles (PET_3D: per ring difference) */
+    int32_t n_rows;      /* CT detector rows / PET planes / PET_3D rings */
     int32_t n_cols;      /* CT detector columns / PET radial bins */
     const double *angles;/* CT: n_views angles in radians (host memory); PET: null or n_views angles */
     double pitch_u, pitch_v;
@@ -112,6 +124,7 @@ typedef struct {
     int32_t n_crystals;  /* PET crystals per ring */
     int32_t arc_mode;    /* PET: 0 arc-corrected, 1 raw chord positions */
     int32_t tile_w, tile_h;
+    int32_t max_ring_diff; /* PET_3D: largest ring difference, 0..n_rows-1 (other kinds: ignored) */
 } rgrt_geom_desc;
 
 /* Adam hyper-parameters of loss_step (Kingma & Ba; the paper trains with

@@ -530,7 +530,7 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
 int validate_desc(const rgrt_geom_desc *d)
 {
     if (!d) return fail(RGRT_E_INVAL, "null geometry description");
-    if (d->kind < 0 || d->kind > 2) return fail(RGRT_E_INVAL, "unknown geometry kind %d", d->kind);
+    if (d->kind < 0 || d->kind > 3) return fail(RGRT_E_INVAL, "unknown geometry kind %d", d->kind);
     if (d->n_views <= 0 || d->n_rows <= 0 || d->n_cols <= 0)
         return fail(RGRT_E_INVAL, "geometry sizes must be positive (%d views, %d x %d)", d->n_views,
                     d->n_rows, d->n_cols);
@@ -539,13 +539,17 @@ int validate_desc(const rgrt_geom_desc *d)
         return fail(RGRT_E_INVAL, "tile %dx%d: width a multiple of 8, height of 4, 32..256 rays", tw, th);
     if ((d->n_cols + tw - 1) / tw > 65535 || (d->n_rows + th - 1) / th > 65535)
         return fail(RGRT_E_INVAL, "too many tiles per detector axis");
-    if ((int64_t)d->n_views * ((d->n_cols + tw - 1) / tw) * ((d->n_rows + th - 1) / th) > (1 << 30))
+    const bool pet = d->kind == RGRT_GEOM_PET_RING || d->kind == RGRT_GEOM_PET_3D;
+    if (d->kind == RGRT_GEOM_PET_3D && (d->max_ring_diff < 0 || d->max_ring_diff >= d->n_rows))
+        return fail(RGRT_E_INVAL, "max_ring_diff %d outside 0..%d", d->max_ring_diff, d->n_rows - 1);
+    if (desc_views(d) > (1 << 30)) return fail(RGRT_E_INVAL, "too many views");
+    if (desc_views(d) * ((d->n_cols + tw - 1) / tw) * ((d->n_rows + th - 1) / th) > (1 << 30))
         return fail(RGRT_E_INVAL, "too many tiles");
-    if (d->kind == RGRT_GEOM_PET_RING && d->angles) {
+    if (pet && d->angles) {
         for (int v = 0; v < d->n_views; v++)
             if (!std::isfinite(d->angles[v])) return fail(RGRT_E_INVAL, "non-finite view angle %d", v);
     }
-    if (d->kind != RGRT_GEOM_PET_RING) {
+    if (!pet) {
         if (!d->angles) return fail(RGRT_E_INVAL, "CT geometry needs view angles");
         for (int v = 0; v < d->n_views; v++)
             if (!std::isfinite(d->angles[v])) return fail(RGRT_E_INVAL, "non-finite view angle %d", v);
@@ -561,11 +565,11 @@ int validate_desc(const rgrt_geom_desc *d)
         if (!(d->dso > 0) || !(d->dsd > d->dso) || !std::isfinite(d->dsd))
             return fail(RGRT_E_INVAL, "cone beam needs 0 < dso < dsd (finite)");
     }
-    if (d->kind == RGRT_GEOM_PET_RING) {
+    if (pet) {
         if (!(d->radius > 0) || !std::isfinite(d->radius) || d->n_crystals <= 0)
             return fail(RGRT_E_INVAL, "PET ring needs radius > 0 and crystals > 0");
         if (!(d->pitch_v > 0) || !std::isfinite(d->pitch_v))
-            return fail(RGRT_E_INVAL, "PET plane spacing must be positive");
+            return fail(RGRT_E_INVAL, "PET plane / ring spacing must be positive");
         if (d->arc_mode != 0 && d->arc_mode != 1) return fail(RGRT_E_INVAL, "arc_mode must be 0 or 1");
         double c = 0.5 * (double)(d->n_cols - 1);
         double smax = d->arc_mode == 0 ? c * (M_PI * d->radius / d->n_crystals) : d->radius;
@@ -591,6 +595,78 @@ int rgrt::gauss_adam(rgrt_gauss *g, cudaStream_t s)
     g->adam_m = (float *)p;
     g->adam_v = g->adam_m + 11 * g->n;
     return RGRT_OK;
+}
+
+int64_t rgrt::desc_views(const rgrt_geom_desc *d)
+{
+    return d->kind == RGRT_GEOM_PET_3D ? (int64_t)d->n_views * (2 * (int64_t)d->max_ring_diff + 1)
+                                       : (int64_t)d->n_views;
+}
+
+int64_t rgrt::desc_rays(const rgrt_geom_desc *d)
+{
+    return desc_views(d) * d->n_rows * d->n_cols;
+}
+
+void rgrt::geom_tables(const rgrt_geom_desc *d, float *tab, DevGeom &dg)
+{
+    const int V = (int)desc_views(d), H = d->n_rows, W = d->n_cols;
+    const bool pet = d->kind == RGRT_GEOM_PET_RING || d->kind == RGRT_GEOM_PET_3D;
+    const int n_ang = d->n_views;   // PET angles (per ring difference for 3-D PET)
+    const double PI = 3.14159265358979323846;
+    for (int v = 0; v < V; v++) {
+        double eu[3], ev[3], ew[3];
+        if (pet) {
+            const int a = v % n_ang;
+            double phi = d->angles ? d->angles[a] : (PI * (double)a) / (double)n_ang;
+            double c = cos(phi), s = sin(phi);
+            eu[0] = c; eu[1] = s; eu[2] = 0.0;
+            ew[0] = s; ew[1] = -c; ew[2] = 0.0;
+        } else {
+            double th_ = d->angles[v];
+            double c = cos(th_), s = sin(th_);
+            ew[0] = c; ew[1] = s; ew[2] = 0.0;
+            eu[0] = -s; eu[1] = c; eu[2] = 0.0;
+        }
+        ev[0] = 0.0; ev[1] = 0.0; ev[2] = 1.0;
+        for (int k = 0; k < 3; k++) {
+            tab[9 * v + k] = (float)eu[k];
+            tab[9 * v + 3 + k] = (float)ev[k];
+            tab[9 * v + 6 + k] = (float)ew[k];
+        }
+    }
+    float *ut = tab + 9 * (size_t)V, *vt = ut + W;
+    for (int i = 0; i < W; i++) {
+        double k = (double)i - 0.5 * (double)(W - 1);
+        double u;
+        if (pet)
+            u = d->arc_mode == 0 ? k * ((PI * d->radius) / (double)d->n_crystals)
+                                 : d->radius * sin((k * PI) / (double)d->n_crystals);
+        else
+            u = k * d->pitch_u;
+        ut[i] = (float)u;
+    }
+    for (int j = 0; j < H; j++) vt[j] = (float)(((double)j - 0.5 * (double)(H - 1)) * d->pitch_v);
+
+    const int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
+    dg = DevGeom{};
+    dg.kind = d->kind == RGRT_GEOM_CT_CONE ? GM_CONE : d->kind == RGRT_GEOM_PET_3D ? GM_PET3D : GM_PARALLEL;
+    dg.pet = pet;
+    dg.n_views = V; dg.n_rows = H; dg.n_cols = W;
+    dg.tile_w = tw; dg.tile_h = th;
+    dg.tiles_x = (W + tw - 1) / tw;
+    dg.tiles_y = (H + th - 1) / th;
+    dg.v0 = 0;
+    if (d->kind == RGRT_GEOM_PET_RING) { dg.stride_view = W; dg.stride_row = (long long)V * W; }
+    else { dg.stride_view = (long long)H * W; dg.stride_row = W; }
+    dg.dso = (float)d->dso;
+    dg.dsd = (float)d->dsd;
+    dg.t_a = (float)d->t_a;
+    dg.t_b = (float)d->t_b;
+    dg.radius2 = (float)(d->radius * d->radius);
+    dg.n_ang = n_ang;
+    dg.max_rd = d->kind == RGRT_GEOM_PET_3D ? d->max_ring_diff : 0;
+    dg.ring_pitch = (float)d->pitch_v;
 }
 
 // validation and error reporting shared with the allocation-free entry point
@@ -638,7 +714,7 @@ int rgrt_ctx_destroy(rgrt_ctx *c)
     prof_harvest(c);
     Buf *bufs[] = { &c->cnt, &c->off, &c->rect, &c->keys, &c->vals, &c->keys_alt, &c->vals_alt,
                     &c->sort_tmp, &c->scan_tmp, &c->ranges, &c->total, &c->I, &c->dLdI, &c->y,
-                    &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss, &c->ball, &c->part,
+                    &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss, &c->loss_acc, &c->ball, &c->part,
                     &c->scene, &c->blk, &c->wblk };
     for (Buf *b : bufs) release(c, *b);
     for (auto &b : c->stage_in) release(c, b);
@@ -771,45 +847,14 @@ int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *d, rgrt_geom **out)
     g->ctx = ctx;
     g->desc = *d;
     g->desc.angles = nullptr;
-    const int V = d->n_views, H = d->n_rows, W = d->n_cols;
-    const int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
-    g->desc.tile_w = tw;
-    g->desc.tile_h = th;
-    // host tables: the binary32 rounding of the binary64 geometry
+    const int V = (int)desc_views(d), H = d->n_rows, W = d->n_cols;
     std::vector<float> tab((size_t)9 * V + W + H);
-    const double PI = 3.14159265358979323846;
-    for (int v = 0; v < V; v++) {
-        double eu[3], ev[3], ew[3];
-        if (d->kind == RGRT_GEOM_PET_RING) {
-            double phi = d->angles ? d->angles[v] : (PI * (double)v) / (double)V;
-            double c = cos(phi), s = sin(phi);
-            eu[0] = c; eu[1] = s; eu[2] = 0.0;
-            ew[0] = s; ew[1] = -c; ew[2] = 0.0;
-        } else {
-            double th_ = d->angles[v];
-            double c = cos(th_), s = sin(th_);
-            ew[0] = c; ew[1] = s; ew[2] = 0.0;
-            eu[0] = -s; eu[1] = c; eu[2] = 0.0;
-        }
-        ev[0] = 0.0; ev[1] = 0.0; ev[2] = 1.0;
-        for (int k = 0; k < 3; k++) {
-            tab[9 * v + k] = (float)eu[k];
-            tab[9 * v + 3 + k] = (float)ev[k];
-            tab[9 * v + 6 + k] = (float)ew[k];
-        }
-    }
-    float *ut = tab.data() + 9 * (size_t)V, *vt = ut + W;
-    for (int i = 0; i < W; i++) {
-        double k = (double)i - 0.5 * (double)(W - 1);
-        double u;
-        if (d->kind == RGRT_GEOM_PET_RING)
-            u = d->arc_mode == 0 ? k * ((PI * d->radius) / (double)d->n_crystals)
-                                 : d->radius * sin((k * PI) / (double)d->n_crystals);
-        else
-            u = k * d->pitch_u;
-        ut[i] = (float)u;
-    }
-    for (int j = 0; j < H; j++) vt[j] = (float)(((double)j - 0.5 * (double)(H - 1)) * d->pitch_v);
+    DevGeom &dg = g->dg;
+    geom_tables(d, tab.data(), dg);
+    g->desc.tile_w = dg.tile_w;
+    g->desc.tile_h = dg.tile_h;
+    // the library's views: 3-D PET has one per (ring difference, angle)
+    g->desc.n_views = V;
     g->bytes = sizeof(float) * tab.size();
     int r = dev_alloc(ctx, (void **)&g->d_tables, g->bytes);
     if (r != RGRT_OK) {
@@ -822,21 +867,6 @@ int geometry_set(rgrt_ctx *ctx, const rgrt_geom_desc *d, rgrt_geom **out)
         delete g;
         return fail(RGRT_E_CUDA, "uploading geometry tables: %s", cudaGetErrorString(e));
     }
-    DevGeom &dg = g->dg;
-    dg.kind = d->kind == RGRT_GEOM_CT_CONE ? 1 : 0;
-    dg.pet = d->kind == RGRT_GEOM_PET_RING;
-    dg.n_views = V; dg.n_rows = H; dg.n_cols = W;
-    dg.tile_w = tw; dg.tile_h = th;
-    dg.tiles_x = (W + tw - 1) / tw;
-    dg.tiles_y = (H + th - 1) / th;
-    dg.v0 = 0;
-    if (dg.pet) { dg.stride_view = W; dg.stride_row = (long long)V * W; }
-    else { dg.stride_view = (long long)H * W; dg.stride_row = W; }
-    dg.dso = (float)d->dso;
-    dg.dsd = (float)d->dsd;
-    dg.t_a = (float)d->t_a;
-    dg.t_b = (float)d->t_b;
-    dg.radius2 = (float)(d->radius * d->radius);
     dg.frames = g->d_tables;
     dg.utab = g->d_tables + 9 * (size_t)V;
     dg.vtab = dg.utab + W;
@@ -1010,6 +1040,56 @@ static int run_loss_grad(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *ge
     int nblk = loss_blocks(R);
     TRY(ensure(ctx, ctx->partial, sizeof(double) * (size_t)nblk));
     TRY(ensure(ctx, ctx->loss, sizeof(float) * 4));
+    const bool view_major = !geom->rays && geom->dg.stride_row == geom->dg.n_cols &&
+                            geom->dg.stride_view == (long long)geom->dg.n_rows * geom->dg.n_cols;
+    if (view_major && N > 0) {
+        // the loss is separable over rays, so each view chunk runs forward,
+        // loss and adjoint on one binning (a geometry binned in several chunks
+        // is binned once per step, not once per pass)
+        TRY(ensure(ctx, ctx->loss_acc, sizeof(double)));
+        TRY(ensure(ctx, ctx->grad, sizeof(float4) * GRAD_F4 * (size_t)N));
+        CK(cudaMemsetAsync(ctx->loss_acc.p, 0, sizeof(double), s));
+        CK(cudaMemsetAsync(ctx->grad.p, 0, sizeof(float4) * GRAD_F4 * (size_t)N, s));
+        TRY(build_records(ctx, g, s));
+        Stats *st = nullptr;
+        if (ctx->stats_on) {
+            TRY(ensure(ctx, ctx->stats, sizeof(Stats)));
+            CK(cudaMemsetAsync(ctx->stats.p, 0, sizeof(Stats), s));
+            st = (Stats *)ctx->stats.p;
+        }
+        ctx->last_keys = 0;
+        const int64_t HW = (int64_t)geom->dg.n_rows * geom->dg.n_cols;
+        float *I = (float *)ctx->I.p, *dLdI = (float *)ctx->dLdI.p;
+        const float *y = (const float *)dy;
+        TRY(for_chunks(ctx, g, geom, s, false, [&](int v0, int nv, uint32_t K) -> int {
+            (void)K;
+            DevGeom dg = geom->dg;
+            dg.v0 = v0;
+            {
+                PROF("k_forward");
+                CK(launch_forward(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
+                                  I, st, g->kernel, s));
+            }
+            const int64_t off = (int64_t)v0 * HW, n = (int64_t)nv * HW;
+            {
+                PROF("k_loss");
+                CK(launch_loss(loss, I + off, y + off, n, hp->kappa, hp->poisson_eps,
+                               geom->d_mult ? geom->d_mult + off : nullptr,
+                               geom->d_add ? geom->d_add + off : nullptr, dLdI + off,
+                               (double *)ctx->partial.p, loss_blocks(n), (float *)ctx->loss.p, s,
+                               (double *)ctx->loss_acc.p));
+            }
+            {
+                PROF("k_adjoint");
+                CK(launch_adjoint(dg, nv, g->rec, g->crec, (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p,
+                                  dLdI, (float4 *)ctx->grad.p, g->kernel, s));
+            }
+            return RGRT_OK;
+        }));
+        PROF("k_param_chain");
+        CK(launch_param_chain(g->mu, g->ls, g->q, g->rho, N, (float4 *)ctx->grad.p, gm, gl, gq, gr, s));
+        return RGRT_OK;
+    }
     TRY(run_forward(ctx, g, geom, (float *)ctx->I.p, s));
     {
         PROF("k_loss");

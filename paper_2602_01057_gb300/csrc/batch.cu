@@ -341,9 +341,9 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g, const rg
             delete b;
             return report_error(RGRT_E_INVAL, "batch scan with a null handle or one of another context");
         }
-        if (geom[i]->rays) {
+        if (geom[i]->rays || geom[i]->dg.kind == GM_PET3D) {
             delete b;
-            return report_error(RGRT_E_INVAL, "explicit-ray geometries are not batched");
+            return report_error(RGRT_E_INVAL, "explicit-ray and 3-D PET geometries are not batched");
         }
         if (g[i]->kernel != RGRT_KERNEL_GAUSSIAN) {
             delete b;
@@ -497,7 +497,7 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
         sub.angles = ang.data();
         sub.n_views = max_views;
     }
-    const int64_t R = (int64_t)sub.n_views * sub.n_rows * sub.n_cols;
+    const int64_t R = desc_rays(&sub);
     float *I = nullptr;
     BTRY(ctx_alloc(ctx, (void **)&I, sizeof(float) * (size_t)R));
     cudaStream_t s = nullptr;

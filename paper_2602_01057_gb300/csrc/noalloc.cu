@@ -111,10 +111,10 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
         return report_error(RGRT_E_INVAL, "null parameter array");
     int rc = validate_geometry(d);
     if (rc != RGRT_OK) return rc;
-    const int V = d->n_views, H = d->n_rows, W = d->n_cols;
-    if (V > MAX_VIEWS || H > MAX_SIDE || W > MAX_SIDE)
+    if (desc_views(d) > MAX_VIEWS || d->n_rows > MAX_SIDE || d->n_cols > MAX_SIDE)
         return report_error(RGRT_E_CAPACITY,
                             "project_forward_noalloc handles at most 1024 views of 1024 x 1024 pixels");
+    const int V = (int)desc_views(d), H = d->n_rows, W = d->n_cols;
     if (!on_device(out_I) || (n > 0 && !(on_device(mu3) && on_device(logscale3) && on_device(quat4) &&
                                          on_device(rho))))
         return report_error(RGRT_E_INVAL, "project_forward_noalloc takes device arrays only");
@@ -132,55 +132,8 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
 
     // geometry tables (the same binary32 values geometry_set uploads)
     float tab[9 * MAX_VIEWS + 2 * MAX_SIDE];
-    const double PI = 3.14159265358979323846;
-    for (int v = 0; v < V; v++) {
-        double eu[3], ev[3] = { 0.0, 0.0, 1.0 }, ew[3];
-        if (d->kind == RGRT_GEOM_PET_RING) {
-            double phi = d->angles ? d->angles[v] : (PI * (double)v) / (double)V;
-            double c = cos(phi), sn = sin(phi);
-            eu[0] = c; eu[1] = sn; eu[2] = 0.0;
-            ew[0] = sn; ew[1] = -c; ew[2] = 0.0;
-        } else {
-            double th = d->angles[v];
-            double c = cos(th), sn = sin(th);
-            ew[0] = c; ew[1] = sn; ew[2] = 0.0;
-            eu[0] = -sn; eu[1] = c; eu[2] = 0.0;
-        }
-        for (int k = 0; k < 3; k++) {
-            tab[9 * v + k] = (float)eu[k];
-            tab[9 * v + 3 + k] = (float)ev[k];
-            tab[9 * v + 6 + k] = (float)ew[k];
-        }
-    }
-    float *ut = tab + 9 * V, *vt = ut + W;
-    for (int i = 0; i < W; i++) {
-        double k = (double)i - 0.5 * (double)(W - 1);
-        double u;
-        if (d->kind == RGRT_GEOM_PET_RING)
-            u = d->arc_mode == 0 ? k * ((PI * d->radius) / (double)d->n_crystals)
-                                 : d->radius * sin((k * PI) / (double)d->n_crystals);
-        else
-            u = k * d->pitch_u;
-        ut[i] = (float)u;
-    }
-    for (int j = 0; j < H; j++) vt[j] = (float)(((double)j - 0.5 * (double)(H - 1)) * d->pitch_v);
-
-    const int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
-    DevGeom dg{};
-    dg.kind = d->kind == RGRT_GEOM_CT_CONE ? 1 : 0;
-    dg.pet = d->kind == RGRT_GEOM_PET_RING;
-    dg.n_views = V; dg.n_rows = H; dg.n_cols = W;
-    dg.tile_w = tw; dg.tile_h = th;
-    dg.tiles_x = (W + tw - 1) / tw;
-    dg.tiles_y = (H + th - 1) / th;
-    dg.v0 = 0;
-    if (dg.pet) { dg.stride_view = W; dg.stride_row = (long long)V * W; }
-    else { dg.stride_view = (long long)H * W; dg.stride_row = W; }
-    dg.dso = (float)d->dso;
-    dg.dsd = (float)d->dsd;
-    dg.t_a = (float)d->t_a;
-    dg.t_b = (float)d->t_b;
-    dg.radius2 = (float)(d->radius * d->radius);
+    DevGeom dg;
+    geom_tables(d, tab, dg);
 
     // carve the fixed-size part of the scratch
     Carver cv{ (unsigned char *)base };

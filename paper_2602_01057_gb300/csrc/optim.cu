@@ -118,11 +118,16 @@ __global__ void k_loss(int kind, const float *__restrict__ I, const float *__res
     }
 }
 
-__global__ void k_loss_final(const double *partial, int nblk, float *loss_out)
+// acc (nullable): running total over several launches (ray ranges of one step)
+__global__ void k_loss_final(const double *partial, int nblk, double *acc, float *loss_out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < nblk; k++) t += partial[k];
+        if (acc) {
+            t += *acc;
+            *acc = t;
+        }
         *loss_out = (float)t;
     }
 }
@@ -167,10 +172,10 @@ int loss_blocks(int64_t n)
 
 cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, float kappa,
                         float eps, const float *mult, const float *add, float *dLdI, double *partial,
-                        int nblk, float *loss_out, cudaStream_t s)
+                        int nblk, float *loss_out, cudaStream_t s, double *acc)
 {
     k_loss<<<nblk, LOSS_BS, 0, s>>>(kind, I, y, n, kappa, eps, mult, add, dLdI, partial);
-    k_loss_final<<<1, 32, 0, s>>>(partial, nblk, loss_out);
+    k_loss_final<<<1, 32, 0, s>>>(partial, nblk, acc, loss_out);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -96,11 +96,14 @@ __device__ __forceinline__ void to_frame(const float *X, const float *eu, const 
 }
 
 // gather one record and turn it into its view-space form for frame F
-template <bool CONE, int KER>
+// (3-D PET: kap0, kap1 are the extreme LOR slopes of the tile's columns)
+template <int GM, int KER>
 __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, uint32_t gid,
                                             const float4 *__restrict__ rec,
-                                            const float4 *__restrict__ crec, VRec &out)
+                                            const float4 *__restrict__ crec, VRec &out,
+                                            float kap0 = 0.0f, float kap1 = 0.0f)
 {
+    constexpr bool CONE = GM == GM_CONE;
     const float4 *r = rec + REC_F4 * (size_t)gid;
     float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
     float4 k1 = __ldg(crec + CREC_F4 * (size_t)gid + 1), k2 = __ldg(crec + CREC_F4 * (size_t)gid + 2);
@@ -146,6 +149,37 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         out.c2 = make_float4(Pf[0], 2.0f * Pf[1], Pf[3], rho * Kern<KER>::FAC);
         // both segment ends (source, detector plane) beyond the 8.66-sigma ball
         sat = D >= Kern<KER>::BALL * smax && (g.dsd - D) >= Kern<KER>::BALL * smax;
+    } else if (GM == GM_PET3D) {
+        // LOR through (u, z) at w = 0 with direction d~ = e_w + kappa e_v:
+        // with du = u - mu_u and v~ = z - mu_v + kappa mu_w (the LOR's height
+        // at depth mu_w, relative to mu), c = d~ x delta = (-v~, du, -kappa du),
+        //   Q = du^2 (S'_vv - 2 kappa S'_vw + kappa^2 S'_ww)
+        //     + 2 du v~ (kappa S'_uw - S'_uv) + v~^2 S'_uu,
+        //   A = d~^T P' d~ = P'_ww (1 + kappa (2 P'_vw + kappa P'_vv) / P'_ww),
+        // and the integral along the unit ray is |d~| rho sqrt(2 pi / A)
+        // exp(-Q / 2A); the coefficients carry the 1/P'_ww.
+        float hu = sqrtf(Kern<KER>::SKIP * quad_form(Sg, eu, eu));
+        ulo = mu_u - hu; uhi = mu_u + hu;
+        // heights z whose LORs can meet the box ellipsoid (the bounds at the
+        // two extreme slopes span those of every slope between them)
+        const float svv = quad_form(Sg, ev, ev), svw = quad_form(Sg, ev, ew), sww = quad_form(Sg, ew, ew);
+        vlo = INFINITY; vhi = -INFINITY;
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const float kap = e ? kap1 : kap0;
+            const float zc = mu_v - kap * mu_w;
+            const float half = sqrtf(fmaxf(Kern<KER>::SKIP * (svv - 2.0f * kap * svw + kap * kap * sww), 0.0f));
+            vlo = fminf(vlo, zc - half);
+            vhi = fmaxf(vhi, zc + half);
+        }
+        const float iP = 1.0f / Pf[5];
+        const float k = Kern<KER>::QSCALE * iP;
+        out.c0 = make_float4(mu_u, mu_v, mu_w, k * Sf[0]);
+        out.c1 = make_float4(k * Sf[3], -2.0f * k * Sf[4], k * Sf[5], -2.0f * k * Sf[1]);
+        out.c2 = make_float4(2.0f * k * Sf[2], 2.0f * Pf[4] * iP, Pf[3] * iP, rho * Kern<KER>::FAC * sqrtf(iP));
+        // the LOR ends on the ring: beyond the ball if the ball is inside it
+        const float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
+        sat = rxy + Kern<KER>::BALL * smax <= sqrtf(g.radius2);
     } else {
         float hu = sqrtf(Kern<KER>::SKIP * quad_form(Sg, eu, eu));
         float hv = sqrtf(Kern<KER>::SKIP * quad_form(Sg, ev, ev));
@@ -171,11 +205,20 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
 }
 
 // ray of detector pixel (u, v) in view frame F (FP32), for the general path
-template <bool CONE>
-__device__ __forceinline__ Ray make_ray(const DevGeom &g, const float *F, float u, float v)
+// (3-D PET: v is the LOR's mid-height, kap its slope dz/dw)
+template <int GM>
+__device__ __forceinline__ Ray make_ray(const DevGeom &g, const float *F, float u, float v, float kap = 0.0f)
 {
     float op0, op1, op2, dp0, dp1, dp2, ta, tb;
-    if (CONE) {
+    if (GM == GM_PET3D) {
+        // o' = (u, v, 0), d' = (0, kappa, 1)/L, L = sqrt(1 + kappa^2); the LOR
+        // runs over w in [-h, h], h = sqrt(R^2 - u^2), i.e. t = w L
+        const float L = sqrtf(1.0f + kap * kap), iL = 1.0f / L;
+        const float h = sqrtf(fmaxf(g.radius2 - u * u, 0.0f));
+        op0 = u; op1 = v; op2 = 0.0f;
+        dp0 = 0.0f; dp1 = kap * iL; dp2 = iL;
+        ta = -h * L; tb = h * L;
+    } else if (GM == GM_CONE) {
         // d' = (u, v, dsd)/L;  o' = closest point to the origin on the ray,
         // o' = dso/L^2 (dsd u, dsd v, -(u^2+v^2)) (no cancellation);
         // segment from the source (t_a) to the pixel (t_b), measured from o'
@@ -211,11 +254,40 @@ __device__ __forceinline__ Ray make_ray(const DevGeom &g, const float *F, float 
 
 struct TileCtx {
     int vl, tx, ty, view, col, row;
-    bool valid;
+    bool valid;                        // the thread's pixel is on the detector
+    bool live;                         // ... and has a ray (3-D PET: a ring pair)
     float wu_lo, wu_hi, wv_lo, wv_hi;  // detector box of this warp's 8 x 4 rays
+    float zoff, dz;                    // 3-D PET: mid-height offset of the rows, axial LOR rise
+    float kap0, kap1;                  // 3-D PET: LOR slopes at the tile's extreme columns
     long long out_idx;
 };
 
+// 3-D PET: LOR slope dz/dw at radial position u (dz: axial rise over the chord)
+__device__ __forceinline__ float pet3d_slope(const DevGeom &g, float dz, float u)
+{
+    return 0.5f * dz / sqrtf(fmaxf(g.radius2 - u * u, 1e-30f));
+}
+
+// 3-D PET view: (offset of the row heights, axial rise, rows with a ring pair)
+__device__ __forceinline__ void pet3d_view(const DevGeom &g, int view, float &zoff, float &dz, int &rows)
+{
+    const int delta = pet3d_delta(g, view), ad = abs(delta);
+    zoff = 0.5f * (float)ad * g.ring_pitch;
+    dz = (float)delta * g.ring_pitch;
+    rows = g.n_rows - ad;
+}
+
+// 3-D PET: LOR slopes at the extreme |u| of columns c0..c1
+__device__ __forceinline__ void pet3d_slopes(const DevGeom &g, float dz, int c0, int c1, float &k0, float &k1)
+{
+    const float ua = __ldg(g.utab + c0), ub = __ldg(g.utab + c1);
+    const float amin = (ua <= 0.0f && ub >= 0.0f) ? 0.0f : fminf(fabsf(ua), fabsf(ub));
+    const float amax = fmaxf(fabsf(ua), fabsf(ub));
+    k0 = pet3d_slope(g, dz, amin);
+    k1 = pet3d_slope(g, dz, amax);
+}
+
+template <int GM>
 __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
 {
     TileCtx c;
@@ -232,10 +304,18 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
     c.col = c0 + (lane & 7);
     c.row = r0 + (lane >> 3);
     c.valid = c.col < g.n_cols && c.row < g.n_rows;
-    if (c0 < g.n_cols && r0 < g.n_rows) {
-        int c1 = min(c0 + 7, g.n_cols - 1), r1 = min(r0 + 3, g.n_rows - 1);
+    int rows = g.n_rows;
+    c.zoff = c.dz = c.kap0 = c.kap1 = 0.0f;
+    if (GM == GM_PET3D) {
+        pet3d_view(g, c.view, c.zoff, c.dz, rows);
+        const int tc0 = c.tx * g.tile_w;
+        pet3d_slopes(g, c.dz, tc0, min(tc0 + g.tile_w - 1, g.n_cols - 1), c.kap0, c.kap1);
+    }
+    c.live = c.valid && c.row < rows;
+    if (c0 < g.n_cols && r0 < rows) {
+        int c1 = min(c0 + 7, g.n_cols - 1), r1 = min(r0 + 3, rows - 1);
         c.wu_lo = __ldg(g.utab + c0); c.wu_hi = __ldg(g.utab + c1);
-        c.wv_lo = __ldg(g.vtab + r0); c.wv_hi = __ldg(g.vtab + r1);
+        c.wv_lo = __ldg(g.vtab + r0) + c.zoff; c.wv_hi = __ldg(g.vtab + r1) + c.zoff;
     } else {
         c.wu_lo = INFINITY; c.wu_hi = -INFINITY; c.wv_lo = INFINITY; c.wv_hi = -INFINITY;
     }
@@ -266,14 +346,15 @@ struct ChunkLists {
     uint8_t gen[8][CH];
 };
 
-template <bool CONE, int KER>
+template <int GM, int KER>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
                                            uint32_t base, uint32_t stride, int cnt,
                                            const float4 *rec, const float4 *crec, VRec *sv,
-                                           const float4 *wbox, int nw, uint32_t *msk)
+                                           const float4 *wbox, int nw, uint32_t *msk,
+                                           float kap0, float kap1)
 {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        prep_record<CONE, KER>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i]);
+        prep_record<GM, KER>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i], kap0, kap1);
         const float4 bb = sv[i].bb;
         uint32_t m = 0;
         for (int w = 0; w < nw; w++) {
@@ -313,16 +394,32 @@ __device__ __forceinline__ void warp_box(const TileCtx &c, float4 *wbox)
     if ((threadIdx.x & 31) == 0) wbox[threadIdx.x >> 5] = make_float4(c.wu_lo, c.wu_hi, c.wv_lo, c.wv_hi);
 }
 
-// view-space value of one pair (without the |d~| factor of cone beam);
-// returns arg = QSCALE m (Gaussian: -m log2(e)/2; Epanechnikov: -m/kappa^2)
-template <bool CONE, int KER>
-__device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float &arg)
+// view-space value of one pair (without the |d~| factor of cone beam and
+// 3-D PET); returns arg = QSCALE m (Gaussian: -m log2(e)/2; Epanechnikov:
+// -m/kappa^2).  kap: the ray's slope (3-D PET).
+template <int GM, int KER>
+__device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float kap, float &arg)
 {
     const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
+    float rA = 1.0f;
+    if (GM == GM_PET3D) {
+        const float du = u - c0.x, vt = fmaf(kap, c0.z, v - c0.y);
+        const float muu = fmaf(fmaf(c1.z, kap, c1.y), kap, c1.x);
+        const float muv2 = fmaf(c2.x, kap, c1.w);
+        const float q = du * (muu * du + muv2 * vt) + c0.w * vt * vt;
+        const float An = fmaf(fmaf(c2.z, kap, c2.y), kap, 1.0f);
+        rA = rsqrt_approx(An);
+        arg = q * (rA * rA);
+        if (KER == 1) {
+            const float c = 1.0f + arg;
+            const float pc = c > 0.0f ? c * sqrt_approx(c) : 0.0f;
+            return c2.w * rA * pc;
+        }
+        return c2.w * rA * ex2_approx(arg);
+    }
     const float du = u - c0.x, dv = v - c0.y;
     const float q = du * (c0.z * du + c0.w * dv) + c1.x * dv * dv;
-    float rA = 1.0f;
-    if (CONE) {
+    if (GM == GM_CONE) {
         const float A = c1.y + du * (c1.z + c2.x * du + c2.y * dv) + dv * (c1.w + c2.z * dv);
         rA = rsqrt_approx(A);
         arg = q * (rA * rA);
@@ -345,7 +442,7 @@ __device__ __forceinline__ bool vs_keep(float arg)
 }
 
 // forward integration of tile `tile` of geometry g (one ray per thread)
-template <bool CONE, bool STATS, int KER>
+template <int GM, bool STATS, int KER>
 __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -358,7 +455,8 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     __shared__ uint32_t msk_buf[NBUF][CH];
     __shared__ float4 wbox[8];
     __shared__ float Fs[9];
-    const TileCtx c = tile_ctx(g, tile);
+    constexpr bool CONE = GM == GM_CONE;
+    const TileCtx c = tile_ctx<GM>(g, tile);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
     warp_box(c, wbox);
@@ -367,8 +465,10 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
 #pragma unroll
     for (int i = 0; i < 9; i++) F[i] = Fs[i];
     const float u = __ldg(g.utab + min(c.col, g.n_cols - 1));
-    const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1));
-    const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd) : 1.0f;
+    const float v = __ldg(g.vtab + min(c.row, g.n_rows - 1)) + c.zoff;
+    const float kap = GM == GM_PET3D ? pet3d_slope(g, c.dz, u) : 0.0f;
+    const float L = CONE ? sqrtf(u * u + v * v + g.dsd * g.dsd)
+                  : GM == GM_PET3D ? sqrtf(1.0f + kap * kap) : 1.0f;
     const uint2 rg = ranges[tile];
     float acc_vs = 0.0f, acc_gen = 0.0f;
     unsigned n_eval = 0, n_kept = 0;
@@ -381,7 +481,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
         VRec *sv = sv_buf[ch % NBUF];
         uint32_t *msk = msk_buf[ch % NBUF];
-        prep_chunk<CONE, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk);
+        prep_chunk<GM, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk, c.kap0, c.kap1);
         // every thread has prepared this chunk and (with two buffers) left the
         // previous one, whose buffer the next chunk's preparation reuses
         __syncthreads();
@@ -391,20 +491,20 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         for (; k + 1 < nvs; k += 2) {
             const int j0 = lists.vs[w][k], j1 = lists.vs[w][k + 1];
             float a0, a1;
-            const float v0 = vs_value<CONE, KER>(sv[j0], u, v, a0);
-            const float v1 = vs_value<CONE, KER>(sv[j1], u, v, a1);
+            const float v0 = vs_value<GM, KER>(sv[j0], u, v, kap, a0);
+            const float v1 = vs_value<GM, KER>(sv[j1], u, v, kap, a1);
             acc_vs += vs_keep<KER>(a0) ? v0 : 0.0f;
             acc_vs += vs_keep<KER>(a1) ? v1 : 0.0f;
             if (STATS) n_kept += vs_keep<KER>(a0) + vs_keep<KER>(a1);
         }
         if (k < nvs) {
             float a0;
-            const float v0 = vs_value<CONE, KER>(sv[lists.vs[w][k]], u, v, a0);
+            const float v0 = vs_value<GM, KER>(sv[lists.vs[w][k]], u, v, kap, a0);
             acc_vs += vs_keep<KER>(a0) ? v0 : 0.0f;
             if (STATS) n_kept += vs_keep<KER>(a0);
         }
         if (ngen > 0) {
-            const Ray ray = make_ray<CONE>(g, F, u, v);
+            const Ray ray = make_ray<GM>(g, F, u, v, kap);
             for (int k2 = 0; k2 < ngen; k2++) {
                 const VRec &r = sv[lists.gen[w][k2]];
                 PairGeo q;
@@ -417,9 +517,9 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         if (STATS) n_eval += nvs + ngen;
         if (NBUF == 1) __syncthreads();
     }
-    if (c.valid) out[c.out_idx] = acc_gen + L * acc_vs;
+    if (c.valid) out[c.out_idx] = c.live ? acc_gen + L * acc_vs : 0.0f;
     if (STATS) {
-        unsigned long long e = c.valid ? n_eval : 0, kk = c.valid ? n_kept : 0;
+        unsigned long long e = c.live ? n_eval : 0, kk = c.live ? n_kept : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -432,14 +532,14 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     }
 }
 
-template <bool CONE, bool STATS, int KER>
+template <int GM, bool STATS, int KER>
 __global__ void __launch_bounds__(256, 4) k_forward(DevGeom g, const float4 *__restrict__ rec,
                                                     const float4 *__restrict__ crec,
                                                     const uint32_t *__restrict__ gids,
                                                     const uint2 *__restrict__ ranges,
                                                     float *__restrict__ out, Stats *stats)
 {
-    forward_tile<CONE, STATS, KER>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
+    forward_tile<GM, STATS, KER>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
 }
 
 // symmetric 3x3 (packed 00 01 02 11 12 22) back to world: G = E G' E^T
@@ -479,10 +579,11 @@ __device__ __forceinline__ void cross_acc(const float *a, const float *b, float 
 //   dL/dmu' = -2 sum dL/dQ (S' c) x d~      (Q = c^T S' c, c = d~ x (S - mu'))
 //   dL/drho = sqrt(2 pi) Sw
 // out16 = (dmu[3], drho, G_P[6], G_S[6]) in world coordinates.
-template <bool CONE, int KER>
+template <int GM, int KER>
 __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, const float4 *rec,
                                            uint32_t gid, const float *s, float *out16)
 {
+    constexpr bool CONE = GM == GM_CONE;
     const float4 *r = rec + REC_F4 * (size_t)gid;
     const float4 r0 = __ldg(r), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
     const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
@@ -560,6 +661,61 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
     from_frame(GSf, eu, ev, ew, out16 + 10);
 }
 
+// Gradient of one Gaussian from its 3-D PET view-space moments, summed over
+// the tile's LORs (d~ = e_w + kappa e_v, c = d~ x (o - mu') = (-v~, du,
+// -kappa du), see prep_record), in the normalised variables of the record
+// (A_n = A / P'_ww, Q_n = Q / P'_ww; h = -dL/dQ_n / alpha', gA = dL/dA_n /
+// alpha', w = dL/dI |d~| A_n^-1/2 K(m), alpha' = alpha / sqrt(P'_ww)):
+//   s = [h v~^2, h v~ du, h kappa v~ du, h du^2, h kappa du^2, h kappa^2 du^2,
+//        h v~, h v~ kappa, h du, h du kappa, h du kappa^2,
+//        gA, gA kappa, gA kappa^2, w]
+// With dL/dQ = -alpha P'_ww^-3/2 h and dL/dA = alpha P'_ww^-3/2 gA:
+//   dL/dS'  = sum dL/dQ c c^T,   dL/dP' = sum dL/dA d~ d~^T,
+//   dL/dmu' = -2 sum dL/dQ (S'c) x d~,  dL/drho = FAC P'_ww^-1/2 sum w.
+template <int KER>
+__device__ __forceinline__ void pet3d_chain(const float *F, const float4 *rec, uint32_t gid,
+                                            const float *s, float *out16)
+{
+    const float4 *r = rec + REC_F4 * (size_t)gid;
+    const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
+    const float P[6] = { r1.x, r1.y, r1.z, r1.w, r2.x, r2.y };
+    const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
+    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
+    float Sf[6];
+    to_frame(Sh, eu, ev, ew, Sf);
+    const float ipw = 1.0f / quad_form(P, ew, ew);
+    const float aw = sqrtf(ipw);
+    const float ah = r0.w * Kern<KER>::FAC * aw * ipw;
+    float GSf[6], GPf[6];
+    GSf[0] = -ah * s[0];   // uu: c_u c_u = v~^2
+    GSf[1] = ah * s[1];    // uv: -v~ du
+    GSf[2] = -ah * s[2];   // uw: kappa v~ du
+    GSf[3] = -ah * s[3];   // vv: du^2
+    GSf[4] = ah * s[4];    // vw: -kappa du^2
+    GSf[5] = -ah * s[5];   // ww: kappa^2 du^2
+    GPf[0] = GPf[1] = GPf[2] = 0.0f;
+    GPf[3] = ah * s[13];   // vv: kappa^2
+    GPf[4] = ah * s[12];   // vw: kappa
+    GPf[5] = ah * s[11];   // ww: 1
+    // columns of S' and (S' c) x d~ =
+    //   -v~ (S'e_u x e_w) - v~ kappa (S'e_u x e_v) + du (S'e_v x e_w)
+    //   + du kappa (S'e_v x e_v - S'e_w x e_w) - du kappa^2 (S'e_w x e_v)
+    // with x x e_u = (0, x_w, -x_v), x x e_v = (-x_w, 0, x_u), x x e_w = (x_v, -x_u, 0)
+    const float cu[3] = { Sf[0], Sf[1], Sf[2] }, cv[3] = { Sf[1], Sf[3], Sf[4] }, cw[3] = { Sf[2], Sf[4], Sf[5] };
+    const float M0 = s[6], M1 = s[7], M2 = s[8], M3 = s[9], M4 = s[10];
+    float T[3];
+    T[0] = -M0 * cu[1] - M1 * (-cu[2]) + M2 * cv[1] + M3 * (-cv[2] - cw[1]) - M4 * (-cw[2]);
+    T[1] = -M0 * (-cu[0]) + M2 * (-cv[0]) + M3 * cw[0];
+    T[2] = -M1 * cu[0] + M3 * cv[0] - M4 * cw[0];
+    const float dmuf[3] = { 2.0f * ah * T[0], 2.0f * ah * T[1], 2.0f * ah * T[2] };
+    out16[0] = dmuf[0] * eu[0] + dmuf[1] * ev[0] + dmuf[2] * ew[0];
+    out16[1] = dmuf[0] * eu[1] + dmuf[1] * ev[1] + dmuf[2] * ew[1];
+    out16[2] = dmuf[0] * eu[2] + dmuf[1] * ev[2] + dmuf[2] * ew[2];
+    out16[3] = Kern<KER>::FAC * aw * s[14];
+    from_frame(GPf, eu, ev, ew, out16 + 4);
+    from_frame(GSf, eu, ev, ew, out16 + 10);
+}
+
 // Adjoint, one Gaussian per thread.  A CTA takes a tile: it stages the
 // tile's dL/dI (times |d~| for cone beam) and pixel coordinates in shared
 // memory, then every thread walks the tile's rays for one Gaussian of the
@@ -570,8 +726,9 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
 // position, so the 32 Gaussians of a warp sit close together: rows and
 // 8-column groups that none of their boxes touches are skipped.  Within a row
 // the Q and A quadratics are evaluated in Horner form in du with the dv terms
-// hoisted.
-template <bool CONE, int TW, int KER>
+// hoisted.  For 3-D PET the LOR slope kappa varies from column to column:
+// the moments carry its powers (pet3d_chain).
+template <int GM, int TW, int KER>
 __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -580,8 +737,10 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              const float *__restrict__ dLdI,
                                              float4 *__restrict__ grad)
 {
+    constexpr bool CONE = GM == GM_CONE, P3 = GM == GM_PET3D;
     __shared__ float sgl[256];   // dL/dI |d~| of the tile's rays, row-major (0 outside the detector)
     __shared__ float su[32], svr[32];
+    __shared__ float skap[P3 ? 32 : 1];   // 3-D PET: LOR slope of every column
     __shared__ float Fs[9];
     const int T = g.tiles_x * g.tiles_y;
     const int vl = (int)(tile / (uint32_t)T);
@@ -590,18 +749,31 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
     const int view = g.v0 + vl;
     const int TH = g.tile_h;
     const int c0 = tx * TW, r0 = ty * TH;
+    float zoff = 0.0f, dz = 0.0f, kap0 = 0.0f, kap1 = 0.0f;
+    int rows = g.n_rows;
+    if (P3) {
+        pet3d_view(g, view, zoff, dz, rows);
+        pet3d_slopes(g, dz, c0, min(c0 + TW - 1, g.n_cols - 1), kap0, kap1);
+    }
     if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)view + threadIdx.x);
-    if (threadIdx.x < TW) su[threadIdx.x] = __ldg(g.utab + min(c0 + (int)threadIdx.x, g.n_cols - 1));
-    if (threadIdx.x < TH) svr[threadIdx.x] = __ldg(g.vtab + min(r0 + (int)threadIdx.x, g.n_rows - 1));
+    if (threadIdx.x < TW) {
+        su[threadIdx.x] = __ldg(g.utab + min(c0 + (int)threadIdx.x, g.n_cols - 1));
+        if (P3) skap[threadIdx.x] = pet3d_slope(g, dz, su[threadIdx.x]);
+    }
+    if (threadIdx.x < TH) svr[threadIdx.x] = __ldg(g.vtab + min(r0 + (int)threadIdx.x, g.n_rows - 1)) + zoff;
     for (int r = threadIdx.x; r < TW * TH; r += blockDim.x) {
         const int col = c0 + r % TW, row = r0 + r / TW;
         float gl = 0.0f;
-        if (col < g.n_cols && row < g.n_rows) {
+        if (col < g.n_cols && row < rows) {
             const long long idx = (long long)view * g.stride_view + (long long)row * g.stride_row + col;
             gl = __ldg(dLdI + idx);
             if (CONE) {
                 const float u = __ldg(g.utab + col), v = __ldg(g.vtab + row);
                 gl *= sqrtf(u * u + v * v + g.dsd * g.dsd);
+            }
+            if (P3) {
+                const float kap = pet3d_slope(g, dz, __ldg(g.utab + col));
+                gl *= sqrtf(1.0f + kap * kap);
             }
         }
         sgl[r] = gl;
@@ -621,7 +793,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
         uint32_t gid = 0;
         if (active) {
             gid = __ldg(gids + k);
-            prep_record<CONE, KER>(g, F, gid, rec, crec, r);
+            prep_record<GM, KER>(g, F, gid, rec, crec, r, kap0, kap1);
         } else {
             r.bb = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
             r.g2 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
@@ -647,7 +819,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
         for (int c8 = 0; c8 < TW / 8; c8++) groups |= (uint32_t)(ilo <= 8 * c8 + 7 && ihi >= 8 * c8) << c8;
         float o[16];
         bool any = false;
-        if (__any_sync(0xffffffffu, active && vs)) {
+        if (!P3 && __any_sync(0xffffffffu, active && vs)) {
             // view-space moments (see view_chain for their meaning)
             const float u0 = r.c0.x, v0 = r.c0.y, kMuu = r.c0.z, kMuv2 = r.c0.w, kMvv = r.c1.x;
             float s[NV_CONE];
@@ -731,7 +903,69 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 if (!CONE) s[6] = s[11];   // parallel layout: [SQ.. (5), SA, Sw]
 #pragma unroll
                 for (int q = 0; q < NV_CONE; q++) any |= s[q] != 0.0f;
-                if (any) view_chain<CONE, KER>(g, F, rec, gid, s, o);
+                if (any) view_chain<GM, KER>(g, F, rec, gid, s, o);
+            }
+        }
+        if (P3 && __any_sync(0xffffffffu, active && vs)) {
+            const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
+            float s[15];
+#pragma unroll
+            for (int q = 0; q < 15; q++) s[q] = 0.0f;
+            for (int j = 0; j < TH; j++) {
+                const bool rowin = active && vs && j >= jlo && j <= jhi;
+                const uint32_t need = __reduce_or_sync(0xffffffffu, rowin ? groups : 0u);
+                if (need == 0u || !rowin) continue;
+                const float dv = svr[j] - c0.y;
+                const float *gl_row = sgl + j * TW;
+#pragma unroll
+                for (int c8 = 0; c8 < TW / 8; c8++) {
+                if (!((need >> c8) & 1u)) continue;
+#pragma unroll
+                for (int i = 8 * c8; i < 8 * c8 + 8; i++) {
+                    const float du = su[i] - c0.x, kap = skap[i];
+                    const float vt = fmaf(kap, c0.z, dv);
+                    const float muu = fmaf(fmaf(c1.z, kap, c1.y), kap, c1.x);
+                    const float muv2 = fmaf(c2.x, kap, c1.w);
+                    const float qv = du * (muu * du + muv2 * vt) + c0.w * vt * vt;
+                    const float rA = rsqrt_approx(fmaf(fmaf(c2.z, kap, c2.y), kap, 1.0f));
+                    const float iA = rA * rA;
+                    const float arg = qv * iA;
+                    float wv, h, gA;
+                    if (KER == 1) {
+                        const float c = 1.0f + arg;
+                        const float sc = c > 0.0f ? sqrt_approx(c) : 0.0f;
+                        const float t = gl_row[i] * rA * sc;
+                        wv = t * c;
+                        h = (1.5f / Kern<1>::KAPPA2) * t * iA;
+                        gA = t * iA * (1.5f - 2.0f * c);
+                    } else {
+                        wv = arg >= CUT_ARG ? gl_row[i] * rA * ex2_approx(arg) : 0.0f;
+                        h = 0.5f * wv * iA;
+                        gA = h * (arg * M_PER_ARG - 1.0f);
+                    }
+                    const float hd = h * du, hv = h * vt, hdk = hd * kap, hdkk = hdk * kap, gk = gA * kap;
+                    s[0] = fmaf(hv, vt, s[0]);
+                    s[1] = fmaf(hv, du, s[1]);
+                    s[2] = fmaf(hdk, vt, s[2]);
+                    s[3] = fmaf(hd, du, s[3]);
+                    s[4] = fmaf(hdk, du, s[4]);
+                    s[5] = fmaf(hdkk, du, s[5]);
+                    s[6] += hv;
+                    s[7] = fmaf(hv, kap, s[7]);
+                    s[8] += hd;
+                    s[9] += hdk;
+                    s[10] += hdkk;
+                    s[11] += gA;
+                    s[12] += gk;
+                    s[13] = fmaf(gk, kap, s[13]);
+                    s[14] += wv;
+                }
+                }
+            }
+            if (active && vs) {
+#pragma unroll
+                for (int q = 0; q < 15; q++) any |= s[q] != 0.0f;
+                if (any) pet3d_chain<KER>(F, rec, gid, s, o);
             }
         }
         if (__any_sync(0xffffffffu, active && !vs)) {
@@ -745,12 +979,13 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                         const float gw0 = sgl[j * TW + i];
                         if (gw0 == 0.0f) continue;
                         const float u = su[i];
-                        const Ray ray = make_ray<CONE>(g, F, u, vj);
+                        const Ray ray = make_ray<GM>(g, F, u, vj, P3 ? skap[i] : 0.0f);
                         PairGeo q;
                         pair_geo(ray, r, q);
                         if (!(q.m <= PAIR_CUT2)) continue;
                         // sgl holds dL/dI |d~|; the general form wants dL/dI
-                        const float gw = CONE ? gw0 * rsqrtf(u * u + vj * vj + g.dsd * g.dsd) : gw0;
+                        const float gw = CONE ? gw0 * rsqrtf(u * u + vj * vj + g.dsd * g.dsd)
+                                       : P3 ? gw0 * rsqrtf(1.0f + skap[i] * skap[i]) : gw0;
                         float pv[NG];
                         general_grad<KER>(ray, q, r.g0.w, gw, pv);
 #pragma unroll
@@ -776,7 +1011,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
     }
 }
 
-template <bool CONE, int TW, int KER>
+template <int GM, int TW, int KER>
 __global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__restrict__ rec,
                                                  const float4 *__restrict__ crec,
                                                  const uint32_t *__restrict__ gids,
@@ -784,7 +1019,7 @@ __global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__r
                                                  const float *__restrict__ dLdI,
                                                  float4 *__restrict__ grad)
 {
-    adjoint_tile<CONE, TW, KER>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
+    adjoint_tile<GM, TW, KER>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
 }
 
 // Persistent forms over a batch of scans: every CTA takes (scan, tile) work
@@ -821,7 +1056,7 @@ __global__ void __launch_bounds__(256, 3) k_forward_persistent(const ScanDesc *_
     int scan;
     while (next_item(d, nscan, total, queue, item, scan)) {
         const ScanDesc &sd = d[scan];
-        forward_tile<CONE, false, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+        forward_tile<CONE ? GM_CONE : GM_PARALLEL, false, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
                                   sd.out, nullptr);
     }
 }
@@ -834,7 +1069,7 @@ __global__ void __launch_bounds__(ADJ_BS) k_adjoint_persistent(const ScanDesc *_
     int scan;
     while (next_item(d, nscan, total, queue, item, scan)) {
         const ScanDesc &sd = d[scan];
-        adjoint_tile<CONE, TW, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
+        adjoint_tile<CONE ? GM_CONE : GM_PARALLEL, TW, 0>(sd.g, item - sd.item_begin, sd.rec, sd.crec, sd.gids, sd.ranges,
                                sd.dLdI, sd.grad);
     }
 }
@@ -901,14 +1136,15 @@ cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const fl
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
     int bs = g.tile_w * g.tile_h;
-#define RGRT_FWD(C, S, K) k_forward<C, S, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats)
-    if (ker == 1) {
-        if (g.kind == 1) { if (stats) RGRT_FWD(true, true, 1); else RGRT_FWD(true, false, 1); }
-        else { if (stats) RGRT_FWD(false, true, 1); else RGRT_FWD(false, false, 1); }
-    } else {
-        if (g.kind == 1) { if (stats) RGRT_FWD(true, true, 0); else RGRT_FWD(true, false, 0); }
-        else { if (stats) RGRT_FWD(false, true, 0); else RGRT_FWD(false, false, 0); }
-    }
+#define RGRT_FWD(M, S, K) k_forward<M, S, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats)
+#define RGRT_FWD_K(M, K) { if (stats) RGRT_FWD(M, true, K); else RGRT_FWD(M, false, K); }
+#define RGRT_FWD_M(K)                                  \
+    if (g.kind == GM_CONE) RGRT_FWD_K(GM_CONE, K)      \
+    else if (g.kind == GM_PET3D) RGRT_FWD_K(GM_PET3D, K) \
+    else RGRT_FWD_K(GM_PARALLEL, K)
+    if (ker == 1) { RGRT_FWD_M(1) } else { RGRT_FWD_M(0) }
+#undef RGRT_FWD_M
+#undef RGRT_FWD_K
 #undef RGRT_FWD
     count_launches(1);
     return cudaGetLastError();
@@ -921,19 +1157,20 @@ cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const fl
     unsigned nt = (unsigned)nv * g.tiles_x * g.tiles_y;
     if (nt == 0) return cudaSuccess;
     const int bs = ADJ_BS;
-#define RGRT_ADJ(CONE, TW, K) k_adjoint<CONE, TW, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
-#define RGRT_ADJ_K(K)                                         \
-    if (g.kind == 1) {                                        \
-        if (g.tile_w == 8) RGRT_ADJ(true, 8, K);              \
-        else if (g.tile_w == 16) RGRT_ADJ(true, 16, K);       \
-        else RGRT_ADJ(true, 32, K);                           \
-    } else {                                                  \
-        if (g.tile_w == 8) RGRT_ADJ(false, 8, K);             \
-        else if (g.tile_w == 16) RGRT_ADJ(false, 16, K);      \
-        else RGRT_ADJ(false, 32, K);                          \
+#define RGRT_ADJ(M, TW, K) k_adjoint<M, TW, K><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad)
+#define RGRT_ADJ_W(M, K)                                      \
+    {                                                         \
+        if (g.tile_w == 8) RGRT_ADJ(M, 8, K);                 \
+        else if (g.tile_w == 16) RGRT_ADJ(M, 16, K);          \
+        else RGRT_ADJ(M, 32, K);                              \
     }
+#define RGRT_ADJ_K(K)                                         \
+    if (g.kind == GM_CONE) RGRT_ADJ_W(GM_CONE, K)             \
+    else if (g.kind == GM_PET3D) RGRT_ADJ_W(GM_PET3D, K)      \
+    else RGRT_ADJ_W(GM_PARALLEL, K)
     if (ker == 1) { RGRT_ADJ_K(1) } else { RGRT_ADJ_K(0) }
 #undef RGRT_ADJ_K
+#undef RGRT_ADJ_W
 #undef RGRT_ADJ
     count_launches(1);
     return cudaGetLastError();

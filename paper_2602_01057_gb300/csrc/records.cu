@@ -183,7 +183,48 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
         ulo = S(mu_u, hu); uhi = A(mu_u, hu); vlo = S(mu_v, hv); vhi = A(mu_v, hv);
     }
     int i0 = lower_idx(g.utab, g.n_cols, ulo), i1 = upper_idx(g.utab, g.n_cols, uhi);
-    int j0 = lower_idx(g.vtab, g.n_rows, vlo), j1 = upper_idx(g.vtab, g.n_rows, vhi);
+    int j0, j1;
+    if (g.kind == GM_PET3D) {
+        // 3-D PET (not part of the FP32 culling specification, which covers
+        // the other kinds): the LOR of radial position s and mid-height z has
+        // direction e_w + kappa e_v, kappa = dz / (2 sqrt(R^2 - s^2)), and
+        // a . x = z along it for a = e_v - kappa e_w, so it can meet the
+        // K-sigma ellipsoid only if z lies in mu.a +- sqrt(K^2 a^T Sigma a).
+        // Both bounds are convex / concave in kappa, so over the columns
+        // i0..i1 the union of these intervals is spanned by their values at
+        // the two extreme slopes.
+        j0 = 0;
+        j1 = -1;
+        if (i0 <= i1) {
+            const int delta = pet3d_delta(g, g.v0 + vl), ad = abs(delta);
+            const float dz = (float)delta * g.ring_pitch, zoff = 0.5f * (float)ad * g.ring_pitch;
+            const float ua = __ldg(g.utab + i0), ub = __ldg(g.utab + i1);
+            const float amin = (ua <= 0.0f && ub >= 0.0f) ? 0.0f : fminf(fabsf(ua), fabsf(ub));
+            const float amax = fmaxf(fabsf(ua), fabsf(ub));
+            const float h2a = g.radius2 - amin * amin, h2b = g.radius2 - amax * amax;
+            const int last = g.n_rows - 1 - ad;
+            if (!(h2b > 0.0f)) {
+                j1 = last;
+            } else {
+                const float mu_w = dot_spec(m, ew);
+                const float svv = form_spec(Sg, ev, ev), svw = form_spec(Sg, ev, ew), sww = form_spec(Sg, ew, ew);
+                float zlo = INFINITY, zhi = -INFINITY;
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const float kap = 0.5f * dz / sqrtf(e ? h2b : h2a);
+                    const float zc = mu_v - kap * mu_w;
+                    const float half = sqrtf(fmaxf(K2 * (svv - 2.0f * kap * svw + kap * kap * sww), 0.0f));
+                    zlo = fminf(zlo, zc - half);
+                    zhi = fmaxf(zhi, zc + half);
+                }
+                j0 = lower_idx(g.vtab, g.n_rows, zlo - zoff);
+                j1 = min(upper_idx(g.vtab, g.n_rows, zhi - zoff), last);
+            }
+        }
+    } else {
+        j0 = lower_idx(g.vtab, g.n_rows, vlo);
+        j1 = upper_idx(g.vtab, g.n_rows, vhi);
+    }
     if (i0 > i1 || j0 > j1) {
         cnt[idx] = 0;
         rect[idx] = make_uint2(0u, 0u);

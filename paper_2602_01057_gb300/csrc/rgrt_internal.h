@@ -8,19 +8,37 @@
 namespace rgrt {
 
 // Geometry as the kernels see it.  kind: 0 = parallel rays (CT parallel and
-// PET), 1 = cone beam.  pet != 0 selects the PET chord segment and the
-// [plane][angle][radial] output layout.
+// the PET ring), 1 = cone beam, 2 = 3-D PET (LORs between two rings: their
+// direction e_w + kappa e_v depends on the radial bin).  pet != 0 selects the
+// PET chord segment between the ring's two crystals.  The output index of
+// (view, row, col) is view stride_view + row stride_row + col.
+constexpr int GM_PARALLEL = 0, GM_CONE = 1, GM_PET3D = 2;
 struct DevGeom {
     int kind, pet;
-    int n_views, n_rows, n_cols;
+    int n_views, n_rows, n_cols;  // 3-D PET: n_views counts (ring difference, angle) pairs
     int tile_w, tile_h, tiles_x, tiles_y;
     int v0;                       // first view of the current chunk
     long long stride_view, stride_row;
     float dso, dsd, t_a, t_b, radius2;
+    int n_ang, max_rd;            // 3-D PET: angles per ring difference, largest ring difference
+    float ring_pitch;             // 3-D PET: axial distance of neighbouring rings
     const float *frames;          // n_views x 9 : e_u, e_v, e_w
     const float *utab;            // n_cols pixel u coordinates
-    const float *vtab;            // n_rows pixel v coordinates
+    const float *vtab;            // n_rows pixel v coordinates (3-D PET: ring heights)
 };
+
+// 3-D PET: ring difference of view `view`
+__host__ __device__ inline int pet3d_delta(const DevGeom &g, int view) { return view / g.n_ang - g.max_rd; }
+
+// Views of a description (3-D PET: one per ring difference and angle) and
+// its rays.
+int64_t desc_views(const rgrt_geom_desc *d);
+int64_t desc_rays(const rgrt_geom_desc *d);
+// Host tables of a validated description -- frames [views x 9], u [n_cols],
+// v [n_rows], the binary32 rounding of the binary64 geometry -- into tab
+// (9 views + n_cols + n_rows floats), and every field of dg but the table
+// pointers.
+void geom_tables(const rgrt_geom_desc *d, float *tab, DevGeom &dg);
 
 // Per-Gaussian records built once per parameter version.
 //   rec  : 5 float4 = (mu, rho), (P00 P01 P02 P11), (P12 P22 S00 S01),
@@ -110,9 +128,11 @@ int persistent_grid(bool forward, bool cone, int tile_w, int tile_threads);
 cudaError_t launch_param_chain(const float *mu, const float *ls, const float *q, const float *rho,
                                int64_t n, const float4 *grad, float *g_mu, float *g_ls,
                                float *g_q, float *g_rho, cudaStream_t s);
+// acc (nullable): device double the step's total is accumulated in (the
+// loss of several ray ranges); loss_out then receives the running total
 cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, float kappa,
                         float eps, const float *mult, const float *add, float *dLdI, double *partial,
-                        int nblk, float *loss_out, cudaStream_t s);
+                        int nblk, float *loss_out, cudaStream_t s, double *acc = nullptr);
 int loss_blocks(int64_t n);
 // Adam; bc_dev (optional) supplies the bias corrections (1 - beta^t) from
 // device memory instead of bc1, bc2; skip (optional) leaves everything

@@ -21,7 +21,7 @@ RGRT_COPY, RGRT_BORROW = 0, 1
 RGRT_LOSS_L2, RGRT_LOSS_POISSON = 0, 1
 RGRT_KERNEL_GAUSSIAN, RGRT_KERNEL_EPANECHNIKOV = 0, 1
 KERNELS = {"gaussian": RGRT_KERNEL_GAUSSIAN, "epanechnikov": RGRT_KERNEL_EPANECHNIKOV}
-_KIND = {"parallel": 0, "cone": 1, "pet": 2}
+_KIND = {"parallel": 0, "cone": 1, "pet": 2, "pet3d": 3}
 
 
 class RgrtError(RuntimeError):
@@ -40,6 +40,7 @@ class GeomDesc(ctypes.Structure):
         ("dso", ctypes.c_double), ("dsd", ctypes.c_double), ("radius", ctypes.c_double),
         ("n_crystals", ctypes.c_int32), ("arc_mode", ctypes.c_int32),
         ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+        ("max_ring_diff", ctypes.c_int32),
     ]
 
 
@@ -283,7 +284,7 @@ def make_desc(d: dict):
         float(d.get("t_a", 0.0)), float(d.get("t_b", 0.0)),
         float(d.get("dso", 0.0)), float(d.get("dsd", 0.0)), float(d.get("radius", 0.0)),
         int(d.get("n_crystals", 0)), int(d.get("arc_mode", 0)),
-        int(d.get("tile_w", 16)), int(d.get("tile_h", 16)))
+        int(d.get("tile_w", 16)), int(d.get("tile_h", 16)), int(d.get("max_ring_diff", 0)))
     return desc, angles
 
 

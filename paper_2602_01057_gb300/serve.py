@@ -99,11 +99,12 @@ def subset_geometries(geom: dict, views_per_iter: int, seed: int):
     """Split the views of `geom` into mini-batch geometries.
 
     Returns (geoms, order): geoms[b] holds views order[b*k:(b+1)*k] with
-    explicit angles (CT, or PET sinogram angles pi j / n_views), order the
-    seeded permutation of the views."""
+    explicit angles (CT, or PET sinogram angles pi j / n_views; a 3-D PET
+    mini-batch keeps every ring difference of its angles), order the seeded
+    permutation of the views."""
     V = int(geom["n_views"])
     order = np.random.default_rng(seed).permutation(V)
-    if geom["kind"] == "pet":
+    if geom["kind"] in ("pet", "pet3d"):
         all_angles = np.pi * np.arange(V, dtype=np.float64) / V
     else:
         all_angles = np.asarray(geom["angles"], dtype=np.float64)
@@ -120,13 +121,15 @@ def subset_geometries(geom: dict, views_per_iter: int, seed: int):
 def subset_measurements(geom: dict, y: np.ndarray, order: np.ndarray, views_per_iter: int):
     """y rearranged so that mini-batch b's measurements are one contiguous
     block in its geometry's layout (CT [view][row][col], PET
-    [plane][angle][radial])."""
+    [plane][angle][radial], 3-D PET [ring difference][angle][ring pair][radial])."""
     V, H, W = int(geom["n_views"]), int(geom["n_rows"]), int(geom["n_cols"])
     parts = []
     for b in range(0, V, views_per_iter):
         idx = order[b:b + views_per_iter]
         if geom["kind"] == "pet":
             parts.append(y.reshape(H, V, W)[:, idx, :].reshape(-1))
+        elif geom["kind"] == "pet3d":
+            parts.append(y.reshape(-1, V, H, W)[:, idx].reshape(-1))
         else:
             parts.append(y.reshape(V, H, W)[idx].reshape(-1))
     return np.concatenate(parts).astype(np.float32)

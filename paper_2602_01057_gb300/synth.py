@@ -186,6 +186,14 @@ def geom_c3(n_angles: int = 288, n_radial: int = 329, n_planes: int = 63, arc_mo
                     plane_pitch=2.0, arc_mode=arc_mode, tile=tile)
 
 
+def geom_c3_3d(max_ring_diff: int = 5, arc_mode: int = 0, tile=(16, 16)) -> dict:
+    """The ring of geom_c3 as a fully 3-D scanner: its 32 rings at a 4 mm
+    pitch (the 63 planes of geom_c3 are the direct and cross planes of these
+    rings) with every ring pair up to the given ring difference."""
+    return geom_pet3d(288, 329, 32, radius=400.0, n_crystals=576, ring_pitch=4.0,
+                      max_ring_diff=max_ring_diff, arc_mode=arc_mode, tile=tile)
+
+
 def num_rays(g: dict) -> int:
     if g["kind"] == "rays":
         return int(np.asarray(g["o"]).shape[0])

@@ -361,6 +361,56 @@ def test_loss_grad_matches_oracle(rg, ctx, torch, oracle, loss):
         np.testing.assert_array_equal(after[k], G[k])
 
 
+@pytest.mark.parametrize("loss", ["l2", "poisson"])
+def test_loss_grad_in_view_chunks(rg, ctx, torch, oracle, loss):
+    """A context whose HBM budget holds the tile lists of a few views only:
+    the step bins, projects, takes the loss of and back-projects one view
+    chunk at a time.  Loss and gradient against the FP64 oracle."""
+    G, gd = case("cone_small")
+    ref_fwd = oracle.forward(gd, G)
+    T = synth.perturbed(G, 78, pos_std=0.01)
+    I_true = oracle.forward(gd, T)["I"]
+    if loss == "l2":
+        y = I_true.astype(np.float32)
+        kappa, eps = 1.0, 0.0
+        L_ref, dLdI = oracle.loss_l2(ref_fwd["I"], y)
+        kind = rg.RGRT_LOSS_L2
+    else:
+        kappa, eps = 50.0, 1e-3
+        y = np.random.default_rng(5).poisson(kappa * I_true + eps).astype(np.float32)
+        L_ref, dLdI = oracle.loss_poisson(ref_fwd["I"], y, kappa, eps)
+        kind = rg.RGRT_LOSS_POISSON
+    hp = rg.adam_params(kappa=kappa, poisson_eps=eps)
+    ref = oracle.backward(gd, G, dLdI)
+    chunked = 0
+    budget = 64 << 20
+    while budget >= 256 << 10 and not chunked:
+        c = rg.Context(0, budget)
+        try:
+            gs = rg.Gaussians(c, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+            geom = rg.Geometry(c, gd)
+            n = gs.n
+            outs = [np.zeros(sz, np.float32) for sz in ((n, 3), (n, 3), (n, 4), (n,))]
+            lo = np.zeros(1, np.float32)
+            c.prof_enable(True)
+            rg.loss_grad(c, gs, geom, y, kind, hp, lo, *outs)
+            launches, _ = c.prof_get("k_forward")
+            if launches >= 2:
+                chunked = launches
+                assert float(lo[0]) == pytest.approx(L_ref, rel=1e-5)
+                got = dict(zip(("mu", "ls", "q", "rho"), outs))
+                for k in ("mu", "ls", "q", "rho"):
+                    assert grad_err(got, ref, k) < GRAD_TOL, k
+            gs.close()
+            geom.close()
+        except rg.RgrtError:
+            break          # the budget no longer holds one view's lists
+        finally:
+            c.close()
+        budget //= 2
+    assert chunked >= 2
+
+
 # ------------------------------------------------------------------ view subsets
 
 @pytest.mark.parametrize("name", ["cone_small", "pet_arc"])
