@@ -286,6 +286,94 @@ def psnr(vol: np.ndarray, ref: np.ndarray) -> float:
 
 
 # ---------------------------------------------------------------------------
+# point sources in a PET ring (the arc vs raw sampling study)
+# ---------------------------------------------------------------------------
+
+def pet_radial_positions(g: dict) -> np.ndarray:
+    """Radial positions s_i of a PET geometry's bins (arc-corrected: uniform
+    pi R / n_crystals apart; raw: R sin of the crystal-pair angle)."""
+    k = np.arange(int(g["n_cols"])) - 0.5 * (int(g["n_cols"]) - 1)
+    R, n = float(g["radius"]), int(g["n_crystals"])
+    if int(g.get("arc_mode", 0)) == 0:
+        return k * (math.pi * R / n)
+    return R * np.sin(k * math.pi / n)
+
+
+def point_source_sinogram(g: dict, centres, radius: float, density: float = 1.0, n_sub: int = 5) -> np.ndarray:
+    """Expected sinogram [plane][angle][radial] of small uniform spheres
+    (point sources of the given radius and density) on a 2-D PET ring
+    geometry: chord lengths 2 sqrt(a^2 - r^2)_+ through each sphere, r^2 =
+    (c . e_u - s)^2 + (c_z - z_p)^2, each bin averaged over n_sub positions
+    across its width (raw bins: crystal-pair angles within half a crystal
+    step either side, so their width shrinks as cos; arc-corrected bins: a
+    uniform width)."""
+    V, H, W = int(g["n_views"]), int(g["n_rows"]), int(g["n_cols"])
+    R, n = float(g["radius"]), int(g["n_crystals"])
+    k = np.arange(W) - 0.5 * (W - 1)
+    off = (np.arange(n_sub) + 0.5) / n_sub - 0.5          # sub-positions across a bin, in bin units
+    if int(g.get("arc_mode", 0)) == 0:
+        s = (k[:, None] + off[None, :]) * (math.pi * R / n)
+    else:
+        s = R * np.sin((k[:, None] + off[None, :]) * math.pi / n)
+    phi = math.pi * np.arange(V) / V
+    z = (np.arange(H) - 0.5 * (H - 1)) * float(g["pitch_v"])
+    out = np.zeros((H, V, W))
+    for c in np.asarray(centres, np.float64):
+        cu = c[0] * np.cos(phi) + c[1] * np.sin(phi)                 # [V]
+        r2 = (cu[None, :, None, None] - s[None, None, :, :]) ** 2 + ((c[2] - z) ** 2)[:, None, None, None]
+        out += density * (2.0 * np.sqrt(np.maximum(radius * radius - r2, 0.0))).mean(axis=3)
+    return out
+
+
+def arc_resample(y: np.ndarray, g_raw: dict) -> np.ndarray:
+    """Arc correction of a raw-mode sinogram [plane][angle][radial]: every
+    projection linearly interpolated from the raw positions R sin(.) onto the
+    uniform positions of the arc-corrected geometry (same bins, arc_mode 0);
+    positions beyond the outermost raw bin get 0."""
+    s_raw = pet_radial_positions(dict(g_raw, arc_mode=1))
+    s_arc = pet_radial_positions(dict(g_raw, arc_mode=0))
+    H, V, W = y.shape
+    flat = y.reshape(-1, W)
+    out = np.empty_like(flat, dtype=np.float64)
+    for r in range(flat.shape[0]):
+        out[r] = np.interp(s_arc, s_raw, flat[r], left=0.0, right=0.0)
+    return out.reshape(H, V, W)
+
+
+def grid_gaussians(radius: float, spacing: float, sigma: float, rho: float, z: float = 0.0) -> dict:
+    """Isotropic Gaussians on a square grid (one layer at height z) filling
+    the disk of the given radius: a blind start for reconstructions."""
+    a = np.arange(-radius, radius + spacing / 2, spacing)
+    X, Y = np.meshgrid(a, a, indexing="ij")
+    keep = X ** 2 + Y ** 2 <= radius ** 2
+    n = int(keep.sum())
+    mu = np.stack([X[keep], Y[keep], np.full(n, z)], 1).astype(np.float32)
+    return dict(mu=mu, ls=np.full((n, 3), math.log(sigma), np.float32),
+                q=np.tile(np.array([1.0, 0.0, 0.0, 0.0], np.float32), (n, 1)),
+                rho=np.full(n, rho, np.float32))
+
+
+def fwhm(profile: np.ndarray, spacing: float) -> float:
+    """Full width at half maximum of a sampled single-peaked profile, the
+    half-maximum crossings found by linear interpolation either side of the
+    peak (nan if a crossing is missing)."""
+    p = np.asarray(profile, np.float64)
+    i = int(np.argmax(p))
+    half = 0.5 * p[i]
+    lo = i
+    while lo > 0 and p[lo] > half:
+        lo -= 1
+    hi = i
+    while hi < p.size - 1 and p[hi] > half:
+        hi += 1
+    if p[lo] > half or p[hi] > half:
+        return float("nan")
+    xl = lo + (half - p[lo]) / (p[lo + 1] - p[lo])
+    xh = hi - (half - p[hi]) / (p[hi - 1] - p[hi])
+    return float((xh - xl) * spacing)
+
+
+# ---------------------------------------------------------------------------
 # explicit ray sets
 # ---------------------------------------------------------------------------
 
