@@ -95,6 +95,35 @@ __device__ __forceinline__ void to_frame(const float *X, const float *eu, const 
     out[5] = quad_form(X, ew, ew);
 }
 
+// The footprint of a cone-beam record on the detector: rays at offset
+// (du, dv) from (u0, v0) with m <= K^2 satisfy Q - K^2 A <= 0, Q and A
+// quadratics in (du, dv):
+//   G(du, dv) = a du^2 + 2 b du dv + c dv^2 + 2 d du + 2 e dv + f <= 0.
+// When the quadratic part is positive definite (an ellipse: the K-sigma
+// ellipsoid lies in front of the source) G is convex, and G(x) >= G(x0) +
+// grad G(x0).(x - x0) bounds it from below over a rectangle around x0.
+struct Conic {
+    float a, b, c, d, e, f;
+    bool ok;
+};
+
+// the footprint conic of a cone-beam view-space record (offsets from u0, v0)
+template <int KER>
+__device__ __forceinline__ Conic cone_conic(const VRec &r)
+{
+    const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
+    const float K2 = Kern<KER>::SKIP, ik = 1.0f / Kern<KER>::QSCALE;
+    Conic cn;
+    cn.a = c0.z * ik - K2 * c2.x;
+    cn.b = 0.5f * (c0.w * ik - K2 * c2.y);
+    cn.c = c1.x * ik - K2 * c2.z;
+    cn.d = -0.5f * K2 * c1.z;
+    cn.e = -0.5f * K2 * c1.w;
+    cn.f = -K2 * c1.y;
+    cn.ok = cn.a > 0.0f && cn.a * cn.c - cn.b * cn.b > 1e-3f * cn.a * cn.c;
+    return cn;
+}
+
 // gather one record and turn it into its view-space form for frame F
 // (3-D PET: kap0, kap1 are the extreme LOR slopes of the tile's columns)
 template <int GM, int KER>
@@ -147,6 +176,7 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         out.c0 = make_float4(u0, v0, k * Muu, 2.0f * k * Muv);
         out.c1 = make_float4(k * Mvv, A0, 2.0f * au, 2.0f * av);
         out.c2 = make_float4(Pf[0], 2.0f * Pf[1], Pf[3], rho * Kern<KER>::FAC);
+
         // both segment ends (source, detector plane) beyond the 8.66-sigma ball
         sat = D >= Kern<KER>::BALL * smax && (g.dsd - D) >= Kern<KER>::BALL * smax;
     } else if (GM == GM_PET3D) {
@@ -191,6 +221,7 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         out.c0 = make_float4(mu_u, mu_v, k * Sf[3], -2.0f * k * Sf[1]);
         out.c1 = make_float4(k * Sf[0], iA, rA, 0.0f);
         out.c2 = make_float4(0.0f, 0.0f, 0.0f, rho * Kern<KER>::FAC * rA);
+
         if (g.pet) {
             float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
             sat = rxy + Kern<KER>::BALL * smax <= sqrtf(g.radius2);
@@ -356,10 +387,32 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         prep_record<GM, KER>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i], kap0, kap1);
         const float4 bb = sv[i].bb;
+        // a block inside the footprint's box may still miss the footprint
+        // ellipse: skip it when the tangent plane of G at the block centre
+        // stays above tol over the block (a pair with m <= 9 + 9e-4 has
+        // G <= -0.19 A < 0 at K^2 = 9.2, so none is lost).  Cone beam only:
+        // the small footprints of the parallel-ray workloads fill their boxes'
+        // blocks, and the test there cost more than it saved.
+        Conic cn;
+        cn.ok = false;
+        float u0 = 0.0f, v0 = 0.0f;
+        if (GM == GM_CONE) {
+            cn = cone_conic<KER>(sv[i]);
+            u0 = sv[i].c0.x;
+            v0 = sv[i].c0.y;
+        }
+        const float tol = 1e-3f * fabsf(cn.f);
         uint32_t m = 0;
         for (int w = 0; w < nw; w++) {
             const float4 wb = wbox[w];
-            const bool hit = !(bb.y < wb.x || bb.x > wb.y || bb.w < wb.z || bb.z > wb.w);
+            bool hit = !(bb.y < wb.x || bb.x > wb.y || bb.w < wb.z || bb.z > wb.w);
+            if (GM == GM_CONE && hit && cn.ok) {
+                const float cu = 0.5f * (wb.x + wb.y) - u0, cv = 0.5f * (wb.z + wb.w) - v0;
+                const float hu = 0.5f * (wb.y - wb.x), hv = 0.5f * (wb.w - wb.z);
+                const float gu = cn.a * cu + cn.b * cv + cn.d, gv = cn.b * cu + cn.c * cv + cn.e;
+                const float G = cu * (gu + cn.d) + cv * (gv + cn.e) + cn.f;
+                hit = G - 2.0f * (fabsf(gu) * hu + fabsf(gv) * hv) <= tol;
+            }
             m |= (uint32_t)hit << w;
         }
         if (sv[i].g2.w != 0.0f) m |= 0x100u;
