@@ -38,9 +38,9 @@ namespace {
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
 // chunk buffers of the forward: with two, a chunk's records are prepared into
 // one buffer while slower warps still read the other, and a single barrier
-// per chunk suffices -- but the doubled shared memory drops the kernel to 3
-// CTAs per SM and the cone-beam forward measured 2% slower, so one it is
-constexpr int NBUF = 1;
+// per chunk suffices.  The staged record (SRec, 80 B) leaves the general-path
+// fields in global memory so that two buffers still fit 4 CTAs per SM.
+constexpr int NBUF = 2;
 constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
 constexpr float M_PER_ARG = -1.38629436111989061f;        // m = arg * (-2 ln 2)
 constexpr float CUT_ARG = -6.49212768400033233f;          // arg at m = 9
@@ -59,6 +59,30 @@ struct VRec {
     float4 g1;  // P00 P01 P02 P11              (general path)
     float4 g2;  // P12 P22, gid bits, 1 = view-space path / 0 = general path
 };
+
+// the forward's shared-memory copy of a VRec: the view-space coefficients,
+// the detector box and (gid, path); general-path records read mu, rho and P
+// from the global records by gid
+struct SRec {
+    float4 c0, c1, c2, bb;
+    uint32_t gid;
+    float vs;       // 1 = view-space path, 0 = general path
+    float pad0, pad1;
+};
+
+// the general-path fields of record gid (mu, rho | P00 P01 P02 P11 | P12 P22)
+struct GRec {
+    float4 g0, g1, g2;
+};
+__device__ __forceinline__ GRec load_grec(const float4 *__restrict__ rec, uint32_t gid)
+{
+    const float4 *r = rec + REC_F4 * (size_t)gid;
+    GRec o;
+    o.g0 = __ldg(r);
+    o.g1 = __ldg(r + 1);
+    o.g2 = __ldg(r + 2);
+    return o;
+}
 
 __device__ __forceinline__ float quad_form(const float *Sg, const float *a, const float *b)
 {
@@ -380,13 +404,21 @@ struct ChunkLists {
 template <int GM, int KER>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
                                            uint32_t base, uint32_t stride, int cnt,
-                                           const float4 *rec, const float4 *crec, VRec *sv,
+                                           const float4 *rec, const float4 *crec, SRec *sv,
                                            const float4 *wbox, int nw, uint32_t *msk,
                                            float kap0, float kap1)
 {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        prep_record<GM, KER>(g, F, __ldg(gids + base + (uint32_t)i * stride), rec, crec, sv[i], kap0, kap1);
-        const float4 bb = sv[i].bb;
+        const uint32_t gid = __ldg(gids + base + (uint32_t)i * stride);
+        VRec vr;
+        prep_record<GM, KER>(g, F, gid, rec, crec, vr, kap0, kap1);
+        sv[i].c0 = vr.c0;
+        sv[i].c1 = vr.c1;
+        sv[i].c2 = vr.c2;
+        sv[i].bb = vr.bb;
+        sv[i].gid = gid;
+        sv[i].vs = vr.g2.w;
+        const float4 bb = vr.bb;
         // a block inside the footprint's box may still miss the footprint
         // ellipse: skip it when the tangent plane of G at the block centre
         // stays above tol over the block (a pair with m <= 9 + 9e-4 has
@@ -397,9 +429,9 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
         cn.ok = false;
         float u0 = 0.0f, v0 = 0.0f;
         if (GM == GM_CONE) {
-            cn = cone_conic<KER>(sv[i]);
-            u0 = sv[i].c0.x;
-            v0 = sv[i].c0.y;
+            cn = cone_conic<KER>(vr);
+            u0 = vr.c0.x;
+            v0 = vr.c0.y;
         }
         const float tol = 1e-3f * fabsf(cn.f);
         uint32_t m = 0;
@@ -415,7 +447,7 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
             }
             m |= (uint32_t)hit << w;
         }
-        if (sv[i].g2.w != 0.0f) m |= 0x100u;
+        if (vr.g2.w != 0.0f) m |= 0x100u;
         msk[i] = m;
     }
 }
@@ -450,8 +482,8 @@ __device__ __forceinline__ void warp_box(const TileCtx &c, float4 *wbox)
 // view-space value of one pair (without the |d~| factor of cone beam and
 // 3-D PET); returns arg = QSCALE m (Gaussian: -m log2(e)/2; Epanechnikov:
 // -m/kappa^2).  kap: the ray's slope (3-D PET).
-template <int GM, int KER>
-__device__ __forceinline__ float vs_value(const VRec &r, float u, float v, float kap, float &arg)
+template <int GM, int KER, class R>
+__device__ __forceinline__ float vs_value(const R &r, float u, float v, float kap, float &arg)
 {
     const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
     float rA = 1.0f;
@@ -503,7 +535,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const uint2 *__restrict__ ranges,
                                              float *__restrict__ out, Stats *stats)
 {
-    __shared__ VRec sv_buf[NBUF][CH];
+    __shared__ SRec sv_buf[NBUF][CH];
     __shared__ ChunkLists lists;
     __shared__ uint32_t msk_buf[NBUF][CH];
     __shared__ float4 wbox[8];
@@ -532,7 +564,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     const uint32_t nch = (nlist + CH - 1) / CH;
     for (uint32_t ch = 0; ch < nch; ch++) {
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
-        VRec *sv = sv_buf[ch % NBUF];
+        SRec *sv = sv_buf[ch % NBUF];
         uint32_t *msk = msk_buf[ch % NBUF];
         prep_chunk<GM, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk, c.kap0, c.kap1);
         // every thread has prepared this chunk and (with two buffers) left the
@@ -559,7 +591,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         if (ngen > 0) {
             const Ray ray = make_ray<GM>(g, F, u, v, kap);
             for (int k2 = 0; k2 < ngen; k2++) {
-                const VRec &r = sv[lists.gen[w][k2]];
+                const GRec r = load_grec(rec, sv[lists.gen[w][k2]].gid);
                 PairGeo q;
                 pair_geo(ray, r, q);
                 const float val = general_value<KER>(q, r.g0.w);
