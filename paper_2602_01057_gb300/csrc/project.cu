@@ -898,10 +898,12 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             ilo = in && i < ilo ? i : ilo;
             ihi = in ? i : ihi;
         }
-        // 8-column groups of the tile the box touches
-        uint32_t groups = 0;
+        // 8-column groups of the tile the box touches (3-D PET), and 4-column
+        // groups (the other geometries)
+        uint32_t groups = 0, groups4 = 0;
 #pragma unroll
         for (int c8 = 0; c8 < TW / 8; c8++) groups |= (uint32_t)(ilo <= 8 * c8 + 7 && ihi >= 8 * c8) << c8;
+        if (ilo <= ihi) groups4 = (2u << (ihi >> 2)) - (1u << (ilo >> 2));
         float o[16];
         bool any = false;
         if (!P3 && __any_sync(0xffffffffu, active && vs)) {
@@ -913,10 +915,10 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             for (int j = 0; j < TH; j++) {
                 const float vj = svr[j];
                 const bool rowin = active && vs && j >= jlo && j <= jhi;
-                // rows and 8-column groups that no Gaussian of the warp touches
+                // rows and 4-column groups that no Gaussian of the warp touches
                 // are skipped (the lists are ordered by footprint position, so
                 // a warp's Gaussians sit close together in the tile)
-                const uint32_t need = __reduce_or_sync(0xffffffffu, rowin ? groups : 0u);
+                const uint32_t need = __reduce_or_sync(0xffffffffu, rowin ? groups4 : 0u);
                 if (need == 0u || !rowin) continue;
                 const float dv = vj - v0, dv2 = dv * dv;
                 const float a1 = kMuv2 * dv, a0 = kMvv * dv2;
@@ -932,10 +934,10 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 float H0 = 0.0f, H1 = 0.0f, H2 = 0.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, Sw = 0.0f;
                 const float *gl_row = sgl + j * TW;
 #pragma unroll
-                for (int c8 = 0; c8 < TW / 8; c8++) {
-                if (!((need >> c8) & 1u)) continue;
+                for (int c4 = 0; c4 < TW / 4; c4++) {
+                if (!((need >> c4) & 1u)) continue;
 #pragma unroll
-                for (int i = 8 * c8; i < 8 * c8 + 8; i++) {
+                for (int i = 4 * c4; i < 4 * c4 + 4; i++) {
                     const float du = su[i] - u0;
                     const float qv = (kMuu * du + a1) * du + a0;
                     float rA, iA, arg;
