@@ -170,44 +170,55 @@ __global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict_
 }
 
 constexpr int SORT_BS = 256;     // one thread per digit value
-constexpr int SORT_ROUNDS = 8;
-constexpr int SORT_TILE = SORT_BS * SORT_ROUNDS;
+constexpr int SORT_ITEMS = 8;    // keys per thread
+constexpr int SORT_TILE = SORT_BS * SORT_ITEMS;
+constexpr int SORT_WARPS = SORT_BS / 32;
+constexpr int SORT_WSEG = 32 * SORT_ITEMS;   // keys of one warp's segment
+
+// Keys of a tile: warp w owns the contiguous segment [w SORT_WSEG, (w + 1)
+// SORT_WSEG) of it, read lane-striped (item i of lane l is key i 32 + l), so
+// walking items in order and lanes in order visits the segment in key order.
 
 __global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int shift,
                             uint32_t *__restrict__ hist, uint32_t nb)
 {
     __shared__ uint32_t h[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     h[threadIdx.x] = 0;
     __syncthreads();
-    uint32_t base = blockIdx.x * SORT_TILE;
+    const uint32_t seg = blockIdx.x * SORT_TILE + w * SORT_WSEG;
 #pragma unroll
-    for (int r = 0; r < SORT_ROUNDS; r++) {
-        uint32_t i = base + r * SORT_BS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    for (int i = 0; i < SORT_ITEMS; i++) {
+        const uint32_t k = seg + i * 32 + lane;
+        if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// stable scatter: rank of a key = keys with the same digit in earlier rounds
-// of this block + in earlier warps of this round + in lower lanes of its warp
-// Scatter of one radix pass.  A CTA takes a tile of SORT_TILE keys: it ranks
-// them stably by digit inside the tile (rounds in order, warps in order, lanes
-// in order), places keys and values at their tile-local positions in shared
-// memory, and then writes the tile out in that order -- each digit's keys are
-// consecutive there and land consecutively at the digit's global offset, so
-// the global writes are runs rather than single words.
-__global__ void k_sort_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                               uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals, uint32_t n,
-                               int shift, const uint32_t *__restrict__ hist,
-                               const uint32_t *__restrict__ offs, uint32_t nb)
+// Scatter of one radix pass.  A CTA takes a tile of SORT_TILE keys and ranks
+// them stably by digit: every warp ranks its segment with warp-private digit
+// counters (items in order, lanes in order, peers of a digit from
+// match_any), a per-digit scan over the warps and one over the digits give
+// tile-local positions; keys and values are placed there in shared memory
+// and written out in that order -- each digit's keys are consecutive there
+// and land consecutively at the digit's global offset (runs, not single words).
+__global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__restrict__ keys,
+                                                          const uint32_t *__restrict__ vals,
+                                                          uint32_t *__restrict__ okeys,
+                                                          uint32_t *__restrict__ ovals, uint32_t n,
+                                                          int shift, const uint32_t *__restrict__ hist,
+                                                          const uint32_t *__restrict__ offs, uint32_t nb)
 {
     __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
-    __shared__ uint32_t lbase[256], run[256];
-    __shared__ uint32_t wc[SORT_BS / 32][256];
+    __shared__ uint32_t wcnt[SORT_WARPS][256];
+    __shared__ uint32_t lbase[256], wsum[SORT_WARPS];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t base = blockIdx.x * SORT_TILE;
+    const uint32_t seg = base + w * SORT_WSEG;
+#pragma unroll
+    for (int ww = 0; ww < SORT_WARPS; ww++) wcnt[ww][t] = 0;
     // tile-local start of every digit: exclusive scan of the tile's histogram
     {
         const uint32_t c = hist[(size_t)t * nb + blockIdx.x];
@@ -217,52 +228,62 @@ __global__ void k_sort_scatter(const uint32_t *__restrict__ keys, const uint32_t
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) wc[0][w] = x;
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
         uint32_t add = 0;
-        for (int ww = 0; ww < w; ww++) add += wc[0][ww];
+        for (int ww = 0; ww < w; ww++) add += wsum[ww];
         lbase[t] = add + x - c;
-        run[t] = add + x - c;
-        __syncthreads();
     }
-    for (int r = 0; r < SORT_ROUNDS; r++) {
+    uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
 #pragma unroll
-        for (int ww = 0; ww < SORT_BS / 32; ww++) wc[ww][t] = 0;
-        __syncthreads();
-        const uint32_t i = base + r * SORT_BS + t;
-        const bool valid = i < n;
-        const uint32_t key = valid ? keys[i] : 0u;
-        const uint32_t val = valid ? vals[i] : 0u;
-        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+    for (int i = 0; i < SORT_ITEMS; i++) {
+        const uint32_t k = seg + i * 32 + lane;
+        key[i] = k < n ? keys[k] : 0u;
+    }
+    // warp-local ranks
+    uint32_t *cnt = wcnt[w];
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; i++) {
+        const bool valid = seg + i * 32 + lane < n;
+        const uint32_t d = valid ? (key[i] >> shift) & 255u : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[w][d] = __popc(peers);
-        __syncthreads();
-        uint32_t acc = run[t];
+        const uint32_t before = cnt[d & 255u];
+        rank[i] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) cnt[d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps' runs (exclusive over warps)
+    {
+        uint32_t acc = lbase[t];
 #pragma unroll
-        for (int ww = 0; ww < SORT_BS / 32; ww++) {
-            const uint32_t c = wc[ww][t];
-            wc[ww][t] = acc;
+        for (int ww = 0; ww < SORT_WARPS; ww++) {
+            const uint32_t c = wcnt[ww][t];
+            wcnt[ww][t] = acc;
             acc += c;
         }
-        run[t] = acc;
-        __syncthreads();
-        if (valid) {
-            const uint32_t at = wc[w][d] + rank;   // tile-local position
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; i++) {
+        const uint32_t k = seg + i * 32 + lane;
+        if (k < n) {
+            const uint32_t at = cnt[(key[i] >> shift) & 255u] + rank[i];
             if (at < SORT_TILE) {
-                sk[at] = key;
-                sv[at] = val;
+                sk[at] = key[i];
+                sv[at] = vals[k];
             }
         }
-        __syncthreads();
     }
-    const uint32_t cnt = min((uint32_t)SORT_TILE, n - base);
-    for (uint32_t k = t; k < cnt; k += SORT_BS) {
-        const uint32_t key = sk[k];
-        const uint32_t d = (key >> shift) & 255u;
+    __syncthreads();
+    const uint32_t cnt_tile = min((uint32_t)SORT_TILE, n - base);
+    for (uint32_t k = t; k < cnt_tile; k += SORT_BS) {
+        const uint32_t kk = sk[k];
+        const uint32_t d = (kk >> shift) & 255u;
         uint32_t dst = offs[(size_t)d * nb + blockIdx.x] + (k - lbase[d]);
         if (dst >= n) dst = base + k;  // never taken when the histogram scan is consistent
-        okeys[dst] = key;
+        okeys[dst] = kk;
         ovals[dst] = sv[k];
     }
 }
