@@ -43,7 +43,7 @@ FLOP_PER_PAIR_ADJ = 180
 # cone-beam CT workload, from the ncu captures summarised in
 # profiles/k_adjoint_c2_cone.md and profiles/k_forward_c2_cone.md; None once a
 # kernel has changed since its capture.
-TRAFFIC_C2 = {"k_adjoint": 272.933632e6 + 4.254976e6, "k_forward": 222.778368e6 + 37.923840e6}
+TRAFFIC_C2 = {"k_adjoint": 272.663040e6 + 4.093184e6, "k_forward": 222.537216e6 + 38.337792e6}
 WORKLOADS = {
     "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
           "180 views over 360 deg, 256x256 detector, source-origin 1000 mm, source-detector 1500 mm",

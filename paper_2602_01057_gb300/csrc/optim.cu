@@ -118,17 +118,26 @@ __global__ void k_loss(int kind, const float *__restrict__ I, const float *__res
     }
 }
 
-// acc (nullable): running total over several launches (ray ranges of one step)
+// acc (nullable): running total over several launches (ray ranges of one
+// step).  One CTA of LOSS_BS threads, a fixed summation order (strided
+// partial sums, then a tree), so the total does not vary from run to run.
 __global__ void k_loss_final(const double *partial, int nblk, double *acc, float *loss_out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < nblk; k++) t += partial[k];
+    __shared__ double sh[LOSS_BS / 32];
+    double t = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) t += partial[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int k = 0; k < LOSS_BS / 32; k++) u += sh[k];
         if (acc) {
-            t += *acc;
-            *acc = t;
+            u += *acc;
+            *acc = u;
         }
-        *loss_out = (float)t;
+        *loss_out = (float)u;
     }
 }
 
@@ -175,7 +184,7 @@ cudaError_t launch_loss(int kind, const float *I, const float *y, int64_t n, flo
                         int nblk, float *loss_out, cudaStream_t s, double *acc)
 {
     k_loss<<<nblk, LOSS_BS, 0, s>>>(kind, I, y, n, kappa, eps, mult, add, dLdI, partial);
-    k_loss_final<<<1, 32, 0, s>>>(partial, nblk, acc, loss_out);
+    k_loss_final<<<1, LOSS_BS, 0, s>>>(partial, nblk, acc, loss_out);
     count_launches(2);
     return cudaGetLastError();
 }
