@@ -79,6 +79,8 @@ def job_budget(job: Job) -> int:
     v = int(job.geom.get("n_views", 1))
     if job.kind == RECON:
         v = min(v, int(job.views_per_iter))
+    if job.geom.get("kind") == "pet3d":
+        v *= 2 * int(job.geom["max_ring_diff"]) + 1      # one view per ring difference and angle
     v = min(v, 64)
     resident = 4 * n * (11 + 22 + 32 + 16 + 22) + 16 * r
     scratch = n * v * (16 + 12 * 16)

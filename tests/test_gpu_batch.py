@@ -1,5 +1,6 @@
 """The batched form (many scans per step, persistent launches, CUDA graph)
-against one-scan-at-a-time calls of the same library, and the autotuner."""
+against one-scan-at-a-time calls of the same library and against the FP64
+oracle, and the autotuner."""
 import math
 
 import numpy as np
@@ -52,6 +53,31 @@ def test_batch_forward_equals_single_scans(env):
             rg.project_forward(ctx, g, geom, ref)
             torch.cuda.synchronize()
             assert torch.equal(o, ref)   # same tiles, same order: identical sums
+
+
+def test_batch_forward_matches_oracle(env, oracle):
+    """The batched forward against the FP64 oracle: every ray of the first 4
+    scans, a stratified 1/64 subsample (every 64th ray) of the others."""
+    torch, rg, ctx = env
+    scans = _scans(3, 8)
+    gs = [rg.Gaussians(ctx, *_dev(torch, G)) for G, _ in scans]
+    geoms = [rg.Geometry(ctx, gd) for _, gd in scans]
+    b = rg.Batch(ctx, gs, geoms)
+    outs = [torch.empty(g.n_rays, device="cuda") for g in geoms]
+    b.forward(outs)
+    torch.cuda.synchronize()
+    for i, ((G, gd), o) in enumerate(zip(scans, outs)):
+        I = o.cpu().numpy().astype(np.float64)
+        if i < 4:
+            ref = oracle.forward(gd, G)
+        else:
+            idx = np.arange(0, I.size, 64)
+            ref = oracle.forward_rays(gd, G, idx)
+            I = I[idx]
+        clip = np.clip(I, ref["I_lo"], ref["I_hi"])
+        err = np.linalg.norm(I - clip) / max(np.linalg.norm(clip), 1e-300)
+        assert np.count_nonzero(ref["I"]) > 0
+        assert err < 1e-5, (i, err)
 
 
 def test_batch_loss_step_matches_single_scans(env):

@@ -241,3 +241,21 @@ def test_rejections(rg, ctx, torch):
     geom = rg.Geometry(ctx, scanner())
     with pytest.raises(rg.RgrtError):
         rg.Batch(ctx, [gs], [geom])
+
+
+def test_reconstruction_job_in_angle_minibatches(rg, torch, oracle):
+    """A serving reconstruction job on a 3-D PET scanner: mini-batches of
+    angles (every ring difference of each), Adam steps lower the loss."""
+    from paper_2602_01057_gb300 import serve
+    G = phantom(31, n=600)
+    T = synth.perturbed(G, 32, pos_std=1.5)
+    gd = scanner(n_ang=16, D=3)
+    y = oracle.forward(gd, T)["I"].astype(np.float32)
+    job = serve.Job(serve.RECON, G, gd, y=y, n_iter=24, views_per_iter=4, seed=5,
+                    hp=dict(lr_mu=0.05, lr_rho=1e-3))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        res = serve.run_job(job, 0, serve.job_budget(job), s)
+    assert res["iterations"] == 24
+    L = res["losses"]
+    assert np.all(np.isfinite(L)) and L[-4:].mean() < 0.8 * L[:4].mean()

@@ -131,13 +131,22 @@ def test_budget_grows_with_size():
     b = serve.job_budget(_job("b", n=100000))
     c = serve.job_budget(_job("c", n=1000, side=512))
     assert b > a and c > a
+    # a 3-D PET job counts one view per (ring difference, angle)
+    G = synth.gaussians_uniform(1000, 1)
+    p0 = serve.job_budget(serve.Job(serve.FWD, G, synth.geom_pet3d(48, 65, 8, 400.0, 576, 4.0, 0)))
+    p3 = serve.job_budget(serve.Job(serve.FWD, G, synth.geom_pet3d(48, 65, 8, 400.0, 576, 4.0, 3)))
+    assert p3 > p0
 
 
-@pytest.mark.parametrize("kind", ["cone", "parallel", "pet"])
+@pytest.mark.parametrize("kind", ["cone", "parallel", "pet", "pet3d"])
 def test_minibatch_subsets_reproduce_the_full_scan(oracle, kind):
     """The mini-batch geometries (explicit angles, PET included) project to
     exactly the matching views of the full scan (FP64 oracle)."""
-    if kind == "pet":
+    if kind == "pet3d":
+        g = synth.geom_pet3d(12, 17, 5, 400.0, 576, 4.0, 2)
+        G = synth.gaussians_uniform(30, 6, half_box=40.0, log_sigma=math.log(6.0))
+        G["mu"][:, 2] *= 0.1
+    elif kind == "pet":
         g = synth.geom_pet(12, 17, 5, 400.0, 576, 2.0)
         G = synth.gaussians_uniform(30, 7, half_box=40.0, log_sigma=math.log(6.0))
         G["mu"][:, 2] *= 0.1
