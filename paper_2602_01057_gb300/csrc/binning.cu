@@ -183,14 +183,31 @@ __global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int s
                             uint32_t *__restrict__ hist, uint32_t nb)
 {
     __shared__ uint32_t h[256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     h[threadIdx.x] = 0;
     __syncthreads();
-    const uint32_t seg = blockIdx.x * SORT_TILE + w * SORT_WSEG;
+    // the tile as 16-byte loads (every load issued before the counting)
+    const uint32_t base = blockIdx.x * SORT_TILE;
+    constexpr int V = SORT_ITEMS / 4;
+    uint4 q[V];
 #pragma unroll
-    for (int i = 0; i < SORT_ITEMS; i++) {
-        const uint32_t k = seg + i * 32 + lane;
-        if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
+    for (int j = 0; j < V; j++) {
+        const uint32_t k = base + 4 * (threadIdx.x + j * SORT_BS);
+        if (k + 3 < n) {
+            q[j] = __ldg(reinterpret_cast<const uint4 *>(keys + k));
+        } else {
+            q[j].x = k < n ? keys[k] : 0u;
+            q[j].y = k + 1 < n ? keys[k + 1] : 0u;
+            q[j].z = k + 2 < n ? keys[k + 2] : 0u;
+            q[j].w = k + 3 < n ? keys[k + 3] : 0u;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        const uint32_t k = base + 4 * (threadIdx.x + j * SORT_BS);
+        if (k < n) atomicAdd(&h[(q[j].x >> shift) & 255u], 1u);
+        if (k + 1 < n) atomicAdd(&h[(q[j].y >> shift) & 255u], 1u);
+        if (k + 2 < n) atomicAdd(&h[(q[j].z >> shift) & 255u], 1u);
+        if (k + 3 < n) atomicAdd(&h[(q[j].w >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
@@ -212,13 +229,24 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
 {
     __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
     __shared__ uint32_t wcnt[SORT_WARPS][256];
-    __shared__ uint32_t lbase[256], wsum[SORT_WARPS];
+    __shared__ uint32_t lbase[256], gofs[256], wsum[SORT_WARPS];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t base = blockIdx.x * SORT_TILE;
     const uint32_t seg = base + w * SORT_WSEG;
+    // every global load of the tile up front: keys, values, and the tile's
+    // count and global offset of every digit
+    uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; i++) {
+        const uint32_t k = seg + i * 32 + lane;
+        key[i] = k < n ? keys[k] : 0u;
+        val[i] = k < n ? vals[k] : 0u;
+    }
+    const uint32_t my_ofs = offs[(size_t)t * nb + blockIdx.x];
 #pragma unroll
     for (int ww = 0; ww < SORT_WARPS; ww++) wcnt[ww][t] = 0;
+    gofs[t] = my_ofs;
     // tile-local start of every digit: exclusive scan of the tile's histogram
     {
         const uint32_t c = hist[(size_t)t * nb + blockIdx.x];
@@ -233,12 +261,6 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
         uint32_t add = 0;
         for (int ww = 0; ww < w; ww++) add += wsum[ww];
         lbase[t] = add + x - c;
-    }
-    uint32_t key[SORT_ITEMS], rank[SORT_ITEMS];
-#pragma unroll
-    for (int i = 0; i < SORT_ITEMS; i++) {
-        const uint32_t k = seg + i * 32 + lane;
-        key[i] = k < n ? keys[k] : 0u;
     }
     // warp-local ranks
     uint32_t *cnt = wcnt[w];
@@ -272,7 +294,7 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
             const uint32_t at = cnt[(key[i] >> shift) & 255u] + rank[i];
             if (at < SORT_TILE) {
                 sk[at] = key[i];
-                sv[at] = vals[k];
+                sv[at] = val[i];
             }
         }
     }
@@ -281,7 +303,7 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
     for (uint32_t k = t; k < cnt_tile; k += SORT_BS) {
         const uint32_t kk = sk[k];
         const uint32_t d = (kk >> shift) & 255u;
-        uint32_t dst = offs[(size_t)d * nb + blockIdx.x] + (k - lbase[d]);
+        uint32_t dst = gofs[d] + (k - lbase[d]);
         if (dst >= n) dst = base + k;  // never taken when the histogram scan is consistent
         okeys[dst] = kk;
         ovals[dst] = sv[k];
