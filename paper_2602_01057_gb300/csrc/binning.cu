@@ -135,37 +135,73 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restric
 // column buckets of the centre of the Gaussian's pixel box within the tile:
 // sorting by it orders each tile's list by footprint position (Gaussians of
 // the same position keep ascending ids, the sort being stable).
-__global__ void k_emit(DevGeom g, int nv, int64_t n, const uint32_t *__restrict__ cnt,
-                       const uint32_t *__restrict__ off, const uint2 *__restrict__ rect,
-                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t cap,
-                       uint32_t *overflow)
+// One thread per (view of the chunk, Gaussian) item; a CTA's 256 items own
+// one contiguous output range (the offsets are their exclusive scan).  With
+// STAGE the range is staged in shared memory and written out coalesced when
+// it fits -- worth it when items emit several keys each (large footprints);
+// with a key or two per item the direct writes are as compact and the
+// staging buffer only costs occupancy.
+constexpr int EMIT_BS = 256;
+constexpr int EMIT_STAGE = 4096;
+
+__device__ __forceinline__ void emit_item(const DevGeom &g, int vl, uint32_t k, uint2 r, uint32_t o,
+                                          uint32_t *kd, uint32_t *vd)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)nv * n) return;
-    uint32_t c = cnt[idx];
-    if (c == 0) return;
-    if ((uint64_t)off[idx] + c > cap) {   // more entries than the buffer holds
-        if (overflow) atomicOr(overflow, 1u);
-        return;
-    }
-    int vl = (int)(idx / n);
-    uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
-    uint2 r = rect[idx];
     const int i0 = r.x & 0xffff, i1 = r.x >> 16, j0 = r.y & 0xffff, j1 = r.y >> 16;
     const int tw = g.tile_w, th = g.tile_h;
     const int tx0 = i0 / tw, tx1 = i1 / tw, ty0 = j0 / th, ty1 = j1 / th;
-    uint32_t o = off[idx];
-    uint32_t tbase = (uint32_t)vl * (uint32_t)(g.tiles_x * g.tiles_y);
+    const uint32_t tbase = (uint32_t)vl * (uint32_t)(g.tiles_x * g.tiles_y);
     for (int ty = ty0; ty <= ty1; ty++) {
         const int jl = max(j0 - ty * th, 0), jh = min(j1 - ty * th, th - 1);
         const uint32_t rb = (uint32_t)(((jl + jh) * 8) / th);
         for (int tx = tx0; tx <= tx1; tx++) {
             const int il = max(i0 - tx * tw, 0), ih = min(i1 - tx * tw, tw - 1);
             const uint32_t cb = (uint32_t)(((il + ih) * 8) / tw);
-            keys[o] = ((tbase + (uint32_t)ty * (uint32_t)g.tiles_x + (uint32_t)tx) << 8) | (rb << 4) | cb;
-            vals[o] = k;
+            kd[o] = ((tbase + (uint32_t)ty * (uint32_t)g.tiles_x + (uint32_t)tx) << 8) | (rb << 4) | cb;
+            vd[o] = k;
             o++;
         }
+    }
+}
+
+template <bool STAGE>
+__global__ void __launch_bounds__(EMIT_BS) k_emit(DevGeom g, int nv, int64_t n,
+                                                  const uint32_t *__restrict__ cnt,
+                                                  const uint32_t *__restrict__ off,
+                                                  const uint2 *__restrict__ rect,
+                                                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                  uint32_t cap, uint32_t *overflow)
+{
+    __shared__ uint32_t sk[STAGE ? EMIT_STAGE : 1], sv[STAGE ? EMIT_STAGE : 1];
+    const int64_t tot = (int64_t)nv * n;
+    const int64_t first = (int64_t)blockIdx.x * EMIT_BS;
+    const int64_t last = min(first + EMIT_BS, tot) - 1;
+    const int64_t idx = first + threadIdx.x;
+    const uint64_t rs = off[first], re = (uint64_t)off[last] + cnt[last];
+    // staged only when the whole range fits the buffer (an item past the
+    // capacity writes nothing, as in the direct path)
+    const bool staged = STAGE && re - rs <= (uint64_t)EMIT_STAGE && re <= (uint64_t)cap;
+    uint32_t c = 0;
+    if (idx < tot) {
+        c = cnt[idx];
+        if (c != 0) {
+            const uint32_t o = off[idx];
+            if ((uint64_t)o + c > cap) {   // more entries than the buffer holds
+                if (overflow) atomicOr(overflow, 1u);
+            } else {
+                const int vl = (int)(idx / n);
+                const uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
+                if (staged) emit_item(g, vl, k, rect[idx], o - (uint32_t)rs, sk, sv);
+                else emit_item(g, vl, k, rect[idx], o, keys, vals);
+            }
+        }
+    }
+    if (!staged) return;     // uniform over the CTA
+    __syncthreads();
+    const uint32_t m = (uint32_t)(re - rs);
+    for (uint32_t e = threadIdx.x; e < m; e += EMIT_BS) {
+        keys[rs + e] = sk[e];
+        vals[rs + e] = sv[e];
     }
 }
 
@@ -346,8 +382,11 @@ cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt
 {
     int64_t tot = (int64_t)nv * n;
     if (tot <= 0) return cudaSuccess;
-    k_emit<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap,
-                                                        overflow);
+    const unsigned grid = (unsigned)((tot + EMIT_BS - 1) / EMIT_BS);
+    if ((double)cap >= 3.0 * (double)tot)
+        k_emit<true><<<grid, EMIT_BS, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap, overflow);
+    else
+        k_emit<false><<<grid, EMIT_BS, 0, s>>>(g, nv, n, cnt, off, rect, keys, vals, cap, overflow);
     count_launches(1);
     return cudaGetLastError();
 }
