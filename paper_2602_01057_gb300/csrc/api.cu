@@ -667,6 +667,12 @@ void rgrt::geom_tables(const rgrt_geom_desc *d, float *tab, DevGeom &dg)
     dg.n_ang = n_ang;
     dg.max_rd = d->kind == RGRT_GEOM_PET_3D ? d->max_ring_diff : 0;
     dg.ring_pitch = (float)d->pitch_v;
+    // uniform tables: the search guesses from t0 + i step (the guess only
+    // starts the search; its result comes from the table comparisons)
+    dg.u0 = ut[0];
+    dg.uinv = (W > 1 && (!pet || d->arc_mode == 0)) ? (float)((double)(W - 1) / ((double)ut[W - 1] - (double)ut[0])) : 0.0f;
+    dg.v0f = vt[0];
+    dg.vinv = H > 1 ? (float)((double)(H - 1) / ((double)vt[H - 1] - (double)vt[0])) : 0.0f;
 }
 
 // validation and error reporting shared with the allocation-free entry point

@@ -133,6 +133,8 @@ __device__ __forceinline__ bool cone_spec(float K2, float dsd, float ae, float a
     return true;
 }
 
+// first index whose table value is >= x (n if none), and the last whose
+// value is <= x (-1 if none), by binary search over the increasing table
 __device__ __forceinline__ int lower_idx(const float *tab, int n, float x)
 {
     int lo = 0, hi = n;
@@ -150,6 +152,30 @@ __device__ __forceinline__ int upper_idx(const float *tab, int n, float x)
         if (__ldg(tab + mid) > x) hi = mid; else lo = mid + 1;
     }
     return lo - 1;
+}
+
+// The same two searches started from a guess: for a uniformly spaced table
+// (t0 + i step in binary32, inv = 1/step) the guess is within a step of the
+// answer and a short walk in the table makes it exact -- the answer is
+// defined by the table comparisons alone, so it equals the binary search's.
+// inv == 0 (an irregular table) falls back to the binary search; NaN gives
+// what the binary search gives (n, n - 1).
+__device__ __forceinline__ int lower_idx_g(const float *tab, int n, float x, float t0, float inv)
+{
+    if (inv == 0.0f || !(x == x)) return lower_idx(tab, n, x);
+    int i = (int)fminf(fmaxf(ceilf((x - t0) * inv), 0.0f), (float)n);
+    while (i > 0 && __ldg(tab + i - 1) >= x) i--;
+    while (i < n && __ldg(tab + i) < x) i++;
+    return i;
+}
+__device__ __forceinline__ int upper_idx_g(const float *tab, int n, float x, float t0, float inv)
+{
+    if (inv == 0.0f || !(x == x)) return upper_idx(tab, n, x);
+    // first index whose value is > x, minus one
+    int i = (int)fminf(fmaxf(floorf((x - t0) * inv) + 1.0f, 0.0f), (float)n);
+    while (i > 0 && __ldg(tab + i - 1) > x) i--;
+    while (i < n && __ldg(tab + i) <= x) i++;
+    return i - 1;
 }
 
 // one thread per (view of the chunk, Gaussian), view-major
@@ -182,7 +208,8 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
         float hv = __fsqrt_rn(M(K2, form_spec(Sg, ev, ev)));
         ulo = S(mu_u, hu); uhi = A(mu_u, hu); vlo = S(mu_v, hv); vhi = A(mu_v, hv);
     }
-    int i0 = lower_idx(g.utab, g.n_cols, ulo), i1 = upper_idx(g.utab, g.n_cols, uhi);
+    int i0 = lower_idx_g(g.utab, g.n_cols, ulo, g.u0, g.uinv);
+    int i1 = upper_idx_g(g.utab, g.n_cols, uhi, g.u0, g.uinv);
     int j0, j1;
     if (g.kind == GM_PET3D) {
         // 3-D PET (not part of the FP32 culling specification, which covers
@@ -217,13 +244,13 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
                     zlo = fminf(zlo, zc - half);
                     zhi = fmaxf(zhi, zc + half);
                 }
-                j0 = lower_idx(g.vtab, g.n_rows, zlo - zoff);
-                j1 = min(upper_idx(g.vtab, g.n_rows, zhi - zoff), last);
+                j0 = lower_idx_g(g.vtab, g.n_rows, zlo - zoff, g.v0f, g.vinv);
+                j1 = min(upper_idx_g(g.vtab, g.n_rows, zhi - zoff, g.v0f, g.vinv), last);
             }
         }
     } else {
-        j0 = lower_idx(g.vtab, g.n_rows, vlo);
-        j1 = upper_idx(g.vtab, g.n_rows, vhi);
+        j0 = lower_idx_g(g.vtab, g.n_rows, vlo, g.v0f, g.vinv);
+        j1 = upper_idx_g(g.vtab, g.n_rows, vhi, g.v0f, g.vinv);
     }
     if (i0 > i1 || j0 > j1) {
         cnt[idx] = 0;

@@ -22,6 +22,9 @@ struct DevGeom {
     float dso, dsd, t_a, t_b, radius2;
     int n_ang, max_rd;            // 3-D PET: angles per ring difference, largest ring difference
     float ring_pitch;             // 3-D PET: axial distance of neighbouring rings
+    // first table value and inverse spacing of utab / vtab when uniformly
+    // spaced (CT, arc-corrected PET radial bins, planes and rings), else 0
+    float u0, uinv, v0f, vinv;
     const float *frames;          // n_views x 9 : e_u, e_v, e_w
     const float *utab;            // n_cols pixel u coordinates
     const float *vtab;            // n_rows pixel v coordinates (3-D PET: ring heights)
