@@ -1135,7 +1135,7 @@ __device__ __forceinline__ bool next_item(const ScanDesc *d, int nscan, uint32_t
 }
 
 template <bool CONE>
-__global__ void __launch_bounds__(256, 3) k_forward_persistent(const ScanDesc *__restrict__ d,
+__global__ void __launch_bounds__(256, 4) k_forward_persistent(const ScanDesc *__restrict__ d,
                                                                int nscan, uint32_t total,
                                                                uint32_t *queue)
 {
