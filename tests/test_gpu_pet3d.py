@@ -259,3 +259,32 @@ def test_reconstruction_job_in_angle_minibatches(rg, torch, oracle):
     assert res["iterations"] == 24
     L = res["losses"]
     assert np.all(np.isfinite(L)) and L[-4:].mean() < 0.8 * L[:4].mean()
+
+
+def test_no_gaussians_and_gaussians_outside_the_rings(rg, ctx, torch, oracle):
+    gd = scanner(D=4)
+    empty = dict(mu=np.zeros((0, 3), np.float32), ls=np.zeros((0, 3), np.float32),
+                 q=np.zeros((0, 4), np.float32), rho=np.zeros(0, np.float32))
+    I, gs, geom = forward(rg, ctx, torch, empty, gd)
+    assert I.size == geom.n_rays and not I.any()
+    # beyond the axial field of view (the rings span +-30 mm): every LOR misses
+    G = phantom(37, n=200)
+    G["mu"][:, 2] = np.where(np.arange(200) % 2 == 0, 80.0, -90.0).astype(np.float32)
+    I, gs, geom = forward(rg, ctx, torch, G, gd)
+    ref = oracle.forward(gd, G)
+    assert not ref["I"].any() and not I.any()
+    w = synth.random_weights(geom.n_rays, 38)
+    got = backward(rg, ctx, torch, gs, geom, w)
+    for k in got:
+        assert not np.asarray(got[k]).any(), k
+
+
+def test_single_ring(rg, ctx, torch, oracle):
+    """One ring, ring difference 0 only: a single row per view."""
+    G = phantom(41, n=300)
+    G["mu"][:, 2] = 0.0
+    gd = scanner(n_rings=1, D=0)
+    I, gs, geom = forward(rg, ctx, torch, G, gd)
+    ref = oracle.forward(gd, G)
+    assert np.count_nonzero(ref["I"]) > 100
+    assert fwd_err(I, ref) < FWD_TOL
