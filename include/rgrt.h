@@ -324,8 +324,9 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
  * RGRT_NOALLOC_SCRATCH_BYTES; no context is needed.  Arguments as for
  * gaussians_create + geometry_set + project_forward, but every array (mu3,
  * logscale3, quat4, rho, out_I) must be device memory of the current device;
- * desc->angles stays host memory.  Limits: at most 1024 views of 1024 x 1024
- * pixels, and the whole pipeline must fit the scratch (C1-sized problems of
+ * desc->angles stays host memory.  Limits: at most 1024 views (PET_3D: angles
+ * x ring differences) of 1024 x 1024 pixels, and the whole pipeline must fit
+ * the scratch (C1-sized problems of
  * a few thousand Gaussians fit easily); otherwise RGRT_E_CAPACITY with a
  * message stating the bytes needed.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and must come before any
