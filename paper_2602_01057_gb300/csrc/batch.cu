@@ -216,13 +216,16 @@ int enqueue_binning(rgrt_batch *b, cudaStream_t s)
         BK(launch_records(x.g->mu, x.g->ls, x.g->q, x.g->rho, x.N, x.g->rec, x.g->crec, nullptr, s));
         BK(launch_cull(dg, dg.n_views, x.g->crec, x.N, b->cnt, b->rect, s));
         BK(launch_scan(b->cnt, b->off, x.E, b->total, b->stmp, s));
-        // padding entries keep the all-ones key: they sort last and map to no tile
-        BK(cudaMemsetAsync(b->keys, 0xff, sizeof(uint32_t) * (size_t)x.cap, s));
+        // the scan's total (on the device) is the number of keys this step
+        // emits: the sort and the ranges take only those (at most the planned
+        // capacity; an item past it writes padding keys, which sort last and
+        // map to no tile, and raises the overflow flag)
         BK(launch_emit(dg, dg.n_views, x.N, b->cnt, b->off, b->rect, b->keys, x.vals, x.cap,
                        b->d_overflow, s));
-        BK(launch_sort(b->keys, x.vals, b->keys_alt, b->vals_alt, x.cap, x.bits, b->sort_tmp, s));
+        BK(launch_sort(b->keys, x.vals, b->keys_alt, b->vals_alt, x.cap, x.bits, b->sort_tmp, s, nullptr,
+                       b->total));
         BK(cudaMemsetAsync(x.ranges, 0, sizeof(uint2) * (size_t)x.T, s));
-        BK(launch_ranges(b->keys, x.cap, x.ranges, x.T, s));
+        BK(launch_ranges(b->keys, x.cap, x.ranges, x.T, s, b->total));
     }
     return RGRT_OK;
 }

@@ -188,6 +188,9 @@ __global__ void __launch_bounds__(EMIT_BS) k_emit(DevGeom g, int nv, int64_t n,
             const uint32_t o = off[idx];
             if ((uint64_t)o + c > cap) {   // more entries than the buffer holds
                 if (overflow) atomicOr(overflow, 1u);
+                // its slots below the capacity get the padding key (sorts
+                // last, maps to no tile), so that no slot is left stale
+                for (uint32_t e = o; e < cap && e < o + c; e++) keys[e] = 0xffffffffu;
             } else {
                 const int vl = (int)(idx / n);
                 const uint32_t k = (uint32_t)(idx - (int64_t)vl * n);
@@ -215,11 +218,19 @@ constexpr int SORT_WSEG = 32 * SORT_ITEMS;   // keys of one warp's segment
 // SORT_WSEG) of it, read lane-striped (item i of lane l is key i 32 + l), so
 // walking items in order and lanes in order visits the segment in key order.
 
+// n_dev (nullable): the number of keys to sort, read on the device (at most n;
+// the grid and the histogram layout follow n)
+__device__ __forceinline__ uint32_t sort_count(uint32_t n, const unsigned long long *n_dev)
+{
+    return n_dev ? (uint32_t)min((unsigned long long)n, *n_dev) : n;
+}
+
 __global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int shift,
-                            uint32_t *__restrict__ hist, uint32_t nb)
+                            uint32_t *__restrict__ hist, uint32_t nb, const unsigned long long *n_dev)
 {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
+    n = sort_count(n, n_dev);
     __syncthreads();
     // the tile as 16-byte loads (every load issued before the counting)
     const uint32_t base = blockIdx.x * SORT_TILE;
@@ -261,7 +272,8 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
                                                           uint32_t *__restrict__ okeys,
                                                           uint32_t *__restrict__ ovals, uint32_t n,
                                                           int shift, const uint32_t *__restrict__ hist,
-                                                          const uint32_t *__restrict__ offs, uint32_t nb)
+                                                          const uint32_t *__restrict__ offs, uint32_t nb,
+                                                          const unsigned long long *n_dev)
 {
     __shared__ uint32_t sk[SORT_TILE], sv[SORT_TILE];
     __shared__ uint32_t wcnt[SORT_WARPS][256];
@@ -270,6 +282,8 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t base = blockIdx.x * SORT_TILE;
     const uint32_t seg = base + w * SORT_WSEG;
+    n = sort_count(n, n_dev);
+    if (base >= n) return;   // uniform over the CTA: a tile past the keys to sort
     // every global load of the tile up front: keys, values, and the tile's
     // count and global offset of every digit
     uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
@@ -347,9 +361,10 @@ __global__ void __launch_bounds__(SORT_BS) k_sort_scatter(const uint32_t *__rest
 }
 
 __global__ void k_ranges(const uint32_t *__restrict__ keys, uint32_t n, uint2 *__restrict__ ranges,
-                         uint32_t n_tiles)
+                         uint32_t n_tiles, const unsigned long long *n_dev)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    n = sort_count(n, n_dev);
     if (i >= n) return;
     uint32_t k = keys[i] >> 8;   // tile id (the low byte is the position code)
     if (k >= n_tiles) return;    // never taken: emitted tile ids are < n_tiles
@@ -398,7 +413,8 @@ size_t sort_tmp_elems(uint32_t n)
 }
 
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt)
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt,
+                        const unsigned long long *n_dev)
 {
     if (in_alt) *in_alt = false;
     if (n == 0) return cudaSuccess;
@@ -414,10 +430,10 @@ cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint
     if (passes < 1) passes = 1;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_sort_hist<<<nb, SORT_BS, 0, s>>>(src_k, n, shift, hist, nb);
+        k_sort_hist<<<nb, SORT_BS, 0, s>>>(src_k, n, shift, hist, nb, n_dev);
         cudaError_t e = launch_scan(hist, offs, (int64_t)hn, stot, stmp, s);
         if (e != cudaSuccess) return e;
-        k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, offs, nb);
+        k_sort_scatter<<<nb, SORT_BS, 0, s>>>(src_k, src_v, dst_k, dst_v, n, shift, hist, offs, nb, n_dev);
         count_launches(2);
         uint32_t *tk = src_k, *tv = src_v;
         src_k = dst_k; src_v = dst_v; dst_k = tk; dst_v = tv;
@@ -434,10 +450,10 @@ cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint
 }
 
 cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
-                          cudaStream_t s)
+                          cudaStream_t s, const unsigned long long *n_dev)
 {
     if (n_keys == 0) return cudaSuccess;
-    k_ranges<<<(n_keys + 255) / 256, 256, 0, s>>>(keys, n_keys, ranges, n_tiles);
+    k_ranges<<<(n_keys + 255) / 256, 256, 0, s>>>(keys, n_keys, ranges, n_tiles, n_dev);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -81,8 +81,9 @@ cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n,
 cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
                         const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
                         uint32_t cap, uint32_t *overflow, cudaStream_t s);
+// n_dev (nullable): the number of sorted keys, read on the device (<= n_keys)
 cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
-                          cudaStream_t s);
+                          cudaStream_t s, const unsigned long long *n_dev = nullptr);
 
 // exclusive scan of n u32 values; writes out[0..n) and the 64-bit total to
 // *total (device).  tmp must hold scan_tmp_elems(n) u64.
@@ -95,9 +96,12 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
 // sort_tmp_elems(n) u32.
 size_t sort_tmp_elems(uint32_t n);
 // in_alt (nullable): set when the result is left in (keys_alt, vals_alt)
-// instead of being copied back (an odd number of passes)
+// instead of being copied back (an odd number of passes).  n_dev (nullable):
+// sort only the first min(n, *n_dev) keys, the count read on the device
+// (buffers and launches sized for n, e.g. inside a captured graph)
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt = nullptr);
+                        uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt = nullptr,
+                        const unsigned long long *n_dev = nullptr);
 
 // ker: kernel of the primitives (RGRT_KERNEL_GAUSSIAN / RGRT_KERNEL_EPANECHNIKOV)
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
