@@ -284,21 +284,24 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g,
 int rgrt_batch_destroy(rgrt_batch *b);
 
 /* Forward projection of every scan (binning of all scans, then one persistent
- * launch over every (scan, tile) work item; captured once in a CUDA graph and
- * replayed).  out_I[i] receives scan i's projection (host or device; null
+ * launch over every (scan, tile) work item of the scans too small to fill the
+ * GPU for 16 waves; a larger scan is projected right after its binning by a
+ * launch of its own.  Captured once in a CUDA graph and replayed).  out_I[i] receives scan i's projection (host or device; null
  * skips it).  Re-plans and repeats when the parameters have moved so far that
  * a scan's tile entries no longer fit.  Synchronises with `stream`. */
 int rgrt_batch_forward(rgrt_batch *b, float *const *out_I, void *stream);
 
 /* One optimisation step of every scan, as loss_step does for one: forward,
- * loss against y[i] (device arrays), adjoint (one persistent launch over all
- * scans), parameter chain and Adam (step t).  loss_out[n_scans] (host or
+ * loss against y[i] (device arrays), adjoint (the small scans: one persistent
+ * forward and one persistent adjoint launch over all of them; a large scan:
+ * binning, forward, loss and adjoint back to back, its lists still in L2),
+ * then the parameter chains and Adam (step t) of every scan.  loss_out[n_scans] (host or
  * device, may be null) receives the losses.  Captured in a CUDA graph that is
  * replayed while y, loss and hp stay the same.  Synchronises with `stream`. */
 int rgrt_batch_loss_step(rgrt_batch *b, const float *const *y, int loss, const rgrt_adam *hp, int t,
                          float *loss_out, void *stream);
 
-/* work items (tiles of all scans), planned key capacity, re-plans so far */
+/* tiles of all scans, planned key capacity, re-plans so far */
 int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans);
 
 /* Tile-shape autotuner: times project_forward + project_backward of g on

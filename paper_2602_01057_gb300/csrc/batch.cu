@@ -55,6 +55,7 @@ struct BatchScan {
     int64_t N = 0, R = 0, E = 0;
     uint32_t T = 0, cap = 0;
     int bits = 0, nblk = 1;
+    bool large = false;         // projected by its own launches (not the persistent ones)
     uint32_t *vals = nullptr;   // sorted Gaussian ids [cap]
     uint2 *ranges = nullptr;    // [T]
     float *I = nullptr, *dLdI = nullptr;
@@ -88,7 +89,9 @@ struct rgrt_batch {
     uint32_t *d_queue = nullptr, *d_overflow = nullptr;
     float *d_loss = nullptr, *d_bc = nullptr;
     float *h_pin = nullptr;       // pinned: [2] bias corrections, [n] losses, [1] overflow bits
-    uint32_t total_items = 0;
+    uint32_t total_items = 0;     // work items of the persistent launches (small scans)
+    uint64_t all_tiles = 0;       // tiles of every scan
+    int n_small = 0;              // scans in the persistent descriptor table
     int grid_f = 0, grid_a = 0;
     uint64_t keys_capacity = 0;
     // graphs
@@ -173,12 +176,23 @@ int plan(rgrt_batch *b)
     BTRY(balloc(b, (void **)&b->keys_alt, sizeof(uint32_t) * capmax));
     BTRY(balloc(b, (void **)&b->vals_alt, sizeof(uint32_t) * capmax));
     BTRY(balloc(b, (void **)&b->sort_tmp, sizeof(uint32_t) * sort_tmp_elems(capmax)));
-    // work items, scan by scan
-    std::vector<ScanDesc> hd(b->n);
+    b->grid_f = persistent_grid(true, b->cone, b->tile_w, b->tile_w * b->tile_h);
+    b->grid_a = persistent_grid(false, b->cone, b->tile_w, b->tile_w * b->tile_h);
+    // A scan whose tiles fill the GPU for 16 waves or more gains nothing from
+    // sharing the persistent launches: it is binned, projected, and its loss
+    // and adjoint taken back to back with launches of its own, while its
+    // lists and records are still in L2.  The others share the persistent
+    // launches (work items, scan by scan).
+    std::vector<ScanDesc> hd;
     uint64_t items = 0;
+    b->all_tiles = 0;
     for (int i = 0; i < b->n; i++) {
         BatchScan &x = b->sc[i];
-        ScanDesc &d = hd[i];
+        b->all_tiles += x.T;
+        x.large = (int64_t)x.T >= 16 * (int64_t)b->grid_f;
+        if (x.large) continue;
+        hd.emplace_back();
+        ScanDesc &d = hd.back();
         d.g = x.geom->dg;
         d.g.v0 = 0;
         d.rec = x.g->rec;
@@ -194,22 +208,22 @@ int plan(rgrt_batch *b)
     }
     if (items >= 0xffffffffull) return report_error(RGRT_E_CAPACITY, "too many tiles in the batch");
     b->total_items = (uint32_t)items;
-    BTRY(balloc(b, (void **)&b->d_desc, sizeof(ScanDesc) * b->n));
-    BK(cudaMemcpyAsync(b->d_desc, hd.data(), sizeof(ScanDesc) * b->n, cudaMemcpyHostToDevice, s));
+    b->n_small = (int)hd.size();
+    BTRY(balloc(b, (void **)&b->d_desc, sizeof(ScanDesc) * std::max<size_t>(hd.size(), 1)));
+    if (!hd.empty())
+        BK(cudaMemcpyAsync(b->d_desc, hd.data(), sizeof(ScanDesc) * hd.size(), cudaMemcpyHostToDevice, s));
     BTRY(balloc(b, (void **)&b->d_queue, sizeof(uint32_t) * 2));
     BTRY(balloc(b, (void **)&b->d_overflow, sizeof(uint32_t)));
     BTRY(balloc(b, (void **)&b->d_loss, sizeof(float) * b->n));
     BTRY(balloc(b, (void **)&b->d_bc, sizeof(float) * 2));
     BK(cudaStreamSynchronize(s));
-    b->grid_f = persistent_grid(true, b->cone, b->tile_w, b->tile_w * b->tile_h);
-    b->grid_a = persistent_grid(false, b->cone, b->tile_w, b->tile_w * b->tile_h);
     return RGRT_OK;
 }
 
-// binning of every scan into its own sorted id list and tile ranges
-int enqueue_binning(rgrt_batch *b, cudaStream_t s)
+// binning of scan i into its own sorted id list and tile ranges
+int enqueue_bin_scan(rgrt_batch *b, int i, cudaStream_t s)
 {
-    for (int i = 0; i < b->n; i++) {
+    {
         BatchScan &x = b->sc[i];
         DevGeom dg = x.geom->dg;
         dg.v0 = 0;
@@ -230,28 +244,69 @@ int enqueue_binning(rgrt_batch *b, cudaStream_t s)
     return RGRT_OK;
 }
 
+// forward of a large scan with launches of its own (all its views at once)
+int enqueue_forward_large(rgrt_batch *b, int i, cudaStream_t s)
+{
+    BatchScan &x = b->sc[i];
+    DevGeom dg = x.geom->dg;
+    dg.v0 = 0;
+    BK(launch_forward(dg, dg.n_views, x.g->rec, x.g->crec, x.vals, x.ranges, x.I, nullptr,
+                      RGRT_KERNEL_GAUSSIAN, s));
+    return RGRT_OK;
+}
+
 int enqueue_forward(rgrt_batch *b, cudaStream_t s)
 {
     BK(cudaMemsetAsync(b->d_overflow, 0, sizeof(uint32_t), s));
-    BTRY(enqueue_binning(b, s));
-    BK(cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), s));
-    BK(launch_forward_persistent(b->cone, b->d_desc, b->n, b->total_items, b->d_queue,
-                                 b->tile_w * b->tile_h, b->grid_f, s));
+    for (int i = 0; i < b->n; i++) {
+        BTRY(enqueue_bin_scan(b, i, s));
+        if (b->sc[i].large) BTRY(enqueue_forward_large(b, i, s));
+    }
+    if (b->n_small > 0) {
+        BK(cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), s));
+        BK(launch_forward_persistent(b->cone, b->d_desc, b->n_small, b->total_items, b->d_queue,
+                                     b->tile_w * b->tile_h, b->grid_f, s));
+    }
+    return RGRT_OK;
+}
+
+int enqueue_loss(rgrt_batch *b, int i, const float *const *y, int loss, const rgrt_adam *hp, cudaStream_t s)
+{
+    BatchScan &x = b->sc[i];
+    BK(launch_loss(loss, x.I, y[i], x.R, hp->kappa, hp->poisson_eps, x.geom->d_mult, x.geom->d_add,
+                   x.dLdI, x.partial, x.nblk, b->d_loss + i, s));
+    BK(cudaMemsetAsync(x.grad, 0, sizeof(float4) * GRAD_F4 * (size_t)std::max<int64_t>(x.N, 1), s));
     return RGRT_OK;
 }
 
 int enqueue_step(rgrt_batch *b, const float *const *y, int loss, const rgrt_adam *hp, cudaStream_t s)
 {
-    BTRY(enqueue_forward(b, s));
+    BK(cudaMemsetAsync(b->d_overflow, 0, sizeof(uint32_t), s));
+    // large scans: binning, forward, loss and adjoint back to back
     for (int i = 0; i < b->n; i++) {
+        BTRY(enqueue_bin_scan(b, i, s));
         BatchScan &x = b->sc[i];
-        BK(launch_loss(loss, x.I, y[i], x.R, hp->kappa, hp->poisson_eps, x.geom->d_mult, x.geom->d_add,
-                       x.dLdI, x.partial, x.nblk, b->d_loss + i, s));
-        BK(cudaMemsetAsync(x.grad, 0, sizeof(float4) * GRAD_F4 * (size_t)std::max<int64_t>(x.N, 1), s));
+        if (!x.large) continue;
+        BTRY(enqueue_forward_large(b, i, s));
+        BTRY(enqueue_loss(b, i, y, loss, hp, s));
+        DevGeom dg = x.geom->dg;
+        dg.v0 = 0;
+        BK(launch_adjoint(dg, dg.n_views, x.g->rec, x.g->crec, x.vals, x.ranges, x.dLdI, x.grad,
+                          RGRT_KERNEL_GAUSSIAN, s));
     }
-    BK(cudaMemsetAsync(b->d_queue + 1, 0, sizeof(uint32_t), s));
-    BK(launch_adjoint_persistent(b->cone, b->tile_w, b->d_desc, b->n, b->total_items, b->d_queue + 1,
-                                 b->grid_a, s));
+    // small scans: one persistent forward and one persistent adjoint
+    if (b->n_small > 0) {
+        BK(cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), s));
+        BK(launch_forward_persistent(b->cone, b->d_desc, b->n_small, b->total_items, b->d_queue,
+                                     b->tile_w * b->tile_h, b->grid_f, s));
+        for (int i = 0; i < b->n; i++)
+            if (!b->sc[i].large) BTRY(enqueue_loss(b, i, y, loss, hp, s));
+        BK(cudaMemsetAsync(b->d_queue + 1, 0, sizeof(uint32_t), s));
+        BK(launch_adjoint_persistent(b->cone, b->tile_w, b->d_desc, b->n_small, b->total_items,
+                                     b->d_queue + 1, b->grid_a, s));
+    }
+    // parameter chains and Adam last: an overflow flagged by any scan's
+    // binning skips every update
     for (int i = 0; i < b->n; i++) {
         BatchScan &x = b->sc[i];
         if (x.N == 0) continue;
@@ -546,7 +601,7 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
 int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans)
 {
     if (!b) return report_error(RGRT_E_INVAL, "null batch");
-    if (work_items) *work_items = b->total_items;
+    if (work_items) *work_items = (int64_t)b->all_tiles;
     if (key_capacity) *key_capacity = (int64_t)b->keys_capacity;
     if (replans) *replans = b->replans;
     return RGRT_OK;

@@ -111,6 +111,49 @@ def test_batch_loss_step_matches_single_scans(env):
             assert np.linalg.norm(da - dc) <= 1e-3 * np.linalg.norm(dc) + 1e-7, (i, k)
 
 
+def test_batch_with_large_and_small_scans(env):
+    """A scan large enough to fill the GPU for many waves (40 views of 256^2,
+    10,240 tiles of 16 x 16) is projected with launches of its own inside the
+    batch; the small ones share the persistent launches.  Forward and three
+    optimisation steps against single-scan calls."""
+    torch, rg, ctx = env
+    G, _ = synth.workload_c2(31, n=5000, n_views=40, side=256)
+    scans = [(G, synth.geom_c2(n_views=40, side=256))] + _scans(4, 3)
+    gb = [rg.Gaussians(ctx, *_dev(torch, G)) for G, _ in scans]
+    gsingle = [rg.Gaussians(ctx, *_dev(torch, G)) for G, _ in scans]
+    geoms = [rg.Geometry(ctx, gd) for _, gd in scans]
+    b = rg.Batch(ctx, gb, geoms)
+    outs = [torch.empty(g.n_rays, device="cuda") for g in geoms]
+    b.forward(outs)
+    for g, geom, o in zip(gsingle, geoms, outs):
+        ref = torch.empty(geom.n_rays, device="cuda")
+        rg.project_forward(ctx, g, geom, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref)
+    hp = rg.adam_params()
+    ys = []
+    for (G, gd), geom in zip(scans, geoms):
+        gt = rg.Gaussians(ctx, *_dev(torch, synth.perturbed(G, 9, pos_std=0.01)))
+        y = torch.empty(geom.n_rays, device="cuda")
+        rg.project_forward(ctx, gt, geom, y)
+        ys.append(y)
+    for t in (1, 2, 3):
+        lb = b.loss_step(ys, rg.RGRT_LOSS_L2, hp, t)
+        for i in range(len(scans)):
+            ls = np.zeros(1, np.float32)
+            rg.loss_step(ctx, gsingle[i], geoms[i], ys[i], rg.RGRT_LOSS_L2, hp, t, ls)
+            assert lb[i] == pytest.approx(float(ls[0]), rel=1e-5, abs=1e-12)
+    for i in range(len(scans)):
+        a, c = gb[i].numpy(), gsingle[i].numpy()
+        for k in ("mu", "ls", "q", "rho"):
+            G0 = scans[i][0][k]
+            da = a[k].astype(np.float64) - G0
+            dc = c[k].astype(np.float64) - G0
+            assert np.linalg.norm(da - dc) <= 1e-3 * np.linalg.norm(dc) + 1e-7, (i, k)
+    assert b.info()["work_items"] == sum(g.n_rays // 256 for g in geoms[:1]) + sum(
+        (gd["n_views"] * ((gd["n_cols"] + 15) // 16) * ((gd["n_rows"] + 15) // 16)) for _, gd in scans[1:])
+
+
 def test_batch_replans_when_entries_outgrow_capacity(env):
     torch, rg, ctx = env
     scans = _scans(3, 3)
