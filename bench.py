@@ -65,6 +65,9 @@ WORKLOADS = {
              "past each segment's last ring pair)",
     "pet3d-rays": "the LORs of pet3d as explicit rays (geometry_set_rays, no detector structure), fwd+bwd "
                   "(Poisson NLL + Adam)",
+    "helical": "helical cone-beam CT as explicit rays (geometry_set_rays): the 50,000 Gaussians of the "
+               "cone-beam workload, one turn of 180 views x 256x256 (source-origin 1000 mm, source-detector "
+               "1500 mm, 128 mm feed per turn), fwd+bwd (L2 + Adam)",
     "points": "arc vs raw radial sampling (a synthetic analogue of the three-point-source study): 1 mm "
               "spheres at (0, 10), (0, 100), (0, 200) mm in the C3 ring (5 planes 2 mm apart), 5M Poisson "
               "counts sampled at raw crystal-pair positions; reconstructed (L2 + Adam, blind 4 mm grid of "
@@ -952,29 +955,48 @@ def run_points(args):
 def run_pet3d(args):
     """The LORs of the 3-D PET workload through the explicit-ray path: rays/s
     of a full step."""
+    G, _ = synth.workload_c3(0)
+    run_explicit(args, "pet3d-rays", G, synth.pet_rays_3d(max_ring_diff=5), "poisson", pos_std=1.0,
+                 note="explicit-ray path (no detector structure): the binning tests every Gaussian against "
+                      "every 128-ray block")
+
+
+def run_helical(args):
+    """Helical cone-beam CT through the explicit-ray path: the cone-beam
+    workload's Gaussians, one turn of 180 views of 256 x 256, rays/s of a
+    full step."""
+    G, gd = synth.workload_c2(0)
+    R = synth.rays_helical(180, 256, 256, gd["pitch_u"], gd["dso"], gd["dsd"], z_per_turn=1.0)
+    run_explicit(args, "helical", G, R, "l2", pos_std=0.01,
+                 note="explicit-ray path: 128 consecutive rays (half a detector row) per block")
+
+
+def run_explicit(args, name, G, R, loss, pos_std, note):
     import torch
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
-    G, _ = synth.workload_c3(0)
     G = _params(G)
-    R = synth.pet_rays_3d(max_ring_diff=5)
     n_rays = R["o"].shape[0]
     ctx = rgrt.Context(0)
     geom = rgrt.Geometry(ctx, R)
-    true = synth.perturbed(G, 101, pos_std=1.0)
+    true = synth.perturbed(G, 101, pos_std=pos_std)
     gt = rgrt.Gaussians(ctx, *[torch.from_numpy(true[k]).cuda() for k in ("mu", "ls", "q", "rho")])
     ytrue = torch.empty(n_rays, device="cuda")
     rgrt.project_forward(ctx, gt, geom, ytrue)
     gt.close()
-    kappa = 1e8 / float(ytrue.sum())
-    y = torch.poisson(kappa * ytrue, generator=torch.Generator(device="cuda").manual_seed(7))
-    hp = rgrt.adam_params(kappa=kappa, poisson_eps=1e-9 * float((kappa * ytrue).max()))
+    if loss == "poisson":
+        kappa = 1e8 / float(ytrue.sum())
+        y = torch.poisson(kappa * ytrue, generator=torch.Generator(device="cuda").manual_seed(7))
+        hp = rgrt.adam_params(kappa=kappa, poisson_eps=1e-9 * float((kappa * ytrue).max()))
+        lkind = rgrt.RGRT_LOSS_POISSON
+    else:
+        y, hp, lkind = ytrue, rgrt.adam_params(), rgrt.RGRT_LOSS_L2
     gs = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).cuda() for k in ("mu", "ls", "q", "rho")])
     lo = torch.zeros(1, device="cuda")
     step = 0
     for _ in range(args.warmup):
         step += 1
-        rgrt.loss_step(ctx, gs, geom, y, rgrt.RGRT_LOSS_POISSON, hp, step, lo)
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, lo)
     torch.cuda.synchronize()
     ctx.prof_enable(True)
     ctx.prof_reset()
@@ -986,25 +1008,23 @@ def run_pet3d(args):
     for k in range(args.steps):
         ev[k][0].record(stream)
         step += 1
-        rgrt.loss_step(ctx, gs, geom, y, rgrt.RGRT_LOSS_POISSON, hp, step, lo)
+        rgrt.loss_step(ctx, gs, geom, y, lkind, hp, step, lo)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     launches = rgrt.launch_count() - l0
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     kernels = {}
-    for name in ("k_records", "rays_bin", "rays_emit", "k_rays_forward", "k_loss", "k_rays_adjoint",
-                 "k_param_chain", "k_adam"):
-        nk, t = ctx.prof_get(name)
-        kernels[name] = dict(launches=nk, ms=t)
+    for kname in ("k_records", "rays_bin", "rays_emit", "k_rays_forward", "k_loss", "k_rays_adjoint",
+                  "k_param_chain", "k_adam"):
+        nk, t = ctx.prof_get(kname)
+        kernels[kname] = dict(launches=nk, ms=t)
     line = dict(metric=METRIC, value=n_rays / (ms / 1e3), unit=UNIT, n_gpus=1, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOADS["pet3d-rays"], rays_per_step=n_rays, gaussians=int(G["mu"].shape[0]),
+                config=dict(workload=WORKLOADS[name], rays_per_step=n_rays, gaussians=int(G["mu"].shape[0]),
                             l2="not flushed: the step's working set is far above L2"),
-                kernels=kernels, keys_per_step=None, gpu_launches=launches, roofline=None,
-                note="explicit-ray path (no detector structure): the binning tests every Gaussian against "
-                     "every 128-ray block", e2e=None)
+                kernels=kernels, keys_per_step=None, gpu_launches=launches, roofline=None, note=note, e2e=None)
     if clk:
         line["clocks"] = clk
     print(json.dumps(line), flush=True)
@@ -1024,6 +1044,8 @@ def main():
         run_recon(args)
     elif args.workload == "pet3d-rays":
         run_pet3d(args)
+    elif args.workload == "helical":
+        run_helical(args)
     elif args.workload == "points":
         run_points(args)
     else:
