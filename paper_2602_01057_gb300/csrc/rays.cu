@@ -29,9 +29,12 @@ constexpr int RB = 128;    // rays per block
 constexpr int RCH = 128;   // records per shared-memory chunk
 constexpr int CULL_BS = 256;
 constexpr int NG_RAYS = 10;  // general_grad components: dmu[3], G_P[6], drho
+// bounding-ball radius factor: K sigma_max with K^2 the culling constant (a
+// margin over the 3-sigma cut), widened by a few ulp for the FP32 tests
+#define BALL_K (3.0103986f * (1.0f + 1e-5f))
 
 struct SRec {
-    float4 g0, g1, g2;     // (mu, rho), (P00 P01 P02 P11), (P12 P22, -, -)
+    float4 g0, g1, g2;     // (mu, rho), (P00 P01 P02 P11), (P12 P22, id, bounding-ball radius)
 };
 
 __device__ __forceinline__ float3 cross3(float3 a, float3 b)
@@ -83,7 +86,7 @@ __global__ void k_balls(const float4 *__restrict__ rec, int64_t n, float4 *ball,
 {
     __shared__ float red[6][CULL_BS / 32];
     float lo[3] = { INFINITY, INFINITY, INFINITY }, hi[3] = { -INFINITY, -INFINITY, -INFINITY };
-    const float K = sqrtf(CULL_K2) * (1.0f + 1e-5f);
+    const float K = BALL_K;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const float4 m = __ldg(rec + REC_F4 * k);
@@ -361,7 +364,8 @@ __global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict_
     }
 }
 
-// a warp stages up to 32 records of its own list (lane i: entry beg + i)
+// a warp stages up to 32 records of its own list (lane i: entry beg + i):
+// mu, rho, P, the id and the radius K sigma_max of the bounding ball
 __device__ __forceinline__ void stage_warp(const float4 *__restrict__ rec,
                                            const uint32_t *__restrict__ gids, uint32_t beg, int cnt,
                                            int lane, SRec *sr)
@@ -372,9 +376,20 @@ __device__ __forceinline__ void stage_warp(const float4 *__restrict__ rec,
         const float4 r2 = __ldg(r + 2);
         sr[lane].g0 = __ldg(r);
         sr[lane].g1 = __ldg(r + 1);
-        sr[lane].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), 0.0f);
+        sr[lane].g2 = make_float4(r2.x, r2.y, __uint_as_float(gid), BALL_K * __ldg(r + 4).x);
     }
     __syncwarp();
+}
+
+// Does the lane's line pass within the bounding ball (mu, rb) of a staged
+// record?  A pair with m <= 9 has its line within 3 sigma_max of mu, inside
+// the ball (K = 3.0104 sigma_max): a warp skips a record no lane's line meets
+// before the closed form is evaluated.
+__device__ __forceinline__ bool line_meets_ball(const Ray &ray, const SRec &s)
+{
+    const float ex = s.g0.x - ray.ox, ey = s.g0.y - ray.oy, ez = s.g0.z - ray.oz;
+    const float cx = ey * ray.dz - ez * ray.dy, cy = ez * ray.dx - ex * ray.dz, cz = ex * ray.dy - ey * ray.dx;
+    return cx * cx + cy * cy + cz * cz <= s.g2.w * s.g2.w;
 }
 
 
@@ -411,6 +426,7 @@ __global__ void __launch_bounds__(RB) k_rays_forward(const float4 *__restrict__ 
         __syncwarp();
         stage_warp(rec, gids, c, cnt, lane, sr);
         for (int i = 0; i < cnt; i++) {
+            if (!__any_sync(0xffffffffu, valid && line_meets_ball(ray, sr[i]))) continue;
             PairGeo q;
             pair_geo(ray, sr[i], q);
             if (q.m <= PAIR_CUT2) acc += general_value<KER>(q, sr[i].g0.w, tf.x, tf.y);
@@ -447,6 +463,7 @@ __global__ void __launch_bounds__(RB) k_rays_adjoint(const float4 *__restrict__ 
         __syncwarp();
         stage_warp(rec, gids, c, cnt, lane, sr);
         for (int i = 0; i < cnt; i++) {
+            if (!__any_sync(0xffffffffu, valid && wgt != 0.0f && line_meets_ball(ray, sr[i]))) continue;
             PairGeo q;
             pair_geo(ray, sr[i], q);
             const bool act = valid && wgt != 0.0f && q.m <= PAIR_CUT2;
