@@ -370,11 +370,12 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
     TRY(ensure(ctx, ctx->ranges, sizeof(uint2) * TL));
     TRY(ensure(ctx, ctx->scan_tmp, sizeof(unsigned long long) * scan_tmp_elems((int64_t)TL)));
     TRY(ensure(ctx, ctx->total, sizeof(unsigned long long) * 2));
+    TRY(ensure(ctx, ctx->clusters, rays_cluster_bytes(N)));
     {
         PROF("rays_bin");
         CK(launch_rays_bin(geom->d_ro, geom->d_rd, geom->n_rays, g->rec, N, (float4 *)ctx->ball.p,
                            (float4 *)ctx->part.p, (float4 *)ctx->scene.p, (float4 *)ctx->blk.p,
-                           (float4 *)ctx->wblk.p, (uint32_t *)ctx->cnt.p, s));
+                           (float4 *)ctx->wblk.p, ctx->clusters.p, (uint32_t *)ctx->cnt.p, s));
     }
     ctx->h_cnt.resize(TL);
     CK(cudaMemcpyAsync(ctx->h_cnt.data(), ctx->cnt.p, sizeof(uint32_t) * TL, cudaMemcpyDeviceToHost, s));
@@ -421,9 +422,8 @@ int for_ray_ranges(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cu
             CK(launch_scan((const uint32_t *)ctx->cnt.p + (size_t)r.first * RAYS_WPB, (uint32_t *)ctx->off.p,
                            (int64_t)r.second * RAYS_WPB, (unsigned long long *)ctx->total.p,
                            (unsigned long long *)ctx->scan_tmp.p, s));
-            CK(launch_rays_emit((const float4 *)ctx->blk.p, (const float4 *)ctx->wblk.p,
-                                (const float4 *)ctx->ball.p, N, r.first, r.second,
-                                (const uint32_t *)ctx->off.p, (const uint32_t *)ctx->cnt.p,
+            CK(launch_rays_emit((const float4 *)ctx->blk.p, (const float4 *)ctx->wblk.p, ctx->clusters.p, N,
+                                r.first, r.second, (const uint32_t *)ctx->off.p, (const uint32_t *)ctx->cnt.p,
                                 (uint32_t *)ctx->vals.p, (uint2 *)ctx->ranges.p, s));
         }
         if (rng.size() == 1) {
@@ -721,7 +721,7 @@ int rgrt_ctx_destroy(rgrt_ctx *c)
     Buf *bufs[] = { &c->cnt, &c->off, &c->rect, &c->keys, &c->vals, &c->keys_alt, &c->vals_alt,
                     &c->sort_tmp, &c->scan_tmp, &c->ranges, &c->total, &c->I, &c->dLdI, &c->y,
                     &c->grad, &c->gflat, &c->partial, &c->stats, &c->loss, &c->loss_acc, &c->ball, &c->part,
-                    &c->scene, &c->blk, &c->wblk };
+                    &c->scene, &c->blk, &c->wblk, &c->clusters };
     for (Buf *b : bufs) release(c, *b);
     for (auto &b : c->stage_in) release(c, b);
     for (auto &b : c->stage_out) release(c, b);

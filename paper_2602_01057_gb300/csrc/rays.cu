@@ -267,54 +267,156 @@ __device__ __forceinline__ bool block_hit(const float4 P, const float4 D, const 
 constexpr int WPB = RB / 32;   // warps (and lists) per ray block
 static_assert(WPB == RAYS_WPB, "one list per warp of a ray block");
 
+// ---- two-level cull: clusters of 32 bounding balls along a Morton curve ----
+//
+// The balls are sorted by the Morton code of their centres in the scene box;
+// every 32 consecutive sorted balls form a cluster, bounded by a ball holding
+// all of them (centre: the middle of their box, radius: the largest distance
+// from it to a member's far side, widened by the scene's FP32 slack).  A
+// member ball that meets a block's cylinder lies inside its cluster's ball,
+// so the cluster meets it too: a ray block tests the clusters and then only
+// the members of the clusters it meets.  Lists come out in cluster order and,
+// within a cluster, in member order -- the same order in the count and the
+// emit pass.
+constexpr int CL = 32;         // balls per cluster
+constexpr int BIN_BS = 128;    // one warp per ray block in the count and emit kernels
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 1023u;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(const float4 *__restrict__ ball, int64_t n, const float4 *__restrict__ scene,
+                         uint32_t *code, uint32_t *perm)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 lo = scene[0], hi = scene[1], b = ball[k];
+    const float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
+    const float fx = ex > 0.0f ? (b.x - lo.x) / ex : 0.0f;
+    const float fy = ey > 0.0f ? (b.y - lo.y) / ey : 0.0f;
+    const float fz = ez > 0.0f ? (b.z - lo.z) / ez : 0.0f;
+    const uint32_t qx = (uint32_t)fminf(fmaxf(fx * 1023.0f, 0.0f), 1023.0f);
+    const uint32_t qy = (uint32_t)fminf(fmaxf(fy * 1023.0f, 0.0f), 1023.0f);
+    const uint32_t qz = (uint32_t)fminf(fmaxf(fz * 1023.0f, 0.0f), 1023.0f);
+    code[k] = spread10(qx) | (spread10(qy) << 1) | (spread10(qz) << 2);
+    perm[k] = (uint32_t)k;
+}
+
+// one warp per cluster: the sorted balls and ids, and the cluster ball
+__global__ void k_clusters(const float4 *__restrict__ ball, const uint32_t *__restrict__ perm, int64_t n,
+                           int64_t nc, const float4 *__restrict__ scene, float4 *sball, uint32_t *sgid,
+                           float4 *cball)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= nc) return;
+    const int64_t j = c * CL + lane;
+    const bool valid = j < n;
+    const uint32_t gid = valid ? __ldg(perm + j) : 0u;
+    const float4 b = valid ? __ldg(ball + gid) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (valid) {
+        sball[j] = b;
+        sgid[j] = gid;
+    }
+    float lo[3] = { valid ? b.x - b.w : INFINITY, valid ? b.y - b.w : INFINITY, valid ? b.z - b.w : INFINITY };
+    float hi[3] = { valid ? b.x + b.w : -INFINITY, valid ? b.y + b.w : -INFINITY, valid ? b.z + b.w : -INFINITY };
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]), cz = 0.5f * (lo[2] + hi[2]);
+    float r = 0.0f;
+    if (valid) {
+        const float dx = b.x - cx, dy = b.y - cy, dz = b.z - cz;
+        r = sqrtf(dx * dx + dy * dy + dz * dz) + b.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) cball[c] = make_float4(cx, cy, cz, r * (1.0f + 2e-5f) + scene[0].w);
+}
+
+// Visit, in order, the members of the clusters that ray block (P, D) meets:
+// visit(j, ball, hit) runs on every lane for every member slot j of such a
+// cluster (hit: the slot holds a ball that passes the block's bound).
+template <class F>
+__device__ __forceinline__ void walk_clusters(const float4 P, const float4 D, const float4 *__restrict__ cball,
+                                              const float4 *__restrict__ sball, int64_t n, int64_t nc,
+                                              int lane, F visit)
+{
+    for (int64_t cb = 0; cb < nc; cb += 32) {
+        const int64_t ci = cb + lane;
+        const bool hc = ci < nc && block_hit(P, D, __ldg(cball + ci));
+        uint32_t m = __ballot_sync(0xffffffffu, hc);
+        while (m) {
+            const int64_t c = cb + (__ffs(m) - 1);
+            m &= m - 1u;
+            const int64_t j = c * CL + lane;
+            const bool valid = j < n;
+            const float4 bl = valid ? __ldg(sball + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            visit(j, bl, valid && block_hit(P, D, bl));
+        }
+    }
+}
+
 // per block: how many Gaussians pass the block's bound and then each warp's
 // bound; cnt[WPB b + w] = the length of warp w's list
-__global__ void __launch_bounds__(CULL_BS) k_rays_count(const float4 *__restrict__ blk,
-                                                        const float4 *__restrict__ wblk,
-                                                        const float4 *__restrict__ ball, int64_t n,
-                                                        uint32_t *cnt)
+__global__ void __launch_bounds__(BIN_BS) k_rays_count(const float4 *__restrict__ blk,
+                                                       const float4 *__restrict__ wblk,
+                                                       const float4 *__restrict__ cball,
+                                                       const float4 *__restrict__ sball, int64_t n,
+                                                       int64_t nc, int64_t T, uint32_t *cnt)
 {
-    __shared__ uint32_t s_c[WPB][CULL_BS / 32];
-    const float4 P = blk[2 * blockIdx.x], D = blk[2 * blockIdx.x + 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * BIN_BS + threadIdx.x) >> 5;
+    if (b >= T) return;
+    const float4 P = blk[2 * b], D = blk[2 * b + 1];
     float4 wP[WPB], wD[WPB];
 #pragma unroll
     for (int w = 0; w < WPB; w++) {
-        wP[w] = wblk[2 * ((size_t)blockIdx.x * WPB + w)];
-        wD[w] = wblk[2 * ((size_t)blockIdx.x * WPB + w) + 1];
+        wP[w] = wblk[2 * ((size_t)b * WPB + w)];
+        wD[w] = wblk[2 * ((size_t)b * WPB + w) + 1];
     }
     uint32_t c[WPB] = {};
     if (D.w != 0.0f)
-        for (int64_t k = threadIdx.x; k < n; k += CULL_BS) {
-            const float4 bl = __ldg(ball + k);
-            if (!block_hit(P, D, bl)) continue;
+        walk_clusters(P, D, cball, sball, n, nc, lane, [&](int64_t j, float4 bl, bool hit) {
+            (void)j;
+            if (hit) {
 #pragma unroll
-            for (int w = 0; w < WPB; w++) c[w] += wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
-        }
+                for (int w = 0; w < WPB; w++) c[w] += wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
+            }
+        });
 #pragma unroll
     for (int w = 0; w < WPB; w++) {
         uint32_t v = c[w];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) s_c[w][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < WPB) {
-        uint32_t t = 0;
-        for (int j = 0; j < CULL_BS / 32; j++) t += s_c[threadIdx.x][j];
-        cnt[(size_t)blockIdx.x * WPB + threadIdx.x] = t;
+        if (lane == w) cnt[(size_t)b * WPB + w] = v;
     }
 }
 
-// blocks b0 .. b0 + gridDim.x - 1; off[] (per warp list) relative to the range;
-// every list in ascending Gaussian order
-__global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict__ blk,
-                                                       const float4 *__restrict__ wblk,
-                                                       const float4 *__restrict__ ball, int64_t n,
-                                                       int64_t b0, const uint32_t *__restrict__ off,
-                                                       const uint32_t *__restrict__ cnt,
-                                                       uint32_t *gids, uint2 *ranges)
+// blocks b0 .. b0 + nb - 1; off[] (per warp list) relative to the range
+__global__ void __launch_bounds__(BIN_BS) k_rays_emit(const float4 *__restrict__ blk,
+                                                      const float4 *__restrict__ wblk,
+                                                      const float4 *__restrict__ cball,
+                                                      const float4 *__restrict__ sball,
+                                                      const uint32_t *__restrict__ sgid, int64_t n,
+                                                      int64_t nc, int64_t b0, int64_t nb,
+                                                      const uint32_t *__restrict__ off,
+                                                      const uint32_t *__restrict__ cnt,
+                                                      uint32_t *gids, uint2 *ranges)
 {
-    __shared__ uint32_t s_w[WPB][CULL_BS / 32];
-    const int64_t b = b0 + blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t bi = ((int64_t)blockIdx.x * BIN_BS + threadIdx.x) >> 5;   // block within the range
+    if (bi >= nb) return;
+    const int64_t b = b0 + bi;
     const float4 P = blk[2 * b], D = blk[2 * b + 1];
     float4 wP[WPB], wD[WPB];
     uint32_t beg[WPB], num[WPB], pos[WPB], total_num = 0;
@@ -322,46 +424,25 @@ __global__ void __launch_bounds__(CULL_BS) k_rays_emit(const float4 *__restrict_
     for (int w = 0; w < WPB; w++) {
         wP[w] = wblk[2 * ((size_t)b * WPB + w)];
         wD[w] = wblk[2 * ((size_t)b * WPB + w) + 1];
-        beg[w] = off[(size_t)blockIdx.x * WPB + w];
+        beg[w] = off[(size_t)bi * WPB + w];
         num[w] = cnt[(size_t)b * WPB + w];
         pos[w] = beg[w];
         total_num += num[w];
     }
-    if (threadIdx.x < WPB)
-        ranges[(size_t)blockIdx.x * WPB + threadIdx.x] = make_uint2(beg[threadIdx.x], beg[threadIdx.x] + num[threadIdx.x]);
+    if (lane < WPB) ranges[(size_t)bi * WPB + lane] = make_uint2(beg[lane], beg[lane] + num[lane]);
     if (D.w == 0.0f || total_num == 0) return;
-    const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    for (int64_t base = 0; base < n; base += CULL_BS) {
-        const int64_t k = base + threadIdx.x;
-        bool h[WPB] = {};
-        if (k < n) {
-            const float4 bl = __ldg(ball + k);
-            if (block_hit(P, D, bl)) {
-#pragma unroll
-                for (int w = 0; w < WPB; w++) h[w] = wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
-            }
-        }
-        uint32_t bal[WPB];
+    walk_clusters(P, D, cball, sball, n, nc, lane, [&](int64_t j, float4 bl, bool hit) {
+        const uint32_t gid = hit ? __ldg(sgid + j) : 0u;
 #pragma unroll
         for (int w = 0; w < WPB; w++) {
-            bal[w] = __ballot_sync(0xffffffffu, h[w]);
-            if (lane == 0) s_w[w][cw] = __popc(bal[w]);
+            const bool h = hit && wD[w].w != 0.0f && block_hit(wP[w], wD[w], bl);
+            const uint32_t bal = __ballot_sync(0xffffffffu, h);
+            const uint32_t at = pos[w] + __popc(bal & lt);
+            if (h && at < beg[w] + num[w]) gids[at] = gid;
+            pos[w] += __popc(bal);
         }
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < WPB; w++) {
-            uint32_t before = 0, total = 0;
-            for (int j = 0; j < CULL_BS / 32; j++) {
-                before += j < cw ? s_w[w][j] : 0u;
-                total += s_w[w][j];
-            }
-            const uint32_t at = pos[w] + before + __popc(bal[w] & lt);
-            if (h[w] && at < beg[w] + num[w]) gids[at] = (uint32_t)k;
-            pos[w] += total;
-        }
-        __syncthreads();
-    }
+    });
 }
 
 // a warp stages up to 32 records of its own list (lane i: entry beg + i):
@@ -503,26 +584,68 @@ int rays_ball_parts(int64_t n)
     return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
 }
 
+namespace {
+struct ClusterBufs {
+    uint32_t *code, *perm, *code_alt, *perm_alt, *tmp, *sgid;
+    float4 *sball, *cball;
+};
+ClusterBufs carve_clusters(void *base, int64_t n)
+{
+    const int64_t nc = (n + CL - 1) / CL;
+    ClusterBufs c;
+    float4 *f = (float4 *)base;
+    c.sball = f;
+    c.cball = f + n;
+    uint32_t *u = (uint32_t *)(c.cball + nc);
+    c.code = u;
+    c.perm = u + n;
+    c.code_alt = u + 2 * n;
+    c.perm_alt = u + 3 * n;
+    c.sgid = u + 4 * n;
+    c.tmp = u + ((5 * n + 3) & ~(int64_t)3);   // 16-byte aligned (the sort keeps 64-bit sums there)
+    return c;
+}
+}  // namespace
+
+size_t rays_cluster_bytes(int64_t n)
+{
+    const int64_t nc = (n + CL - 1) / CL;
+    return sizeof(float4) * (size_t)(n + nc) + sizeof(uint32_t) * (size_t)((5 * n + 3) & ~(int64_t)3) +
+           sizeof(uint32_t) * sort_tmp_elems((uint32_t)n) + 64;
+}
+
 cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
                             int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
-                            float4 *wblk, uint32_t *cnt, cudaStream_t s)
+                            float4 *wblk, void *clusters, uint32_t *cnt, cudaStream_t s)
 {
     const int parts = rays_ball_parts(n);
     k_balls<<<parts, CULL_BS, 0, s>>>(rec, n, ball, part);
     k_scene<<<1, 32, 0, s>>>(part, parts, scene);
+    const ClusterBufs cb = carve_clusters(clusters, n);
+    const int64_t nc = (n + CL - 1) / CL;
+    k_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ball, n, scene, cb.code, cb.perm);
+    count_launches(3);
+    cudaError_t e = launch_sort(cb.code, cb.perm, cb.code_alt, cb.perm_alt, (uint32_t)n, 30, cb.tmp, s);
+    if (e != cudaSuccess) return e;
+    k_clusters<<<(unsigned)((nc * 32 + 127) / 128), 128, 0, s>>>(ball, cb.perm, n, nc, scene, cb.sball, cb.sgid,
+                                                               cb.cball);
     const int T = rays_blocks(n_rays);
     k_ray_blocks<<<T, RB, 0, s>>>(ro, rd, n_rays, scene, blk, wblk);
-    k_rays_count<<<T, CULL_BS, 0, s>>>(blk, wblk, ball, n, cnt);
-    count_launches(4);
+    k_rays_count<<<(unsigned)(((int64_t)T * 32 + BIN_BS - 1) / BIN_BS), BIN_BS, 0, s>>>(blk, wblk, cb.cball,
+                                                                                       cb.sball, n, nc, T, cnt);
+    count_launches(3);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const float4 *ball, int64_t n, int64_t b0,
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const void *clusters, int64_t n, int64_t b0,
                              int nb, const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
                              cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    k_rays_emit<<<nb, CULL_BS, 0, s>>>(blk, wblk, ball, n, b0, off, cnt, gids, ranges);
+    const ClusterBufs cb = carve_clusters(const_cast<void *>(clusters), n);
+    const int64_t nc = (n + CL - 1) / CL;
+    k_rays_emit<<<(unsigned)(((int64_t)nb * 32 + BIN_BS - 1) / BIN_BS), BIN_BS, 0, s>>>(
+        blk, wblk, cb.cball, cb.sball, cb.sgid, n, nc, b0, nb, off, cnt, gids, ranges);
     count_launches(1);
     return cudaGetLastError();
 }

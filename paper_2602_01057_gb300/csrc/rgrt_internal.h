@@ -159,13 +159,17 @@ int rays_ball_parts(int64_t n);        // partial scene boxes of the ball pass
 // balls (n float4), partial boxes (2 x parts), scene box (2), block lines
 // (2 x blocks) and per-block Gaussian counts
 // wblk: the same bound per 32-ray warp (4 per block, 2 float4 each)
+// clusters: scratch of rays_cluster_bytes(n) bytes (the bounding balls in
+// Morton order, their ids, the cluster balls and the sort's buffers)
+size_t rays_cluster_bytes(int64_t n);
 cudaError_t launch_rays_bin(const float4 *ro, const float4 *rd, int64_t n_rays, const float4 *rec,
                             int64_t n, float4 *ball, float4 *part, float4 *scene, float4 *blk,
-                            float4 *wblk, uint32_t *cnt, cudaStream_t s);
-// per-warp lists (RAYS_WPB per block, ascending Gaussian ids) of blocks
-// b0 .. b0+nb-1 at offsets off[0 .. RAYS_WPB nb); cnt holds RAYS_WPB counts per block
+                            float4 *wblk, void *clusters, uint32_t *cnt, cudaStream_t s);
+// per-warp lists (RAYS_WPB per block; clusters in Morton order, members in
+// order) of blocks b0 .. b0+nb-1 at offsets off[0 .. RAYS_WPB nb); cnt holds
+// RAYS_WPB counts per block
 constexpr int RAYS_WPB = 4;
-cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const float4 *ball, int64_t n, int64_t b0,
+cudaError_t launch_rays_emit(const float4 *blk, const float4 *wblk, const void *clusters, int64_t n, int64_t b0,
                              int nb, const uint32_t *off, const uint32_t *cnt, uint32_t *gids, uint2 *ranges,
                              cudaStream_t s);
 // tof (nullable, Gaussian kernel only): per ray (t_c, tau)

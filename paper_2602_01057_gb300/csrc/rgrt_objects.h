@@ -28,7 +28,7 @@ struct rgrt_ctx {
     // scratch
     rgrt::Buf cnt, off, rect, keys, vals, keys_alt, vals_alt, sort_tmp, scan_tmp, ranges, total;
     rgrt::Buf stage_in[4], stage_out[4], I, dLdI, y, grad, gflat, partial, stats, loss, loss_acc;
-    rgrt::Buf ball, part, scene, blk, wblk;    // explicit-ray binning
+    rgrt::Buf ball, part, scene, blk, wblk, clusters;    // explicit-ray binning
     std::vector<uint32_t> h_cnt;               // per-block list lengths (explicit rays)
     unsigned long long *h_total = nullptr;  // pinned
     // binning cache
