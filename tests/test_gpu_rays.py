@@ -102,6 +102,26 @@ def test_forward_and_adjoint_parity(rg, ctx, torch, oracle, name):
         assert grad_err(got, gref, k) < GRAD_TOL, k
 
 
+@pytest.mark.parametrize("n", [1, 7, 33, 100])
+def test_partial_clusters(rg, ctx, torch, oracle, n):
+    """Gaussian counts that leave the last cluster of 32 bounding balls
+    partly filled (or a single ball): forward and adjoint against the oracle."""
+    G = synth.gaussians_uniform(n, 70 + n, half_box=0.5, log_sigma=math.log(0.15))
+    R = synth.rays_random(4000, 71 + n, radius=0.8, seg=0.5)
+    I, gs, geom = gpu_fwd(torch, rg, ctx, G, R)
+    ref = oracle.forward_list(R["o"], R["d"], R["t"], G)
+    assert np.count_nonzero(ref["I"]) > 50
+    assert fwd_err(I, ref) < FWD_TOL
+    w = synth.random_weights(I.size, 72)
+    outs = [torch.empty(sz, device="cuda") for sz in ((n, 3), (n, 3), (n, 4), (n,))]
+    rg.project_backward(ctx, gs, geom, torch.from_numpy(w.astype(np.float32)).cuda(), *outs)
+    torch.cuda.synchronize()
+    got = dict(zip(("mu", "ls", "q", "rho"), (o.cpu().numpy() for o in outs)))
+    gref = oracle.backward_list(R["o"], R["d"], R["t"], G, w.astype(np.float32).astype(np.float64))
+    for k in ("mu", "ls", "q", "rho"):
+        assert grad_err(got, gref, k) < GRAD_TOL, k
+
+
 def test_circular_cone_as_rays_matches_detector_kernels(rg, ctx, torch):
     """The same cone-beam scan through the detector kernels and as explicit
     rays: two different FP32 evaluations of the same sums."""
