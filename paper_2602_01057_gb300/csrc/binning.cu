@@ -232,14 +232,16 @@ __global__ void k_sort_hist(const uint32_t *__restrict__ keys, uint32_t n, int s
     h[threadIdx.x] = 0;
     n = sort_count(n, n_dev);
     __syncthreads();
-    // the tile as 16-byte loads (every load issued before the counting)
+    // the tile as 16-byte loads (every load issued before the counting);
+    // scalar loads when the key array is not 16-byte aligned
     const uint32_t base = blockIdx.x * SORT_TILE;
+    const bool vec = ((uintptr_t)keys & 15u) == 0;
     constexpr int V = SORT_ITEMS / 4;
     uint4 q[V];
 #pragma unroll
     for (int j = 0; j < V; j++) {
         const uint32_t k = base + 4 * (threadIdx.x + j * SORT_BS);
-        if (k + 3 < n) {
+        if (vec && k + 3 < n) {
             q[j] = __ldg(reinterpret_cast<const uint4 *>(keys + k));
         } else {
             q[j].x = k < n ? keys[k] : 0u;

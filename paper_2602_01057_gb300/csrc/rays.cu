@@ -596,13 +596,16 @@ ClusterBufs carve_clusters(void *base, int64_t n)
     float4 *f = (float4 *)base;
     c.sball = f;
     c.cball = f + n;
+    // every u32 array starts on a 16-byte boundary (the sort reads its keys
+    // with 16-byte loads and keeps 64-bit sums in its scratch)
+    const int64_t n4 = (n + 3) & ~(int64_t)3;
     uint32_t *u = (uint32_t *)(c.cball + nc);
     c.code = u;
-    c.perm = u + n;
-    c.code_alt = u + 2 * n;
-    c.perm_alt = u + 3 * n;
-    c.sgid = u + 4 * n;
-    c.tmp = u + ((5 * n + 3) & ~(int64_t)3);   // 16-byte aligned (the sort keeps 64-bit sums there)
+    c.perm = u + n4;
+    c.code_alt = u + 2 * n4;
+    c.perm_alt = u + 3 * n4;
+    c.sgid = u + 4 * n4;
+    c.tmp = u + 5 * n4;
     return c;
 }
 }  // namespace
@@ -610,7 +613,8 @@ ClusterBufs carve_clusters(void *base, int64_t n)
 size_t rays_cluster_bytes(int64_t n)
 {
     const int64_t nc = (n + CL - 1) / CL;
-    return sizeof(float4) * (size_t)(n + nc) + sizeof(uint32_t) * (size_t)((5 * n + 3) & ~(int64_t)3) +
+    const int64_t n4 = (n + 3) & ~(int64_t)3;
+    return sizeof(float4) * (size_t)(n + nc) + sizeof(uint32_t) * (size_t)(5 * n4) +
            sizeof(uint32_t) * sort_tmp_elems((uint32_t)n) + 64;
 }
 
