@@ -15,11 +15,14 @@
 //    further than dev from L0 (distance to a line is convex along a segment),
 //    so the Gaussian can pair with the block only if
 //        dist(mu, L0) <= K sigma_max + dev;
-//  * the same bound is taken per warp (32 rays); per block, a pass over all
-//    Gaussians counts and then emits, in ascending Gaussian order, the ones
-//    that pass the block's test and then a warp's test into that warp's list.
+//  * the same bound is taken per warp (32 rays); per block, one warp counts
+//    and then emits the Gaussians that pass the block's test and then a
+//    warp's test into that warp's list, visiting them through clusters of 32
+//    Morton-ordered balls (a cluster ball holds its members' balls, so only
+//    the members of the clusters the block meets are tested).
 // Integration and adjoint: every warp walks its own list, 32 records at a
-// time staged in its own slice of shared memory (no barrier across the CTA).
+// time staged in its own slice of shared memory (no barrier across the CTA),
+// and skips a record when no lane's line meets its bounding ball.
 #include "pair.cuh"
 
 namespace rgrt {
