@@ -29,7 +29,6 @@ namespace rgrt {
 namespace {
 
 constexpr int RB = 128;    // rays per block
-constexpr int RCH = 128;   // records per shared-memory chunk
 constexpr int CULL_BS = 256;
 constexpr int NG_RAYS = 10;  // general_grad components: dmu[3], G_P[6], drho
 // bounding-ball radius factor: K sigma_max with K^2 the culling constant (a
