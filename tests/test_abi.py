@@ -51,3 +51,35 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert L.rgrt_ctx_create(None, 0, 0) == -1        # RGRT_E_INVAL
     assert L.project_forward(None, None, None, None, None) == -1
     assert b"null" in L.rgrt_last_error()
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program compiled here."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rgrt.h"', 'int main(void) {',
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("struct,cls", [("rgrt_geom_desc", "GeomDesc"), ("rgrt_adam", "Adam"),
+                                        ("rgrt_volume_desc", "VolumeDesc")])
+def test_binding_structs_match_the_header(struct, cls, tmp_path):
+    """The ctypes mirrors of the descriptor structs have the header's field
+    order, offsets and size."""
+    from paper_2602_01057_gb300 import rgrt
+    C = getattr(rgrt, cls)
+    names = [f[0] for f in C._fields_]
+    size, offs = _c_layout(struct, names, tmp_path)
+    assert ctypes.sizeof(C) == size
+    assert [getattr(C, n).offset for n in names] == offs
