@@ -1,19 +1,23 @@
 // Batched form: one optimisation step (or one forward pass) over many
 // independent scans -- each with its own Gaussians and geometry -- as a single
-// stream of work.  The binning of every scan runs back to back, then ONE
-// persistent launch integrates every (scan, tile) work item, taken from an
-// atomic counter (uneven scans share the GPU instead of leaving it
-// under-filled one by one), then the losses, ONE persistent adjoint launch,
-// the parameter chains and the Adam updates.  The whole step is captured once
-// in a CUDA graph and replayed, so a step costs one graph launch and one
-// small read-back (losses and the key-capacity overflow flag) instead of a
-// host round trip per scan.
+// stream of work.  The scans are binned one after another.  A scan large
+// enough to fill the GPU for 16 waves of tiles is projected, its loss taken
+// and back-projected right after its binning, with launches of its own (its
+// lists and records are still in L2 for the adjoint).  The smaller scans
+// share ONE persistent launch that integrates every (scan, tile) work item,
+// taken from an atomic counter (uneven scans fill the GPU together instead of
+// leaving it under-filled one by one), then their losses and ONE persistent
+// adjoint launch.  The parameter chains and the Adam updates of every scan
+// come last.  The whole step is captured once in a CUDA graph and replayed,
+// so a step costs one graph launch and one small read-back (losses and the
+// key-capacity overflow flag) instead of a host round trip per scan.
 //
 // Key capacities are planned from a real binning pass (with 25% headroom);
-// if the parameters move so far that a scan's (tile, Gaussian) entries no
-// longer fit, the emit kernel raises the overflow flag, every Adam update of
-// that step is skipped on the device, and the host re-plans, re-captures and
-// repeats the step.  Only the sorted Gaussian ids and tile ranges of a scan
+// a step sorts only the entries it emits (their count is read on the
+// device).  If the parameters move so far that a scan's (tile, Gaussian)
+// entries no longer fit, the emit kernel raises the overflow flag, every Adam
+// update of that step is skipped on the device, and the host re-plans,
+// re-captures and repeats the step.  Only the sorted Gaussian ids and tile ranges of a scan
 // are kept per scan; counts, keys and sort buffers are shared scratch sized
 // for the largest scan.
 #include <cuda_runtime.h>

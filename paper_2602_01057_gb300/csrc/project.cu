@@ -1,13 +1,16 @@
 // Per-tile ray integration (a3) and its adjoint (a5).
 //
 // One CTA per detector tile of tile_w x tile_h rays, one ray per thread,
-// warps laid out as 8 x 4 ray blocks.  The tile's Gaussian list (ascending
-// ids) is walked in chunks: the CTA gathers each chunk's records into shared
-// memory, turning every Gaussian into its view-space form for this view (see
-// below) together with its detector bounding box.  A warp skips a Gaussian
-// whose box misses its 8 x 4 block (a warp-uniform branch); otherwise every
-// lane evaluates its pair and the pair counts when m <= 9 (3-sigma cut).
-// FP32 throughout, FP32 accumulation per ray.
+// warps laid out as 8 x 4 ray blocks.  The tile's Gaussian list (ordered by
+// footprint position, then id) is walked in chunks: the CTA gathers each
+// chunk's records, turning every Gaussian into its view-space form for this
+// view (see below) together with its detector bounding box, into one of two
+// shared-memory buffers.  A warp skips a Gaussian whose box misses its 8 x 4
+// block, or (cone beam) whose footprint ellipse misses it (a warp-uniform
+// branch); otherwise every lane evaluates its pair and the pair counts when
+// m <= 9 (3-sigma cut).  FP32 throughout, FP32 accumulation per ray.
+// 3-D PET LORs (direction e_w + kappa e_v, kappa per detector column) have a
+// view-space form of their own (prep_record, pet3d_chain).
 //
 // The closed form (Eqs. 7-11) for a ray and one Gaussian is
 //   rho sqrt(2 pi / A) exp(-m/2),  A = d^T P d,  m = C - B^2/A,
