@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="c5: arrival rate (jobs/s)")
     ap.add_argument("--iters", type=int, default=300, help="recon: optimisation steps")
     ap.add_argument("--point-iters", type=int, default=1500, help="points: optimisation steps per reconstruction")
+    ap.add_argument("--pet3d-angles", type=int, default=288,
+                    help="pet3d: sinogram angles (fewer: a smaller case of the same scanner, for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fitted", action="store_true", help="skip the fitted-state timing")
@@ -109,8 +111,10 @@ def _params(G):
     return {k: G[k] for k in ("mu", "ls", "q", "rho")}
 
 
-def workload(name, seed):
+def workload(name, seed, pet3d_angles=288):
     G, true, gd, loss = _workload(name, seed)
+    if name == "pet3d" and pet3d_angles != gd["n_views"]:
+        gd = dict(gd, n_views=int(pet3d_angles))
     return _params(G), _params(true), gd, loss
 
 
@@ -339,7 +343,7 @@ def run_ours(args):
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
     dev = torch.device("cuda", local)
-    G, Gt, gd, loss = workload(args.workload, args.seed + rank)
+    G, Gt, gd, loss = workload(args.workload, args.seed + rank, args.pet3d_angles)
     R = synth.num_rays(gd)
     ctx = rgrt.Context(local)
     t_auto = None
@@ -432,6 +436,7 @@ def run_ours(args):
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload=WORKLOADS[args.workload], rays_per_step=R,
                             gaussians=int(G["mu"].shape[0]),
+                            **({"angles": int(gd["n_views"])} if args.workload == "pet3d" else {}),
                             tile=f"{tw}x{th}" + (" (autotuner)" if t_auto is not None else ""),
                             seed=args.seed,
                             l2=("flushed between timed steps (256 MiB write outside the events)"
