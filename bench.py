@@ -131,9 +131,11 @@ def _workload(name, seed):
         G, _ = synth.workload_c3(seed)
         true = synth.perturbed(G, seed + 101, pos_std=1.0)
         return G, true, synth.geom_c3_3d(), "poisson"
-    G, gd = synth.workload_c1(seed)
-    true = synth.perturbed(G, seed + 101, pos_std=0.01)
-    return G, true, gd, "l2"
+    if name == "c1":
+        G, gd = synth.workload_c1(seed)
+        true = synth.perturbed(G, seed + 101, pos_std=0.01)
+        return G, true, gd, "l2"
+    raise ValueError(f"no single-scan step for workload {name!r}")
 
 
 def dist_env():
@@ -247,9 +249,17 @@ def auto_views(name):
     return {"c2": 4, "c3": 4, "c1": 16, "pet3d": 1}[name]
 
 
+REFERENCE_WORKLOADS = ("c1", "c2", "c3", "pet3d")
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
+        return
+    if args.workload not in REFERENCE_WORKLOADS:
+        print(json.dumps(dict(impl="reference", unavailable=(
+            f"the oracle's timed sample covers the single-scan steps {', '.join(REFERENCE_WORKLOADS)}, "
+            f"not {args.workload}"))), flush=True)
         return
     G, _, gd, loss = workload(args.workload, 0)
     nv = args.cpu_views or auto_views(args.workload)

@@ -23,3 +23,13 @@ def test_reference_arm_line(workload):
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_reference_arm_without_an_oracle_sample():
+    """Workloads the oracle's timed sample does not cover say so (one JSON
+    line, exit status 0) instead of timing another workload."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c5",
+           "--steps", "1", "--warmup", "0"]
+    out = subprocess.run(cmd, cwd=ROOT, check=True, capture_output=True, text=True, timeout=300).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
