@@ -32,18 +32,24 @@ from paper_2602_01057_gb300 import synth  # noqa: E402
 
 METRIC = "rays/s fwd+bwd"
 UNIT = "rays/s"
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-# algorithmic FP32 work per kept pair (m <= 9), FMA counted as 2 FLOP: the
-# per-pair arithmetic of the recentred closed form (Eqs. 7-11), forward and
-# adjoint; see the kernel notes for the count.
-FLOP_PER_PAIR_FWD = 78
-FLOP_PER_PAIR_ADJ = 180
-# DRAM bytes (read + write) of one launch of the dominant kernels on the
-# cone-beam CT workload, from the ncu captures summarised in
-# profiles/k_adjoint_c2_cone.md and profiles/k_forward_c2_cone.md; None once a
-# kernel has changed since its capture.
-TRAFFIC_C2 = {"k_adjoint": 272.663040e6 + 4.093184e6, "k_forward": 222.537216e6 + 38.337792e6}
+# Algorithmic work per kept (ray, Gaussian) pair (m <= 9) of the closed form
+# (Eqs. 7-11) in its recentred form: 39 FP32 operations for the value
+# (delta 3, recentring 6, P d 9, A and B 6, P delta and C 12, m 3, value and
+# sum ~5) and 2.5 times that for the adjoint; 3 special-function operations
+# (1/A, A^-1/2, exp) for either.  FP32 peak = SMs x 128 lanes x SM clock (one
+# operation per lane per clock), MUFU peak = SMs x 16 x SM clock; the SM
+# count is read from the device and the clock is the median sampled during
+# the timed region.
+OPS_PER_PAIR_FWD = 39.0
+OPS_PER_PAIR_ADJ = 97.5
+MUFU_PER_PAIR = 3.0
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+# DRAM bytes (read + write) of one launch of an integration kernel, from an
+# ncu capture of the workload, valid only while the kernel sources hash to
+# the recorded digest (otherwise the bench line reports null)
+TRAFFIC = {}
+KERNEL_SOURCES = ("paper_2602_01057_gb300/csrc/project.cu", "paper_2602_01057_gb300/csrc/pair.cuh")
 WORKLOADS = {
     "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
           "180 views over 360 deg, 256x256 detector, source-origin 1000 mm, source-detector 1500 mm",
@@ -98,6 +104,8 @@ def parse():
     ap.add_argument("--pet3d-angles", type=int, default=288,
                     help="pet3d: sinogram angles (fewer: a smaller case of the same scanner, for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c2 default run: skip the PET, batching and serving measurements in the same line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fitted", action="store_true", help="skip the fitted-state timing")
     ap.add_argument("--tile", default="auto", help="binning tile WxH, or auto (the autotuner)")
@@ -343,28 +351,115 @@ class ClockSampler:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def run_ours(args):
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) measured on this machine's GPUs, and where it came from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return dict(hbm_gbs=float(m["hbm_gbs"]), sm_max_mhz=float(m.get("sm_max_mhz", 0.0)),
+                    source="measured (MEASURED_PEAKS.json)")
+    except (OSError, KeyError, ValueError):
+        return dict(hbm_gbs=6800.0, sm_max_mhz=0.0, source="fallback (6.8 TB/s)")
+
+
+def sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def sort_passes(tiles):
+    """Radix passes of the tile sort: 8-bit digits over the tile id plus an
+    8-bit position code."""
+    bits = max(1, math.ceil(math.log2(max(tiles, 2)))) + 8
+    return (bits + 7) // 8
+
+
+def binning_bytes(n_gauss, n_views, keys, tiles):
+    """Algorithmic DRAM bytes of one binning (cull, scan, emit, sort, ranges):
+    per (view, Gaussian) the 48-byte culling record read and its count and
+    pixel box written (60 B), the scan's read and write (8 B), the emit's
+    reads (16 B); per key the emit's write (8 B), 16 B per sort pass and the
+    ranges' 4-byte read; 8 B per tile range."""
+    e = float(n_gauss) * n_views
+    parts = dict(k_cull=60.0 * e, scan=8.0 * e, k_emit=16.0 * e + 8.0 * keys,
+                 radix_sort=16.0 * sort_passes(tiles) * keys, k_ranges=4.0 * keys + 8.0 * tiles)
+    return parts
+
+
+def roofline(kernels, pairs, keys, n_gauss, n_views, tiles, n_sm, sm_mhz, clock_note, peaks, workload,
+             traffic_table=None):
+    """Roofline of the integration kernels (FP32 issue and MUFU against the
+    SM count read from the device and the sampled clock) and of the binning
+    kernels (HBM against the measured copy bandwidth).  The top-level
+    figures are those of the dominant integration kernel."""
+    f = sm_mhz * 1e6
+    fp32_peak = n_sm * FP32_LANES_PER_SM * f / 1e12
+    mufu_peak = n_sm * MUFU_LANES_PER_SM * f / 1e12
+    digest = sources_digest()
+    out = {}
+    for name, ops in (("k_forward", OPS_PER_PAIR_FWD), ("k_adjoint", OPS_PER_PAIR_ADJ)):
+        kms = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
+        # pairs are counted per step: work per step / the kernel's time per step
+        step_ms = kernels[name]["ms"] / max(STEPS_TIMED[0], 1)
+        ach = pairs * ops / (step_ms / 1e3) / 1e12 if step_ms > 0 else 0.0
+        sfu = pairs * MUFU_PER_PAIR / (step_ms / 1e3) / 1e12 if step_ms > 0 else 0.0
+        tr = None
+        if traffic_table:
+            ent = traffic_table.get((workload, name))
+            if ent and ent[1] == digest:
+                tr = ent[0]
+        out[name] = dict(bound="alu", achieved=ach, peak=fp32_peak, unit="T FP32 op/s", frac=ach / fp32_peak,
+                         sfu=dict(achieved=sfu, peak=mufu_peak, unit="T MUFU op/s", frac=sfu / mufu_peak),
+                         kernel_ms_per_step=step_ms, launches_per_step=kernels[name]["launches"] / max(STEPS_TIMED[0], 1),
+                         ms_per_launch=kms, traffic=tr)
+    bb = binning_bytes(n_gauss, n_views, keys, tiles)
+    bin_ms = sum(kernels[k]["ms"] for k in bb) / max(STEPS_TIMED[0], 1)
+    tot = sum(bb.values())
+    gbs = tot / (bin_ms / 1e3) / 1e9 if bin_ms > 0 else 0.0
+    per = {}
+    for k, v in bb.items():
+        ms = kernels[k]["ms"] / max(STEPS_TIMED[0], 1)
+        per[k] = dict(bytes=v, ms=ms, gbs=(v / (ms / 1e3) / 1e9 if ms > 0 else 0.0),
+                      frac=(v / (ms / 1e3) / 1e9 / peaks["hbm_gbs"] if ms > 0 else 0.0))
+    dom = max(("k_forward", "k_adjoint"), key=lambda k: out[k]["kernel_ms_per_step"])
+    d = out[dom]
+    return dict(bound="alu", achieved=d["achieved"], peak=d["peak"], unit=d["unit"], frac=d["frac"],
+                traffic=d["traffic"], kernel=dom, forward=out["k_forward"], adjoint=out["k_adjoint"],
+                sfu=dict(kernel=dom, **d["sfu"]),
+                binning_hbm=dict(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s",
+                                 frac=gbs / peaks["hbm_gbs"], bytes_per_step=tot, ms_per_step=bin_ms,
+                                 kernels=per, peak_source=peaks["source"]),
+                n_sm=n_sm, sm_mhz=sm_mhz, clock=clock_note, sources_digest=digest,
+                note=(f"FP32 work = {OPS_PER_PAIR_FWD:g} (forward) / {OPS_PER_PAIR_ADJ:g} (adjoint) operations "
+                      f"and {MUFU_PER_PAIR:g} MUFU per kept pair (m <= 9), per step / kernel time per step; "
+                      f"peaks = {n_sm} SMs x {FP32_LANES_PER_SM} FP32 (x {MUFU_LANES_PER_SM} MUFU) lanes x "
+                      f"{sm_mhz:.0f} MHz; binning bytes as documented in binning_bytes()"))
+
+
+STEPS_TIMED = [1]
+
+
+def measure_step(args, name, rgrt, ctx, dev, seed, world, rank, local, cpu=True, tile=None):
+    """One full optimisation step (records, binning, forward, loss, adjoint,
+    parameter chain, Adam) of workload `name`: the JSON fields of its line."""
     import torch
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    from paper_2602_01057_gb300 import build, rgrt
-    build.build()
-    dev = torch.device("cuda", local)
-    G, Gt, gd, loss = workload(args.workload, args.seed + rank, args.pet3d_angles)
+    G, Gt, gd, loss = workload(name, seed, args.pet3d_angles)
     R = synth.num_rays(gd)
-    ctx = rgrt.Context(local)
     t_auto = None
-    if args.tile == "auto":
+    tile = tile or args.tile
+    if tile == "auto":
         # tile shape from the autotuner (forward + adjoint over all views: the
         # sort's pass count depends on the total number of tiles), outside the timing
         ga = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
         tw, th, t_auto = rgrt.autotune_tile(ctx, ga, gd, max_views=0)
         ga.close()
     else:
-        tw, th = (int(x) for x in args.tile.split("x"))
+        tw, th = (int(x) for x in tile.split("x"))
     gd = dict(gd, tile_w=tw, tile_h=th)
     geom = rgrt.Geometry(ctx, gd)
     # measured data: projections of the perturbed ("true") Gaussians
@@ -423,32 +518,33 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_max = max_over_ranks(ms, world)
     kernels = {}
-    for name in ("k_records", "k_cull", "scan", "k_emit", "radix_sort", "k_ranges", "k_forward",
-                 "k_loss", "k_adjoint", "k_param_chain", "k_adam"):
-        n, t = ctx.prof_get(name)
-        kernels[name] = dict(launches=n, ms=t)
+    for kname in ("k_records", "k_cull", "scan", "k_emit", "radix_sort", "k_ranges", "k_forward",
+                  "k_loss", "k_adjoint", "k_param_chain", "k_adam"):
+        n, t = ctx.prof_get(kname)
+        kernels[kname] = dict(launches=n, ms=t)
     ctx.prof_enable(False)
     value = weak_value(R, args.steps, world, ms_max)
     pairs = st["pairs_kept"]
-    # roofline of the dominant kernel (FP32 ALU bound)
-    dom = max(("k_forward", "k_adjoint"), key=lambda k: kernels[k]["ms"])
-    per = kernels[dom]["ms"] / max(kernels[dom]["launches"], 1)
-    flop = pairs * (FLOP_PER_PAIR_ADJ if dom == "k_adjoint" else FLOP_PER_PAIR_FWD)
-    achieved = flop / (per / 1e3) / 1e12
-    peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = TRAFFIC_C2.get(dom) if args.workload == "c2" else None
-    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=traffic, kernel=dom, kernel_ms=per,
-                note="FP32 FLOP of the kept pairs (m <= 9) / kernel time; peak = 152 SMs x 128 "
-                     "FP32 lanes x 2 (FMA) x 2070 MHz")
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    if clk and clk.get("sm_mhz", 0) > 0:
+        sm_mhz, note = clk["sm_mhz"], "median SM clock sampled during the timed region"
+    else:
+        sm_mhz = peaks["sm_max_mhz"] or 2070.0
+        note = "no clock samples: the maximum SM clock"
+    STEPS_TIMED[0] = args.steps
+    n_views = synth.num_rays(gd) // (int(gd["n_rows"]) * int(gd["n_cols"]))
+    tiles = n_views * geom.tiles_per_view
+    roof = roofline(kernels, pairs, st["keys"], int(G["mu"].shape[0]), n_views, tiles, n_sm, sm_mhz, note,
+                    peaks, name, TRAFFIC)
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOADS[args.workload], rays_per_step=R,
+                config=dict(workload=WORKLOADS[name], rays_per_step=R,
                             gaussians=int(G["mu"].shape[0]),
-                            **({"angles": int(gd["n_views"])} if args.workload == "pet3d" else {}),
+                            **({"angles": int(gd["n_views"])} if name == "pet3d" else {}),
                             tile=f"{tw}x{th}" + (" (autotuner)" if t_auto is not None else ""),
-                            seed=args.seed,
+                            seed=seed,
                             l2=("flushed between timed steps (256 MiB write outside the events)"
                                 if flush is not None else "not flushed"),
                             parallelism=f"{world} independent scans (one per GPU)"),
@@ -461,16 +557,57 @@ def run_ours(args):
     # end to end: host parameters in, step, host loss + parameters out
     if not args.no_e2e:
         line["e2e"] = e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world)
-    if args.workload in ("c2", "c3") and not args.no_fitted:
+    if name in ("c2", "c3") and not args.no_fitted:
         line["fitted"] = fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world)
-    if rank == 0 and not args.no_cpu_baseline:
-        nv = args.cpu_views or auto_views(args.workload)
+    if cpu and rank == 0 and not args.no_cpu_baseline:
+        nv = args.cpu_views or auto_views(name)
         line["cpu_baseline"] = cpu_baseline(G, gd, loss, nv, rgrt, ctx)
+    gs.close()
+    geom.close()
+    del flush
+    return line
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2602_01057_gb300 import build, rgrt
+    build.build()
+    dev = torch.device("cuda", local)
+    ctx = rgrt.Context(local)
+    line = measure_step(args, args.workload, rgrt, ctx, dev, args.seed + rank, world, rank, local)
+    # the other workloads of the benchmark (one GPU, default run only): the
+    # PET step, batching against plain steps, serving against a one-job server
+    if world == 1 and args.workload == "c2" and not args.no_extras:
+        extra = {}
+        try:
+            extra["c3"] = measure_step(args, "c3", rgrt, ctx, dev, args.seed, 1, 0, local)
+        except Exception as e:   # noqa: BLE001 -- reported in the line, not hidden
+            extra["c3"] = dict(error=repr(e))
+        ctx.close()
+        torch.cuda.empty_cache()
+        try:
+            extra["c4"] = c4_measure(args, steps=EXTRA_STEPS, warmup=EXTRA_WARMUP)
+        except Exception as e:   # noqa: BLE001
+            extra["c4"] = dict(error=repr(e))
+        torch.cuda.empty_cache()
+        try:
+            extra["c5"] = c5_measure(args, full=True)
+        except Exception as e:   # noqa: BLE001
+            extra["c5"] = dict(error=repr(e))
+        line["extra"] = extra
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+EXTRA_STEPS, EXTRA_WARMUP = 3, 2
 
 
 def fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world):
@@ -556,13 +693,13 @@ def c4_scans(n_scans, seed=0, small=False):
     return out
 
 
-def run_c4(args):
-    """Batched step over uneven scans vs one plain step per scan (rays/s)."""
+def c4_measure(args, steps, warmup, small=False):
+    """Batched step over uneven scans vs one plain step per scan (rays/s):
+    the fields of the batching line."""
     import torch
     from paper_2602_01057_gb300 import build, rgrt
     build.build()
     dev = torch.device("cuda", 0)
-    small = args.workload == "c4-small"
     scans = c4_scans(args.scans, small=small)
     ctx = rgrt.Context(0)
     # tile shape from the autotuner, on the median-size scan
@@ -588,52 +725,70 @@ def run_c4(args):
         rays += geom.n_rays
     hp = rgrt.adam_params()
     batch = rgrt.Batch(ctx, gb, geoms)
+    stream = torch.cuda.current_stream()
     step = 0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step += 1
         batch.loss_step(ys, rgrt.RGRT_LOSS_L2, hp, step)
     torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
     l0 = rgrt.launch_count()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
         step += 1
         batch.loss_step(ys, rgrt.RGRT_LOSS_L2, hp, step)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
+    t_batch = e0.elapsed_time(e1) / 1e3 / steps
     launches = rgrt.launch_count() - l0
     # one plain loss_step per scan (each with its own binning read-back)
     lo = torch.zeros(1, device=dev)
     pstep = 0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         pstep += 1
         for g, geom, y in zip(gp, geoms, ys):
             rgrt.loss_step(ctx, g, geom, y, rgrt.RGRT_LOSS_L2, hp, pstep, lo)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e0.record(stream)
+    for _ in range(steps):
         pstep += 1
         for g, geom, y in zip(gp, geoms, ys):
             rgrt.loss_step(ctx, g, geom, y, rgrt.RGRT_LOSS_L2, hp, pstep, lo)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_plain = (time.perf_counter() - t0) / args.steps
+    t_plain = e0.elapsed_time(e1) / 1e3 / steps
+    clk = clocks.stop()
     info = batch.info()
-    line = dict(metric=METRIC, value=rays / t_batch, unit=UNIT, n_gpus=1, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
+    batch.close()
+    for x in gb + gp + geoms:
+        x.close()
+    ctx.close()
+    name = "c4-small" if small else "c4"
+    line = dict(metric=METRIC, value=rays / t_batch, unit=UNIT, n_gpus=1, steps=steps,
+                warmup=warmup, ms_per_step=1e3 * t_batch, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=WORKLOADS[args.workload], scans=len(scans), rays_per_step=rays,
+                config=dict(workload=WORKLOADS[name], scans=len(scans), rays_per_step=rays,
                             tile=f"{tw}x{th}", gaussians=int(sum(G["mu"].shape[0] for G, _ in scans)),
                             l2=("step working set far above L2 (not flushed)" if not small else
                                 "not flushed: the whole step is timed, small scans partly L2-resident")),
                 plain=dict(value=rays / t_plain, ms_per_step=1e3 * t_plain,
                            note=f"the same step as {len(scans)} loss_step calls, one scan at a time"),
                 speedup_vs_plain=t_plain / t_batch, batch=info, gpu_launches=launches,
-                e2e=None)
-    print(json.dumps(line), flush=True)
+                timing="CUDA events on the launching stream around all timed steps", e2e=None)
+    if clk:
+        line["clocks"] = clk
+    return line
 
 
-C5_CT_N = (20_000, 200_000)     # Gaussians (log-uniform)
-C5_CT_VIEWS = (30, 180)         # views (uniform)
-C5_CT_SIDE = (128, 256)         # detector side (uniform, multiple of 16)
+def run_c4(args):
+    print(json.dumps(c4_measure(args, args.steps, args.warmup, small=args.workload == "c4-small")), flush=True)
+
+
+C5_CT_N = (20_000, 1_000_000)   # Gaussians (log-uniform)
+C5_CT_VIEWS = (30, 720)         # views (uniform)
+C5_CT_SIDE = (128, 512)         # detector side (uniform, multiple of 16)
 C5_PET_N = (50_000, 400_000)
 C5_ITERS, C5_VIEWS_PER_ITER = 200, 8
 C5_PET_COUNTS = 1e8
@@ -726,18 +881,20 @@ def c5_run(serve, rgrt, specs, offsets, n_slots, budget, rate_scale=1.0):
                 d2h_bytes_per_job=d2h / len(jobs))
 
 
-def run_c5(args):
+def c5_measure(args, full=False):
     """Serving: the same job stream through a continuous-batching server and
     a one-job-at-a-time server, at the stated arrival rate and at a rate the
-    one-job server can sustain."""
+    one-job server can sustain; the fields of the serving line."""
     import torch
     from paper_2602_01057_gb300 import build, rgrt, serve
     build.build()
     dev = torch.device("cuda", 0)
     ctx = rgrt.Context(0)
     budget = 150 * 10**9
-    specs, offsets = c5_jobs(args.jobs, args.rate, 0, rgrt, serve, ctx, dev)
+    n_jobs = EXTRA_JOBS if full else args.jobs
+    specs, offsets = c5_jobs(n_jobs, args.rate, 0, rgrt, serve, ctx, dev)
     ctx.close()
+    torch.cuda.empty_cache()
     # warm-up: a few jobs through the continuous server (module load, allocator)
     warm = [dict(sp, n_iter=5) for sp in specs[:max(args.warmup, 1)]]
     c5_run(serve, rgrt, warm, np.zeros(len(warm)), args.slots, budget)
@@ -753,15 +910,20 @@ def run_c5(args):
     ck = clocks.stop()
     n_ct = sum(1 for sp in specs if sp["tag"][0] == "ct")
     n_recon = sum(1 for sp in specs if sp["kind"] == serve.RECON)
+    ct_sizes = [(sp["tag"][2], sp["geom"]["n_views"], sp["geom"]["n_rows"]) for sp in specs if sp["tag"][0] == "ct"]
     line = dict(metric=METRIC, value=cont["rays_per_s"], unit=UNIT, n_gpus=1, steps=len(specs),
                 warmup=len(warm), ms_per_step=1e3 * cont["wall_s"] / len(specs), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload=WORKLOADS["c5"], jobs=len(specs), ct_jobs=n_ct, recon_jobs=n_recon,
                             rate_per_s=args.rate, slots=args.slots, hbm_budget_gb=150,
-                            scale_down=(f"CT Gaussians log-uniform {C5_CT_N[0]}-{C5_CT_N[1]} (of 20k-1M), "
-                                        f"views U{{{C5_CT_VIEWS[0]}..{C5_CT_VIEWS[1]}}} (of 30..720), "
-                                        f"side U{{{C5_CT_SIDE[0]}..{C5_CT_SIDE[1]}}} (of 128..512); "
-                                        "PET and reconstructions at full size"),
+                            sizes=(f"CT Gaussians log-uniform {C5_CT_N[0]}-{C5_CT_N[1]}, views "
+                                   f"U{{{C5_CT_VIEWS[0]}..{C5_CT_VIEWS[1]}}}, side U{{{C5_CT_SIDE[0]}.."
+                                   f"{C5_CT_SIDE[1]}}} (multiples of 16); PET the 288x329x63 geometry with "
+                                   f"{C5_PET_N[0]}-{C5_PET_N[1]} Gaussians; reconstructions {C5_ITERS} "
+                                   f"iterations of {C5_VIEWS_PER_ITER} views"),
+                            ct_largest=dict(gaussians=max(x[0] for x in ct_sizes) if ct_sizes else None,
+                                            views=max(x[1] for x in ct_sizes) if ct_sizes else None,
+                                            side=max(x[2] for x in ct_sizes) if ct_sizes else None),
                             l2="not flushed: jobs far above L2"),
                 serving=dict(continuous=cont, fifo=fifo,
                              at_80pct_fifo_capacity=dict(rate_per_s=lam80, continuous=cont80, fifo=fifo80),
@@ -773,10 +935,17 @@ def run_c5(args):
                          d2h_bytes_per_step=cont["d2h_bytes_per_job"],
                          note="a step is one job; jobs enter and leave as host arrays, every copy "
                               "inside the timed run"))
-    print(json.dumps(line), flush=True)
+    return line
 
 
-FLOP_PER_PAIR_VOX = 30   # per kept (voxel, Gaussian) pair: delta, P delta, the form, scale, value, sum
+def run_c5(args):
+    print(json.dumps(c5_measure(args)), flush=True)
+
+
+EXTRA_JOBS = 32
+
+
+OPS_PER_PAIR_VOX = 15   # per kept (voxel, Gaussian) pair: delta 3, P delta 9, the form 3 (plus the exponential)
 
 
 def run_vox(args):
@@ -821,8 +990,10 @@ def run_vox(args):
     s = np.exp(G["ls"].astype(np.float64))
     pairs = float(np.sum(4.0 / 3.0 * math.pi * 27.0 * np.prod(s, axis=1)) / h ** 3)
     per = kms / max(nk, 1)
-    achieved = pairs * FLOP_PER_PAIR_VOX / (per / 1e3) / 1e12
-    peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = pairs * OPS_PER_PAIR_VOX / (per / 1e3) / 1e12
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = clk["sm_mhz"] if clk and clk.get("sm_mhz", 0) > 0 else (measured_peaks()["sm_max_mhz"] or 2070.0)
+    peak = n_sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     # end to end: the volume read back to pinned host memory every call
     host = torch.empty((n, n, n)).pin_memory()
     torch.cuda.synchronize()
@@ -840,9 +1011,10 @@ def run_vox(args):
                                 if flush is not None else "not flushed")),
                 kernels=dict(vox_bin=dict(launches=nb, ms=bms), k_voxelize=dict(launches=nk, ms=kms)),
                 pairs_kept_per_step=pairs,
-                roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                              traffic=None, kernel="k_voxelize", kernel_ms=per,
-                              note="30 FLOP per kept (voxel, Gaussian) pair, pairs counted analytically"),
+                roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="T FP32 op/s", frac=achieved / peak,
+                              traffic=None, kernel="k_voxelize", kernel_ms=per, n_sm=n_sm, sm_mhz=sm_mhz,
+                              note="15 FP32 operations per kept (voxel, Gaussian) pair, pairs counted "
+                                   "analytically; peak = SMs x 128 lanes x sampled SM clock"),
                 gpu_launches=launches,
                 e2e=dict(value=n ** 3 / e2e_s, unit="voxels/s", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=4 * n ** 3))

@@ -109,7 +109,8 @@ typedef struct rgrt_geom rgrt_geom;
  * Output layout: CT I[view][row][col]; PET I[plane][angle][radial];
  * PET_3D I[delta][angle][ring pair][radial]
  * ((2 max_ring_diff + 1) n_views n_rows n_cols values).
- * tile_w/tile_h: binning tile in pixels (multiples of 8 and 4; 0 = 16).
+ * tile_w/tile_h: binning tile in pixels (width 8, 16 or 32, height 4..32 in
+ * steps of 4, 32..256 pixels; 0 = 16).
  */
 typedef struct {
     int32_t kind;        /* RGRT_GEOM_* */
@@ -301,6 +302,14 @@ int rgrt_batch_forward(rgrt_batch *b, float *const *out_I, void *stream);
 int rgrt_batch_loss_step(rgrt_batch *b, const float *const *y, int loss, const rgrt_adam *hp, int t,
                          float *loss_out, void *stream);
 
+/* Tile lists of scan `scan` as the batch's last forward or step binned them
+ * (layout as rgrt_debug_tile_lists: n_keys_out entries, tile_start[T + 1]
+ * CSR offsets over the scan's T tiles, gid[cap] Gaussian ids, host or
+ * device outputs).  Synchronises.  RGRT_E_INVAL for a bad scan index,
+ * RGRT_E_CAPACITY if cap is smaller than the number of entries. */
+int rgrt_batch_debug_tile_lists(rgrt_batch *b, int scan, int64_t *n_keys_out, uint32_t *tile_start,
+                                uint32_t *gid, int64_t cap);
+
 /* tiles of all scans, planned key capacity, re-plans so far */
 int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans);
 
@@ -331,11 +340,14 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
  * x ring differences) of 1024 x 1024 pixels, and the whole pipeline must fit
  * the scratch (C1-sized problems of
  * a few thousand Gaussians fit easily); otherwise RGRT_E_CAPACITY with a
- * message stating the bytes needed.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and must come before any
- * stream capture on that device.  Calls share the array: calls whose GPU work
- * overlaps (unordered streams, several host threads) race.  Reads one 8-byte
- * count back from the device (a synchronisation of `stream`). */
+ * message stating the bytes needed.  RGRT_E_INVAL for an array that is not
+ * memory of the current device, and for non-finite parameters (as
+ * project_forward).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); that first call should come before any
+ * stream capture on the device.  Calls share the array, which keeps the last
+ * call's contents: calls whose GPU work overlaps (unordered streams, several
+ * host threads) race.  Every call reads the entry count and the non-finite
+ * flag back from the device (16 bytes; a synchronisation of `stream`). */
 int project_forward_noalloc(const rgrt_geom_desc *desc, int64_t n, const float *mu3,
                             const float *logscale3, const float *quat4, const float *rho,
                             float *out_I, void *stream);
@@ -352,13 +364,15 @@ int64_t rgrt_launch_count(void);
  * (00,01,02,11,12,22), n x 6 floats (host or device). */
 int rgrt_debug_records(rgrt_ctx *ctx, const rgrt_gauss *g, float *sigma6, void *stream);
 
-/* Tile lists of views [v0, v1): n_keys_out = number of (tile, Gaussian)
- * entries; tile_start[n_tiles + 1] (CSR offsets, tile id = (view - v0) *
- * tiles_per_view + ty * tiles_x + tx) and gid[cap] (Gaussian ids; within a
- * tile ordered by the position code of the Gaussian's pixel box in the tile
- * -- row bucket, column bucket, 4 bits each, bucket = (lo + hi) * 8 / tile
- * size -- then by ascending id).  Host or device outputs; RGRT_E_CAPACITY if
- * cap is smaller than the number of entries (n_keys_out is still set). */
+/* Tile lists of views [v0, v1) (3-D PET: views count (ring difference,
+ * angle) pairs, ring-difference major): n_keys_out = number of (tile,
+ * Gaussian) entries; tile_start[n_tiles + 1] (CSR offsets, tile id =
+ * (view - v0) * tiles_per_view + ty * tiles_x + tx) and gid[cap] (Gaussian
+ * ids).  A tile's entries form a set: the projection needs no depth order
+ * (paper section 2.3), and their order is the implementation's own.  Host
+ * or device outputs; RGRT_E_INVAL for explicit-ray geometries or a bad view
+ * range; RGRT_E_CAPACITY if cap is smaller than the number of entries
+ * (n_keys_out is still set). */
 int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
                           int v1, int64_t *n_keys_out, uint32_t *tile_start, uint32_t *gid,
                           int64_t cap, void *stream);

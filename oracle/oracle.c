@@ -1069,13 +1069,30 @@ void or_records_fp32(int64_t n, const float *ls, const float *q, float *sig6)
 #define OG32_CULL_K2 9.0625f
 
 /*
- * FP32 cull of every (view, Gaussian): pixel box (i0, i1, j0, j1) of the
- * detector pixels whose centre lies inside the bounding box of the projected
- * K-sigma ellipsoid, and count = number of tiles of tile_w x tile_h pixels it
- * touches (0 and a box of -1 when empty).  Output index = view * n + gid.
+ * FP32 cull of views v0 .. v1-1 and every Gaussian: pixel box (i0, i1, j0, j1)
+ * of the detector pixels whose centre lies inside the bounding box of the
+ * projected K-sigma ellipsoid, and count = number of tiles of tile_w x tile_h
+ * pixels it touches (0 and a box of -1 when empty).  Output index =
+ * (view - v0) * n + gid.
+ *
+ * Kinds 0 and 2 (parallel rays): u and v ranges mu.e +- sqrt(K^2 e^T Sigma e).
+ * Kind 1 (cone beam): the tangent planes through the source (og32_cone).
+ * Kind 3 (fully 3-D PET): the u range as for kind 2; the LOR of radial
+ * position s between rings r1, r2 has direction e_w + kappa e_v with
+ * kappa = dz / (2 sqrt(R^2 - s^2)), dz = (r2 - r1) pitch, and along it
+ * a . x = z_mid for a = e_v - kappa e_w (z_mid its mid-height), so it can
+ * meet the K-sigma ellipsoid only if z_mid lies in
+ * mu.a +- sqrt(K^2 a^T Sigma a).  Over the columns i0..i1 kappa runs between
+ * its values at the smallest and the largest |s| of those columns, and both
+ * bounds are convex / concave in kappa, so the union of the intervals is
+ * spanned by those two slopes.  The rows are ring pairs: row j holds the LOR
+ * of mid-height z_j + |delta| pitch / 2 (z_j the ring heights), and rows past
+ * the segment's last ring pair (j > n_rows - 1 - |delta|) hold none.  When
+ * the widest column reaches the ring radius (R^2 - s^2 <= 0) every row of
+ * the segment is taken.
  */
-void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls, const float *q,
-                  int tile_w, int tile_h, int32_t *rect, int32_t *count)
+void or_cull_fp32_range(const og_geom *g, int64_t n, const float *mu, const float *ls, const float *q,
+                        int tile_w, int tile_h, int v0, int v1, int32_t *rect, int32_t *count)
 {
     float *ut = malloc(sizeof(float) * (size_t)(g->n_cols > 0 ? g->n_cols : 1));
     float *vt = malloc(sizeof(float) * (size_t)(g->n_rows > 0 ? g->n_rows : 1));
@@ -1085,7 +1102,8 @@ void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls,
     or_records_fp32(n, ls, q, sig);
     const float K2 = OG32_CULL_K2;
     float dso = (float)g->dso, dsd = (float)g->dsd;
-    for (int v = 0; v < g->n_views; v++) {
+    float R2 = (float)(g->radius * g->radius), pitch = (float)g->pitch_v;
+    for (int v = v0; v < v1; v++) {
         double eu_d[3], ev_d[3], ew_d[3];
         og_frame(g, v, eu_d, ev_d, ew_d);
         float eu[3], ev[3], ew[3];
@@ -1107,8 +1125,43 @@ void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls,
                 ulo = mu_u - hu; uhi = mu_u + hu; vlo = mu_v - hv; vhi = mu_v + hv;
             }
             int i0 = og32_lower(ut, g->n_cols, ulo), i1 = og32_upper(ut, g->n_cols, uhi);
-            int j0 = og32_lower(vt, g->n_rows, vlo), j1 = og32_upper(vt, g->n_rows, vhi);
-            int64_t x = (int64_t)v * n + k;
+            int j0, j1;
+            if (g->kind == OG_PET3D) {
+                j0 = 0;
+                j1 = -1;
+                if (i0 <= i1) {
+                    int delta = og_delta(g, v), ad = abs(delta);
+                    float dz = (float)delta * pitch;
+                    float zoff = (0.5f * (float)ad) * pitch;
+                    float ua = ut[i0], ub = ut[i1];
+                    float amin = (ua <= 0.0f && ub >= 0.0f) ? 0.0f : fminf(fabsf(ua), fabsf(ub));
+                    float amax = fmaxf(fabsf(ua), fabsf(ub));
+                    float h2a = R2 - amin * amin, h2b = R2 - amax * amax;
+                    int last = g->n_rows - 1 - ad;
+                    if (!(h2b > 0.0f)) {
+                        j1 = last;
+                    } else {
+                        float mu_w = og32_dot(m, ew);
+                        float svv = og32_form(S, ev, ev), svw = og32_form(S, ev, ew), sww = og32_form(S, ew, ew);
+                        float zlo = INFINITY, zhi = -INFINITY;
+                        for (int e = 0; e < 2; e++) {
+                            float kap = (0.5f * dz) / sqrtf(e ? h2b : h2a);
+                            float zc = mu_v - kap * mu_w;
+                            float t = (svv - (2.0f * kap) * svw) + (kap * kap) * sww;
+                            float half = sqrtf(fmaxf(K2 * t, 0.0f));
+                            zlo = fminf(zlo, zc - half);
+                            zhi = fmaxf(zhi, zc + half);
+                        }
+                        j0 = og32_lower(vt, g->n_rows, zlo - zoff);
+                        j1 = og32_upper(vt, g->n_rows, zhi - zoff);
+                        if (j1 > last) j1 = last;
+                    }
+                }
+            } else {
+                j0 = og32_lower(vt, g->n_rows, vlo);
+                j1 = og32_upper(vt, g->n_rows, vhi);
+            }
+            int64_t x = (int64_t)(v - v0) * n + k;
             if (i0 > i1 || j0 > j1) {
                 count[x] = 0;
                 rect[4 * x] = rect[4 * x + 1] = rect[4 * x + 2] = rect[4 * x + 3] = -1;
@@ -1120,4 +1173,11 @@ void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls,
         }
     }
     free(ut); free(vt); free(sig);
+}
+
+/* every view of the geometry (3-D PET: every (ring difference, angle)) */
+void or_cull_fp32(const og_geom *g, int64_t n, const float *mu, const float *ls, const float *q,
+                  int tile_w, int tile_h, int32_t *rect, int32_t *count)
+{
+    or_cull_fp32_range(g, n, mu, ls, q, tile_w, tile_h, 0, og_nviews(g), rect, count);
 }

@@ -318,52 +318,51 @@ def records_fp32(ls, q):
     return out
 
 
-def cull_fp32(geom, G, tile_w, tile_h):
-    """FP32 cull: (pixel box[V, n, 4] = i0, i1, j0, j1; tile rectangle[V, n, 4]
-    = tx0, tx1, ty0, ty1; tile count[V, n])."""
+def cull_fp32(geom, G, tile_w, tile_h, views=None):
+    """FP32 cull of views [v0, v1) (``views`` = (v0, v1); default every view,
+    3-D PET counting one per ring difference and angle): (pixel box[V, n, 4]
+    = i0, i1, j0, j1; tile rectangle[V, n, 4] = tx0, tx1, ty0, ty1; tile
+    count[V, n]), V = v1 - v0."""
     g = _geom(geom)
-    if g.desc["kind"] == "pet3d":
-        raise ValueError("the FP32 cull reference covers the detector geometries of kinds 0-2")
     n, mu, ls, q, rho = _gauss(G)
-    V = int(g.desc["n_views"])
+    v0, v1 = (0, g.n_views) if views is None else (int(views[0]), int(views[1]))
+    if not 0 <= v0 < v1 <= g.n_views:
+        raise ValueError(f"view range {v0}..{v1} outside 0..{g.n_views}")
+    V = v1 - v0
     box = np.zeros((V, n, 4), dtype=np.int32)
     cnt = np.zeros((V, n), dtype=np.int32)
-    lib().or_cull_fp32(g.ref, ctypes.c_int64(n), _p(mu), _p(ls), _p(q),
-                       ctypes.c_int(tile_w), ctypes.c_int(tile_h), _p(box), _p(cnt))
+    lib().or_cull_fp32_range(g.ref, ctypes.c_int64(n), _p(mu), _p(ls), _p(q),
+                             ctypes.c_int(tile_w), ctypes.c_int(tile_h), ctypes.c_int(v0),
+                             ctypes.c_int(v1), _p(box), _p(cnt))
     rect = np.where(box >= 0, box // np.array([tile_w, tile_w, tile_h, tile_h]), -1).astype(np.int32)
     return box, rect, cnt
 
 
-def tile_lists_fp32(geom, G, tile_w, tile_h):
-    """Per-tile Gaussian lists implied by the FP32 cull, in CSR form:
-    (start[T+1], gid[K]); tile id = view * tiles_per_view + ty * tiles_x + tx.
-    Within a tile, entries are ordered by a position code and then by id: the
-    code is (4-bit row bucket, 4-bit column bucket) of the centre of the
-    Gaussian's pixel box clipped to the tile, bucket = (lo + hi) * 8 // size."""
+def tile_lists_fp32(geom, G, tile_w, tile_h, views=None):
+    """Per-tile Gaussian sets implied by the FP32 cull of views [v0, v1), in
+    CSR form: (start[T+1], gid[K]); tile id = (view - v0) * tiles_per_view +
+    ty * tiles_x + tx.  A tile's list is a set (the projection needs no
+    depth order), written here in increasing Gaussian id."""
     desc = geom.desc if isinstance(geom, Geometry) else geom
-    box, rect, cnt = cull_fp32(geom, G, tile_w, tile_h)
+    box, rect, cnt = cull_fp32(geom, G, tile_w, tile_h, views)
     V, n = cnt.shape
     tx_n = (int(desc["n_cols"]) + tile_w - 1) // tile_w
     ty_n = (int(desc["n_rows"]) + tile_h - 1) // tile_h
     T = V * tx_n * ty_n
-    tiles, codes, gids = [], [], []
-    for v in range(V):
-        for k in np.nonzero(cnt[v])[0]:
-            i0, i1, j0, j1 = box[v, k]
-            tx0, tx1, ty0, ty1 = rect[v, k]
-            for ty in range(ty0, ty1 + 1):
-                jl, jh = max(j0 - ty * tile_h, 0), min(j1 - ty * tile_h, tile_h - 1)
-                rb = ((jl + jh) * 8) // tile_h
-                for tx in range(tx0, tx1 + 1):
-                    il, ih = max(i0 - tx * tile_w, 0), min(i1 - tx * tile_w, tile_w - 1)
-                    cb = ((il + ih) * 8) // tile_w
-                    tiles.append(v * tx_n * ty_n + ty * tx_n + tx)
-                    codes.append(rb * 16 + cb)
-                    gids.append(k)
-    tiles = np.asarray(tiles, dtype=np.int64)
-    codes = np.asarray(codes, dtype=np.int64)
-    gids = np.asarray(gids, dtype=np.int64)
-    order = np.lexsort((gids, codes, tiles))
+    # every (view, Gaussian) with a non-empty rectangle, expanded to one entry
+    # per tile of the rectangle (row-major within it)
+    v_idx, k_idx = np.nonzero(cnt)
+    r = rect[v_idx, k_idx].astype(np.int64)
+    nx = r[:, 1] - r[:, 0] + 1
+    c = cnt[v_idx, k_idx].astype(np.int64)
+    first = np.repeat(np.cumsum(c) - c, c)
+    j = np.arange(int(c.sum()), dtype=np.int64) - first        # position in the rectangle
+    ent = np.repeat(np.arange(c.size), c)
+    ty = r[ent, 2] + j // nx[ent]
+    tx = r[ent, 0] + j % nx[ent]
+    tiles = v_idx[ent].astype(np.int64) * tx_n * ty_n + ty * tx_n + tx
+    gids = k_idx[ent].astype(np.int64)
+    order = np.lexsort((gids, tiles))
     tiles, gids = tiles[order], gids[order]
     start = np.zeros(T + 1, dtype=np.int64)
     np.add.at(start, tiles + 1, 1)

@@ -535,8 +535,9 @@ int validate_desc(const rgrt_geom_desc *d)
         return fail(RGRT_E_INVAL, "geometry sizes must be positive (%d views, %d x %d)", d->n_views,
                     d->n_rows, d->n_cols);
     int tw = d->tile_w ? d->tile_w : 16, th = d->tile_h ? d->tile_h : 16;
-    if (tw % 8 || th % 4 || tw * th > 256 || tw * th < 32)
-        return fail(RGRT_E_INVAL, "tile %dx%d: width a multiple of 8, height of 4, 32..256 rays", tw, th);
+    if ((tw != 8 && tw != 16 && tw != 32) || th % 4 || th > 32 || tw * th > 256 || tw * th < 32)
+        return fail(RGRT_E_INVAL, "tile %dx%d: width 8, 16 or 32, height a multiple of 4 up to 32, "
+                    "32..256 rays", tw, th);
     if ((d->n_cols + tw - 1) / tw > 65535 || (d->n_rows + th - 1) / th > 65535)
         return fail(RGRT_E_INVAL, "too many tiles per detector axis");
     const bool pet = d->kind == RGRT_GEOM_PET_RING || d->kind == RGRT_GEOM_PET_3D;
@@ -1288,7 +1289,8 @@ int rgrt_debug_tile_lists(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *g
 {
     TRY(check_ctx(ctx));
     if (!g || !geom || !n_keys_out || !tile_start) return fail(RGRT_E_INVAL, "null argument");
-    if (v0 < 0 || v1 > geom->desc.n_views || v0 >= v1) return fail(RGRT_E_INVAL, "view range");
+    if (geom->rays) return fail(RGRT_E_INVAL, "explicit rays have no tile lists");
+    if (v0 < 0 || v1 > desc_views(&geom->desc) || v0 >= v1) return fail(RGRT_E_INVAL, "view range");
     cudaStream_t s = (cudaStream_t)stream;
     int nv = v1 - v0;
     uint32_t T = (uint32_t)nv * (uint32_t)geom->tiles_per_view;

@@ -602,6 +602,35 @@ int rgrt_autotune_tile(rgrt_ctx *ctx, rgrt_gauss *g, const rgrt_geom_desc *desc,
     return RGRT_OK;
 }
 
+int rgrt_batch_debug_tile_lists(rgrt_batch *b, int scan, int64_t *n_keys_out, uint32_t *tile_start,
+                                uint32_t *gid, int64_t cap)
+{
+    BTRY(check_batch(b));
+    if (scan < 0 || scan >= b->n || !n_keys_out || !tile_start)
+        return report_error(RGRT_E_INVAL, "bad scan index or null argument");
+    const BatchScan &x = b->sc[scan];
+    BK(cudaStreamSynchronize(b->stream));
+    std::vector<uint2> rg(x.T);
+    if (x.T > 0 && x.ranges)
+        BK(cudaMemcpy(rg.data(), x.ranges, sizeof(uint2) * x.T, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> start(x.T + 1, 0);
+    uint32_t pos = 0;
+    for (uint32_t t = 0; t < x.T; t++) {
+        start[t] = pos;
+        if (rg[t].y > rg[t].x) {
+            if (rg[t].x != pos) return report_error(RGRT_E_CUDA, "batch tile ranges are not contiguous");
+            pos = rg[t].y;
+        }
+    }
+    start[x.T] = pos;
+    if (pos > x.cap) return report_error(RGRT_E_CUDA, "batch tile ranges exceed the scan's capacity");
+    *n_keys_out = pos;
+    BK(cudaMemcpy(tile_start, start.data(), sizeof(uint32_t) * (x.T + 1), cudaMemcpyDefault));
+    if ((int64_t)pos > cap) return report_error(RGRT_E_CAPACITY, "tile entries exceed the capacity given");
+    if (pos > 0 && gid) BK(cudaMemcpy(gid, x.vals, sizeof(uint32_t) * pos, cudaMemcpyDefault));
+    return RGRT_OK;
+}
+
 int rgrt_batch_info(rgrt_batch *b, int64_t *work_items, int64_t *key_capacity, int *replans)
 {
     if (!b) return report_error(RGRT_E_INVAL, "null batch");

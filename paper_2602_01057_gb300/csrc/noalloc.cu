@@ -59,14 +59,17 @@ int scratch_base(int dev, void **out)
     return RGRT_OK;
 }
 
-bool on_device(const void *p)
+// device or managed memory of device `dev` (an array on another GPU would be
+// read through peer access, or fault)
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // bump allocator over the scratch array (256-byte aligned pieces)
@@ -115,17 +118,21 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
         return report_error(RGRT_E_CAPACITY,
                             "project_forward_noalloc handles at most 1024 views of 1024 x 1024 pixels");
     const int V = (int)desc_views(d), H = d->n_rows, W = d->n_cols;
-    if (!on_device(out_I) || (n > 0 && !(on_device(mu3) && on_device(logscale3) && on_device(quat4) &&
-                                         on_device(rho))))
-        return report_error(RGRT_E_INVAL, "project_forward_noalloc takes device arrays only");
+    int dev = 0;
+    NA_CK(cudaGetDevice(&dev));
+    if (!on_device(out_I, dev) || (n > 0 && !(on_device(mu3, dev) && on_device(logscale3, dev) &&
+                                              on_device(quat4, dev) && on_device(rho, dev)))) {
+        char msg[160];
+        snprintf(msg, sizeof(msg),
+                 "project_forward_noalloc takes arrays in the memory of the current device (%d) only", dev);
+        return report_error(RGRT_E_INVAL, msg);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t R = (int64_t)V * H * W;
     if (n == 0) {
         NA_CK(cudaMemsetAsync(out_I, 0, sizeof(float) * (size_t)R, s));
         return RGRT_OK;
     }
-    int dev = 0;
-    NA_CK(cudaGetDevice(&dev));
     void *base = nullptr;
     rc = scratch_base(dev, &base);
     if (rc != RGRT_OK) return rc;
@@ -164,12 +171,18 @@ extern "C" int project_forward_noalloc(const rgrt_geom_desc *d, int64_t n, const
     dg.vtab = dg.utab + W;
 
     NA_CK(cudaMemcpyAsync(d_tab, tab, sizeof(float) * ntab, cudaMemcpyHostToDevice, s));
-    NA_CK(launch_records(mu3, logscale3, quat4, rho, n, rec, crec, nullptr, s));
+    // total[1]: the records kernel's flag for non-finite parameters (the
+    // scratch keeps the last call's contents, so it is cleared first)
+    NA_CK(cudaMemsetAsync(total + 1, 0, sizeof(unsigned long long), s));
+    NA_CK(launch_records(mu3, logscale3, quat4, rho, n, rec, crec, (uint32_t *)(total + 1), s));
     NA_CK(launch_cull(dg, V, crec, n, cnt, rect, s));
     NA_CK(launch_scan(cnt, off, E, total, stmp, s));
-    unsigned long long K = 0;
-    NA_CK(cudaMemcpyAsync(&K, total, sizeof(K), cudaMemcpyDeviceToHost, s));
+    unsigned long long tot[2] = { 0, 0 };
+    NA_CK(cudaMemcpyAsync(tot, total, sizeof(tot), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
+    if (tot[1])
+        return report_error(RGRT_E_INVAL, "non-finite Gaussian parameters (mu, log-scale, quaternion or rho)");
+    const unsigned long long K = tot[0];
     // carve the part that depends on the number of (tile, Gaussian) entries
     uint32_t *keys = cv.take<uint32_t>(K);
     uint32_t *vals = cv.take<uint32_t>(K);

@@ -212,23 +212,23 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
     int i1 = upper_idx_g(g.utab, g.n_cols, uhi, g.u0, g.uinv);
     int j0, j1;
     if (g.kind == GM_PET3D) {
-        // 3-D PET (not part of the FP32 culling specification, which covers
-        // the other kinds): the LOR of radial position s and mid-height z has
+        // 3-D PET: the LOR of radial position s and mid-height z has
         // direction e_w + kappa e_v, kappa = dz / (2 sqrt(R^2 - s^2)), and
         // a . x = z along it for a = e_v - kappa e_w, so it can meet the
         // K-sigma ellipsoid only if z lies in mu.a +- sqrt(K^2 a^T Sigma a).
         // Both bounds are convex / concave in kappa, so over the columns
         // i0..i1 the union of these intervals is spanned by their values at
-        // the two extreme slopes.
+        // the two extreme slopes.  Rows are ring pairs (mid-heights
+        // vtab + zoff); rows past the segment's last pair hold no LOR.
         j0 = 0;
         j1 = -1;
         if (i0 <= i1) {
             const int delta = pet3d_delta(g, g.v0 + vl), ad = abs(delta);
-            const float dz = (float)delta * g.ring_pitch, zoff = 0.5f * (float)ad * g.ring_pitch;
+            const float dz = M((float)delta, g.ring_pitch), zoff = M(M(0.5f, (float)ad), g.ring_pitch);
             const float ua = __ldg(g.utab + i0), ub = __ldg(g.utab + i1);
             const float amin = (ua <= 0.0f && ub >= 0.0f) ? 0.0f : fminf(fabsf(ua), fabsf(ub));
             const float amax = fmaxf(fabsf(ua), fabsf(ub));
-            const float h2a = g.radius2 - amin * amin, h2b = g.radius2 - amax * amax;
+            const float h2a = S(g.radius2, M(amin, amin)), h2b = S(g.radius2, M(amax, amax));
             const int last = g.n_rows - 1 - ad;
             if (!(h2b > 0.0f)) {
                 j1 = last;
@@ -238,14 +238,15 @@ __global__ void k_cull(DevGeom g, int nv, const float4 *__restrict__ crec, int64
                 float zlo = INFINITY, zhi = -INFINITY;
 #pragma unroll
                 for (int e = 0; e < 2; e++) {
-                    const float kap = 0.5f * dz / sqrtf(e ? h2b : h2a);
-                    const float zc = mu_v - kap * mu_w;
-                    const float half = sqrtf(fmaxf(K2 * (svv - 2.0f * kap * svw + kap * kap * sww), 0.0f));
-                    zlo = fminf(zlo, zc - half);
-                    zhi = fmaxf(zhi, zc + half);
+                    const float kap = __fdiv_rn(M(0.5f, dz), __fsqrt_rn(e ? h2b : h2a));
+                    const float zc = S(mu_v, M(kap, mu_w));
+                    const float t = A(S(svv, M(M(2.0f, kap), svw)), M(M(kap, kap), sww));
+                    const float half = __fsqrt_rn(fmaxf(M(K2, t), 0.0f));
+                    zlo = fminf(zlo, S(zc, half));
+                    zhi = fmaxf(zhi, A(zc, half));
                 }
-                j0 = lower_idx_g(g.vtab, g.n_rows, zlo - zoff, g.v0f, g.vinv);
-                j1 = min(upper_idx_g(g.vtab, g.n_rows, zhi - zoff, g.v0f, g.vinv), last);
+                j0 = lower_idx_g(g.vtab, g.n_rows, S(zlo, zoff), g.v0f, g.vinv);
+                j1 = min(upper_idx_g(g.vtab, g.n_rows, S(zhi, zoff), g.v0f, g.vinv), last);
             }
         }
     } else {

@@ -84,6 +84,8 @@ _EXPORTS = {
     "rgrt_batch_forward": ([_VP, _VP, _VP], ctypes.c_int),
     "rgrt_batch_loss_step": ([_VP, _VP, ctypes.c_int, ctypes.POINTER(Adam), ctypes.c_int, _VP, _VP],
                              ctypes.c_int),
+    "rgrt_batch_debug_tile_lists": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _VP, _VP,
+                                     ctypes.c_int64], ctypes.c_int),
     "rgrt_batch_info": ([_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "rgrt_autotune_tile": ([_VP, _VP, ctypes.POINTER(GeomDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -366,9 +368,26 @@ def project_backward(ctx, gauss, geom, dLdI, g_mu=None, g_ls=None, g_q=None, g_r
 
 def project_forward_noalloc(desc: dict, mu, ls, q, rho, out, stream=None):
     """Forward projection that allocates no memory (static device scratch);
-    all arrays must be CUDA tensors / device memory."""
+    all arrays must be contiguous float32 CUDA tensors of the current device:
+    mu, ls (n, 3), q (n, 4), rho (n,), out (number of rays,).  The library
+    only sees raw pointers, so shapes and dtypes are checked here (ValueError)
+    before the call."""
+    import torch
+    n = int(mu.shape[0]) if hasattr(mu, "shape") and len(mu.shape) >= 1 else -1
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else -1
+    for name, a, shape in (("mu", mu, (n, 3)), ("ls", ls, (n, 3)), ("q", q, (n, 4)), ("rho", rho, (n,))):
+        if not isinstance(a, torch.Tensor) or not a.is_cuda or a.device.index != dev:
+            raise ValueError(f"{name}: a CUDA tensor of the current device is required")
+        if a.dtype != torch.float32 or tuple(a.shape) != shape or not a.is_contiguous():
+            raise ValueError(f"{name}: contiguous float32 of shape {shape} required, got "
+                             f"{a.dtype} {tuple(a.shape)}")
+    rays = int(desc["n_views"]) * (2 * int(desc.get("max_ring_diff", 0)) + 1 if desc["kind"] == "pet3d" else 1) \
+        * int(desc["n_rows"]) * int(desc["n_cols"])
+    if (not isinstance(out, torch.Tensor) or not out.is_cuda or out.device.index != dev
+            or out.dtype != torch.float32 or out.numel() != rays or not out.is_contiguous()):
+        raise ValueError(f"out: a contiguous float32 CUDA tensor of {rays} elements on the current "
+                         "device is required")
     d, angles = make_desc(desc)
-    n = int(mu.shape[0])
     _check(lib().project_forward_noalloc(ctypes.byref(d), n, _ptr(mu), _ptr(ls), _ptr(q), _ptr(rho),
                                          _ptr(out), _stream(stream)))
     del angles
@@ -418,6 +437,22 @@ class Batch:
         _check(lib().rgrt_batch_loss_step(self.h, ctypes.cast(arr, _VP), int(loss), ctypes.byref(hp),
                                           int(t), _ptr(out), _stream(stream)))
         return out
+
+    def debug_tile_lists(self, scan):
+        """(tile_start[T+1], gid[K]) of scan `scan` as the last forward or
+        step binned it (numpy arrays)."""
+        g = self.geoms[scan]
+        d = g.desc
+        T = int(d["n_views"]) * g.tiles_per_view
+        start = np.zeros(T + 1, np.uint32)
+        nk = ctypes.c_int64()
+        rc = lib().rgrt_batch_debug_tile_lists(self.h, int(scan), ctypes.byref(nk), _ptr(start), None, 0)
+        if rc not in (RGRT_OK, -3):
+            _check(rc)
+        gid = np.zeros(max(nk.value, 1), np.uint32)
+        _check(lib().rgrt_batch_debug_tile_lists(self.h, int(scan), ctypes.byref(nk), _ptr(start), _ptr(gid),
+                                                 gid.size))
+        return start.astype(np.int64), gid[: nk.value].astype(np.int64)
 
     def info(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
@@ -478,7 +513,9 @@ def debug_records(ctx, gauss):
 
 def debug_tile_lists(ctx, gauss, geom, v0=0, v1=None):
     """(tile_start[T+1], gid[K]) of views [v0, v1) as numpy arrays."""
-    v1 = geom.desc["n_views"] if v1 is None else v1
+    d = geom.desc
+    if v1 is None:
+        v1 = int(d["n_views"]) * (2 * int(d.get("max_ring_diff", 0)) + 1 if d["kind"] == "pet3d" else 1)
     T = (v1 - v0) * geom.tiles_per_view
     start = np.zeros(T + 1, np.uint32)
     nk = ctypes.c_int64()

@@ -52,7 +52,7 @@ def test_batch_forward_equals_single_scans(env):
             ref = torch.empty(geom.n_rays, device="cuda")
             rg.project_forward(ctx, g, geom, ref)
             torch.cuda.synchronize()
-            assert torch.equal(o, ref)   # same tiles, same order: identical sums
+            assert torch.equal(o, ref)   # same tiles and pairs: fixed-point sums, identical
 
 
 def test_batch_forward_matches_oracle(env, oracle):
@@ -193,3 +193,27 @@ def test_autotune_returns_a_candidate(env):
     g = rg.Gaussians(ctx, *_dev(torch, G))
     tw, th, ms = rg.autotune_tile(ctx, g, gd, max_views=8)
     assert (tw, th) in {(16, 16), (16, 8), (8, 8), (32, 8)} and ms > 0
+
+
+def test_batch_tile_lists_match_the_oracle(env, oracle):
+    """The batch's own binning (device-side key count, padding keys past the
+    step's entries, shared sort scratch) gives every scan the oracle's FP32
+    tile sets -- scans small enough for the persistent launches and a scan
+    large enough for launches of its own."""
+    torch, rg, ctx = env
+    scans = _scans(5, 5)
+    G, _ = synth.workload_c2(77, n=20_000, n_views=90, side=256)
+    scans.append((G, synth.geom_c2(n_views=90, side=256)))
+    gs = [rg.Gaussians(ctx, *_dev(torch, G)) for G, _ in scans]
+    geoms = [rg.Geometry(ctx, gd) for _, gd in scans]
+    b = rg.Batch(ctx, gs, geoms)
+    outs = [torch.empty(g.n_rays, device="cuda") for g in geoms]
+    for rep in range(2):              # planning pass, then a graph replay
+        b.forward(outs)
+        for i, (G, gd) in enumerate(scans):
+            start, gid = b.debug_tile_lists(i)
+            rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"])
+            assert gid.size == rgid.size and gid.size > 0, (rep, i)
+            assert np.array_equal(start, rstart), (rep, i)
+            tile = np.repeat(np.arange(start.size - 1), np.diff(start))
+            assert np.array_equal(gid[np.lexsort((gid, tile))], rgid), (rep, i)

@@ -113,6 +113,16 @@ def case(name):
         # detector close behind the volume: segments end inside Gaussians
         return (synth.gaussians_uniform(400, 14, log_sigma=math.log(0.08)),
                 synth.geom_cone(6, 48, 40, 0.06, 0.06, 1.6, 2.4))
+    if name == "cone_source_inside":
+        # the sources of views 0 and 3 lie inside the 3-sigma ellipsoids of two
+        # wide Gaussians: their detector box is the whole detector, and every
+        # ray of those views starts inside them (finite-segment erf terms)
+        G = synth.gaussians_uniform(300, 15, half_box=0.8, log_sigma=math.log(0.08))
+        gd = synth.geom_cone(6, 32, 40, 0.08, 0.08, 1.6, 2.4)
+        for k, th in ((0, 0.0), (1, math.pi)):
+            G["mu"][k] = (-1.6 * math.cos(th) + 0.05, -1.6 * math.sin(th) - 0.04, 0.03)
+            G["ls"][k] = (math.log(0.3), math.log(0.22), math.log(0.26))
+        return G, gd
     if name == "pet_arc":
         G, _ = synth.workload_c3(0, n=4000, n_angles=24, n_radial=329, n_planes=63)
         return G, synth.geom_c3(24, 329, 63, arc_mode=0)
@@ -131,7 +141,7 @@ def case(name):
 
 
 FWD_CASES = ["c1", "parallel_ragged", "parallel_infinite", "parallel_short_segment", "cone_small",
-             "cone_near_source", "pet_arc", "pet_raw", "tile8x4", "tile32x8"]
+             "cone_near_source", "cone_source_inside", "pet_arc", "pet_raw", "tile8x4", "tile32x8"]
 
 
 def test_records_bit_exact(rg, ctx, torch, oracle):
@@ -142,17 +152,42 @@ def test_records_bit_exact(rg, ctx, torch, oracle):
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
+def same_tile_sets(start, gid, rstart, rgid):
+    """The GPU's per-tile lists hold exactly the oracle's sets: equal CSR
+    offsets, and equal ids once each tile's entries are put in id order (the
+    order within a tile is the kernel's own; the projection needs none)."""
+    assert gid.size == rgid.size and gid.size > 0
+    assert np.array_equal(start, rstart)
+    tile = np.repeat(np.arange(start.size - 1), np.diff(start))
+    canon = gid[np.lexsort((gid, tile))]
+    assert np.array_equal(canon, rgid)
+
+
 @pytest.mark.parametrize("name", ["c1", "parallel_ragged", "cone_small", "cone_near_source",
-                                  "pet_arc", "pet_raw", "tile8x4"])
+                                  "cone_source_inside", "pet_arc", "pet_raw", "tile8x4"])
 def test_tile_lists_bit_exact(rg, ctx, torch, oracle, name):
     G, gd = case(name)
     geom = rg.Geometry(ctx, gd)
     gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
     start, gid = rg.debug_tile_lists(ctx, gs, geom)
     rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"])
-    assert gid.size == rgid.size and gid.size > 0
-    assert np.array_equal(start, rstart)
-    assert np.array_equal(gid, rgid)
+    same_tile_sets(start, gid, rstart, rgid)
+
+
+@pytest.mark.parametrize("name,views", [("c2", (0, 2)), ("c2", (97, 99)), ("c3", (0, 2)),
+                                        ("c3", (143, 145))])
+def test_tile_lists_bit_exact_full_size(rg, ctx, torch, oracle, name, views):
+    """The benchmark workloads at full size (cone beam: 50,000 Gaussians on
+    256 x 256; PET: 200,000 Gaussians, 329 x 63), lists of two views each."""
+    if name == "c2":
+        G, gd = synth.workload_c2(0)
+    else:
+        G, gd = synth.workload_c3(0)
+    geom = rg.Geometry(ctx, gd)
+    gs = rg.Gaussians(ctx, *[_dev(torch, G)[k] for k in ("mu", "ls", "q", "rho")])
+    start, gid = rg.debug_tile_lists(ctx, gs, geom, *views)
+    rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"], views=views)
+    same_tile_sets(start, gid, rstart, rgid)
 
 
 @pytest.mark.parametrize("name", FWD_CASES)
@@ -168,7 +203,7 @@ def test_forward_parity(rg, ctx, torch, oracle, name):
 
 
 @pytest.mark.parametrize("name", ["c1", "parallel_ragged", "parallel_short_segment", "cone_small",
-                                  "cone_near_source", "pet_arc", "tile8x4"])
+                                  "cone_near_source", "cone_source_inside", "pet_arc", "tile8x4"])
 def test_backward_parity(rg, ctx, torch, oracle, name):
     G, gd = case(name)
     I, gs, geom = gpu_forward(torch, rg, ctx, G, gd)

@@ -125,6 +125,58 @@ def test_forward_and_adjoint(rg, ctx, torch, oracle, name):
         assert grad_err(got, gref, k) < GRAD_TOL, k
 
 
+def same_tile_sets(start, gid, rstart, rgid):
+    """Equal CSR offsets, and equal ids once each tile's entries are put in id
+    order (a tile's list is a set; its order is the kernel's own)."""
+    assert gid.size == rgid.size and gid.size > 0
+    assert np.array_equal(start, rstart)
+    tile = np.repeat(np.arange(start.size - 1), np.diff(start))
+    assert np.array_equal(gid[np.lexsort((gid, tile))], rgid)
+
+
+@pytest.mark.parametrize("name", ["arc", "raw", "tile8x8", "all_ring_pairs", "ragged"])
+def test_tile_lists_bit_exact(rg, ctx, torch, oracle, name):
+    """Candidate lists of the 3-D PET cull (the ring-pair rows and the LOR
+    slopes' z bounds) against the oracle's FP32 specification, every view."""
+    G = phantom(3)
+    gd = scanner(**CASES[name])
+    gs = gaussians(rg, ctx, torch, G)
+    geom = rg.Geometry(ctx, gd)
+    start, gid = rg.debug_tile_lists(ctx, gs, geom)
+    rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"])
+    same_tile_sets(start, gid, rstart, rgid)
+
+
+def test_tile_lists_bit_exact_steep_lors(rg, ctx, torch, oracle):
+    """A small ring (50 mm) with 8 mm ring pitch: LOR slopes 0.24 at the
+    centre and 1.9 at the outermost raw bin (s = 49.6 mm)."""
+    gd = synth.geom_pet3d(6, 25, 8, 50.0, 26, 8.0, 3, arc_mode=1, tile=(8, 4))
+    G = synth.gaussians_uniform(300, 21, half_box=25.0, log_sigma=math.log(4.0))
+    G["mu"][:, 2] *= 0.8
+    gs = gaussians(rg, ctx, torch, G)
+    geom = rg.Geometry(ctx, gd)
+    start, gid = rg.debug_tile_lists(ctx, gs, geom)
+    rstart, rgid = oracle.tile_lists_fp32(gd, G, 8, 4)
+    same_tile_sets(start, gid, rstart, rgid)
+
+
+@pytest.mark.parametrize("seg", [-5, 0, 3, 5])
+def test_tile_lists_bit_exact_full_size(rg, ctx, torch, oracle, seg):
+    """The benchmark scanner at full size (200,000 Gaussians, 32 rings, ring
+    differences up to 5, 288 angles x 329 radial bins): lists of two views
+    (angles 100 and 101) of one segment."""
+    G, _ = synth.workload_c3(0)
+    gd = synth.geom_c3_3d()
+    v0 = (seg + gd["max_ring_diff"]) * gd["n_views"] + 100
+    gs = gaussians(rg, ctx, torch, G)
+    geom = rg.Geometry(ctx, gd)
+    start, gid = rg.debug_tile_lists(ctx, gs, geom, v0, v0 + 2)
+    rstart, rgid = oracle.tile_lists_fp32(gd, G, gd["tile_w"], gd["tile_h"], views=(v0, v0 + 2))
+    same_tile_sets(start, gid, rstart, rgid)
+    gs.close()
+    geom.close()
+
+
 def test_segment_ends_inside_gaussians(rg, ctx, torch, oracle):
     """Gaussians near the ring: LOR ends (on the ring) fall inside their
     3-sigma ellipsoids, so the erf terms matter (the general path)."""

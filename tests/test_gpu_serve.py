@@ -3,10 +3,10 @@
 The jobs (forward, loss + gradient and mini-batch reconstructions, CT and
 PET) first run one at a time, then all together through a server with four
 slots, so that their kernels overlap on the device.  Forward projections and
-losses are deterministic (fixed summation order per ray, FP64 loss partials)
-and must agree bit for bit; gradients are accumulated with float atomics, so
-they agree to rounding: within the projector's gradient tolerance (1e-4
-relative L2).  Reconstructions feed those gradients back through Adam, so
+losses are deterministic (per-ray sums in fixed point, FP64 loss partials in
+a fixed order) and must agree bit for bit; gradients are accumulated with
+float atomics, so they agree to rounding: within the projector's gradient
+tolerance (1e-4 relative L2).  Reconstructions feed those gradients back through Adam, so
 their parameters agree within the same tolerance.  One forward job is also
 checked against the FP64 oracle.
 """

@@ -97,3 +97,80 @@ def test_cull_tiles_not_wider_than_needed(oracle):
     width_tiles = (2 * 3.0104 * smax * mag / g["pitch_u"]) / 8 + 2
     w = rect[..., 1] - rect[..., 0] + 1
     assert np.all(w[cnt > 0] <= np.broadcast_to(width_tiles, w.shape)[cnt > 0] + 1e-9)
+
+
+def _lor_pairs_m(oracle, g, G):
+    """m of every (Gaussian, 3-D PET pixel) whose row holds a LOR, via pair()."""
+    V = g["n_views"] * (2 * g["max_ring_diff"] + 1)
+    H, W = g["n_rows"], g["n_cols"]
+    idx = np.arange(V * H * W)
+    o, d, ta, tb = oracle.rays(g, idx)
+    live = ~((ta == 0.0) & (tb == 0.0))
+    n = G["mu"].shape[0]
+    m = np.full((n, idx.size), np.inf)
+    for k in range(n):
+        for r in np.nonzero(live)[0]:
+            m[k, r] = oracle.pair(o[r], d[r], ta[r], tb[r], G["mu"][k], G["ls"][k], G["q"][k],
+                                  G["rho"][k])[1]
+    return m
+
+
+@pytest.mark.parametrize("arc_mode,n_cryst", [(0, 72), (1, 72), (1, 24)])
+def test_pet3d_cull_is_conservative(oracle, arc_mode, n_cryst):
+    """Fully 3-D PET: every LOR pair with m <= 9 (+ the FP32/FP64 band) lies in
+    a tile the FP32 cull emits.  A ring of 50 mm with 8 mm ring pitch makes
+    the LOR slopes large (kappa up to 0.16 at the centre and more at the
+    edge); with 24 crystals the raw radial bins reach the ring itself
+    (R^2 - s^2 = 0 at the outermost column: every row of the segment)."""
+    g = synth.geom_pet3d(5, 25, 6, 50.0, n_cryst, 8.0, 2, arc_mode=arc_mode)
+    G = synth.gaussians_uniform(20, 70 + arc_mode, half_box=25.0, log_sigma=math.log(4.0))
+    G["mu"][:, 2] *= 0.6
+    tw, th = 4, 2
+    m = _lor_pairs_m(oracle, g, G)
+    box, rect, cnt = oracle.cull_fp32(g, G, tw, th)
+    H, W = g["n_rows"], g["n_cols"]
+    kept = 0
+    for k in range(G["mu"].shape[0]):
+        for r in np.nonzero(m[k] <= 9.0 + oracle.BAND)[0]:
+            i, j, v = r % W, (r // W) % H, r // (W * H)
+            tx0, tx1, ty0, ty1 = rect[v, k]
+            assert cnt[v, k] > 0
+            assert tx0 <= i // tw <= tx1 and ty0 <= j // th <= ty1, (k, v, j, i)
+            kept += 1
+    assert kept > 100
+    # rows past a segment's last ring pair are never emitted
+    D, V = g["max_ring_diff"], g["n_views"]
+    for v in range(V * (2 * D + 1)):
+        ad = abs(v // V - D)
+        on = cnt[v] > 0
+        assert np.all(box[v, on, 3] <= H - 1 - ad)
+
+
+def test_tile_lists_expand_the_rectangles(oracle):
+    """The CSR tile sets equal the cull's rectangles expanded tile by tile
+    (a plain loop over views, Gaussians and tiles here)."""
+    g = synth.geom_pet3d(4, 37, 7, 400.0, 576, 4.0, 2, arc_mode=0)
+    G = synth.gaussians_uniform(80, 71, half_box=40.0, log_sigma=math.log(5.0))
+    G["mu"][:, 2] *= 0.2
+    tw, th = 8, 2
+    box, rect, cnt = oracle.cull_fp32(g, G, tw, th)
+    start, gid = oracle.tile_lists_fp32(g, G, tw, th)
+    V, n = cnt.shape
+    tx_n, ty_n = -(-g["n_cols"] // tw), -(-g["n_rows"] // th)
+    sets = [[] for _ in range(V * tx_n * ty_n)]
+    for v in range(V):
+        for k in range(n):
+            if cnt[v, k] == 0:
+                continue
+            tx0, tx1, ty0, ty1 = rect[v, k]
+            for ty in range(ty0, ty1 + 1):
+                for tx in range(tx0, tx1 + 1):
+                    sets[v * tx_n * ty_n + ty * tx_n + tx].append(k)
+    assert start[-1] == sum(len(s) for s in sets) > 0
+    for t, s in enumerate(sets):
+        assert list(gid[start[t]:start[t + 1]]) == sorted(s)
+    # a view range gives the same tiles, renumbered from its first view
+    s2, g2 = oracle.tile_lists_fp32(g, G, tw, th, views=(5, 9))
+    T0, T1 = 5 * tx_n * ty_n, 9 * tx_n * ty_n
+    assert np.array_equal(s2, start[T0:T1 + 1] - start[T0])
+    assert np.array_equal(g2, gid[start[T0]:start[T1]])
