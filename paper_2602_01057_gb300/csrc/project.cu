@@ -41,7 +41,7 @@ namespace {
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
 // chunk buffers of the forward: with two, a chunk's records are prepared into
 // one buffer while slower warps still read the other, and a single barrier
-// per chunk suffices.  The staged record (SRec, 80 B) leaves the general-path
+// per chunk suffices.  The staged record (SRec, 64 B) leaves the general-path
 // fields in global memory so that two buffers still fit 4 CTAs per SM.
 constexpr int NBUF = 2;
 constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
@@ -63,11 +63,11 @@ struct VRec {
     float4 g2;  // P12 P22, gid bits, 1 = view-space path / 0 = general path
 };
 
-// the forward's shared-memory copy of a VRec: the view-space coefficients,
-// the detector box and (gid, path); general-path records read mu, rho and P
-// from the global records by gid
+// the forward's shared-memory copy of a VRec: the view-space coefficients
+// and (gid, path); general-path records read mu, rho and P from the global
+// records by gid
 struct SRec {
-    float4 c0, c1, c2, bb;
+    float4 c0, c1, c2;
     uint32_t gid;
     float vs;       // 1 = view-space path, 0 = general path
     float pad0, pad1;
@@ -87,14 +87,6 @@ __device__ __forceinline__ GRec load_grec(const float4 *__restrict__ rec, uint32
     return o;
 }
 
-__device__ __forceinline__ float quad_form(const float *Sg, const float *a, const float *b)
-{
-    float t0 = Sg[0] * b[0] + Sg[1] * b[1] + Sg[2] * b[2];
-    float t1 = Sg[1] * b[0] + Sg[3] * b[1] + Sg[4] * b[2];
-    float t2 = Sg[2] * b[0] + Sg[4] * b[1] + Sg[5] * b[2];
-    return a[0] * t0 + a[1] * t1 + a[2] * t2;
-}
-
 __device__ __forceinline__ bool cone_interval(float K2, float dsd, float ae, float aw, float see,
                                               float sew, float sww, float &lo, float &hi)
 {
@@ -109,17 +101,45 @@ __device__ __forceinline__ bool cone_interval(float K2, float dsd, float ae, flo
     return true;
 }
 
-// symmetric X (packed 00 01 02 11 12 22) in the view frame E = [e_u e_v e_w]:
-// out = (X'_uu, X'_uv, X'_uw, X'_vv, X'_vw, X'_ww)
-__device__ __forceinline__ void to_frame(const float *X, const float *eu, const float *ev,
-                                         const float *ew, float *out)
+// Every detector geometry's view frame is a rotation about z (geom_tables):
+// e_v = (0, 0, 1), e_u = (a, b, 0), e_w = (p, q, 0).  The transforms below
+// use that shape: a symmetric X in the frame costs 18 operations instead of
+// six general quadratic forms, and a frame matrix back to world as many.
+struct AxFrame {
+    float a, b, p, q;
+};
+__device__ __forceinline__ AxFrame ax_frame(const float *F)
 {
-    out[0] = quad_form(X, eu, eu);
-    out[1] = quad_form(X, eu, ev);
-    out[2] = quad_form(X, eu, ew);
-    out[3] = quad_form(X, ev, ev);
-    out[4] = quad_form(X, ev, ew);
-    out[5] = quad_form(X, ew, ew);
+    AxFrame f;
+    f.a = F[0]; f.b = F[1]; f.p = F[6]; f.q = F[7];
+    return f;
+}
+
+// X (symmetric, packed 00 01 02 11 12 22) in the frame: (uu, uv, uw, vv, vw, ww)
+__device__ __forceinline__ void to_frame_ax(const float *X, const AxFrame &f, float *o)
+{
+    const float xa = X[0] * f.a + X[1] * f.b, xb = X[1] * f.a + X[3] * f.b;   // X e_u (x, y)
+    const float xp = X[0] * f.p + X[1] * f.q, xq = X[1] * f.p + X[3] * f.q;   // X e_w (x, y)
+    o[0] = f.a * xa + f.b * xb;
+    o[1] = X[2] * f.a + X[4] * f.b;
+    o[2] = f.a * xp + f.b * xq;
+    o[3] = X[5];
+    o[4] = X[2] * f.p + X[4] * f.q;
+    o[5] = f.p * xp + f.q * xq;
+}
+
+// symmetric G' (packed uu uv uw vv vw ww) back to world, G = E G' E^T with
+// E = [e_u e_v e_w]: world x = a u + p w, y = b u + q w, z = v
+__device__ __forceinline__ void from_frame_ax(const float *Gf, const AxFrame &f, float *G)
+{
+    const float hu0 = Gf[0] * f.a + Gf[2] * f.p, hw0 = Gf[2] * f.a + Gf[5] * f.p;
+    const float hu1 = Gf[0] * f.b + Gf[2] * f.q, hw1 = Gf[2] * f.b + Gf[5] * f.q;
+    G[0] = f.a * hu0 + f.p * hw0;
+    G[1] = f.a * hu1 + f.p * hw1;
+    G[2] = f.a * Gf[1] + f.p * Gf[4];
+    G[3] = f.b * hu1 + f.q * hw1;
+    G[4] = f.b * Gf[1] + f.q * Gf[4];
+    G[5] = Gf[3];
 }
 
 // The footprint of a cone-beam record on the detector: rays at offset
@@ -168,19 +188,20 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
     const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
     const float m[3] = { r0.x, r0.y, r0.z };
     const float rho = r0.w, smax = r4.x;
-    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
-    const float mu_u = m[0] * eu[0] + m[1] * eu[1] + m[2] * eu[2];
-    const float mu_v = m[0] * ev[0] + m[1] * ev[1] + m[2] * ev[2];
-    const float mu_w = m[0] * ew[0] + m[1] * ew[1] + m[2] * ew[2];
-    float Pf[6], Sf[6];
-    to_frame(P, eu, ev, ew, Pf);
-    to_frame(Sh, eu, ev, ew, Sf);
+    const AxFrame fr = ax_frame(F);
+    const float mu_u = m[0] * fr.a + m[1] * fr.b;
+    const float mu_v = m[2];
+    const float mu_w = m[0] * fr.p + m[1] * fr.q;
+    float Pf[6], Sf[6], Gf[6];   // P, Sigma / det Sigma and Sigma in the frame
+    to_frame_ax(P, fr, Pf);
+    to_frame_ax(Sh, fr, Sf);
+    to_frame_ax(Sg, fr, Gf);
     float ulo = -INFINITY, uhi = INFINITY, vlo = -INFINITY, vhi = INFINITY;
     bool sat;
     if (CONE) {
         const float D = mu_w + g.dso;           // depth of mu from the source
-        float suu = quad_form(Sg, eu, eu), svv = quad_form(Sg, ev, ev), sww = quad_form(Sg, ew, ew);
-        float suw = quad_form(Sg, eu, ew), svw = quad_form(Sg, ev, ew);
+        float suu = Gf[0], svv = Gf[3], sww = Gf[5];
+        float suw = Gf[2], svw = Gf[4];
         float lo, hi;
         if (cone_interval(Kern<KER>::SKIP, g.dsd, mu_u, D, suu, suw, sww, lo, hi)) { ulo = lo; uhi = hi; }
         if (cone_interval(Kern<KER>::SKIP, g.dsd, mu_v, D, svv, svw, sww, lo, hi)) { vlo = lo; vhi = hi; }
@@ -215,11 +236,11 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         //   A = d~^T P' d~ = P'_ww (1 + kappa (2 P'_vw + kappa P'_vv) / P'_ww),
         // and the integral along the unit ray is |d~| rho sqrt(2 pi / A)
         // exp(-Q / 2A); the coefficients carry the 1/P'_ww.
-        float hu = sqrtf(Kern<KER>::SKIP * quad_form(Sg, eu, eu));
+        float hu = sqrtf(Kern<KER>::SKIP * Gf[0]);
         ulo = mu_u - hu; uhi = mu_u + hu;
         // heights z whose LORs can meet the box ellipsoid (the bounds at the
         // two extreme slopes span those of every slope between them)
-        const float svv = quad_form(Sg, ev, ev), svw = quad_form(Sg, ev, ew), sww = quad_form(Sg, ew, ew);
+        const float svv = Gf[3], svw = Gf[4], sww = Gf[5];
         vlo = INFINITY; vhi = -INFINITY;
 #pragma unroll
         for (int e = 0; e < 2; e++) {
@@ -238,8 +259,8 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         const float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
         sat = rxy + Kern<KER>::BALL * smax <= sqrtf(g.radius2);
     } else {
-        float hu = sqrtf(Kern<KER>::SKIP * quad_form(Sg, eu, eu));
-        float hv = sqrtf(Kern<KER>::SKIP * quad_form(Sg, ev, ev));
+        float hu = sqrtf(Kern<KER>::SKIP * Gf[0]);
+        float hv = sqrtf(Kern<KER>::SKIP * Gf[3]);
         ulo = mu_u - hu; uhi = mu_u + hu; vlo = mu_v - hv; vhi = mu_v + hv;
         const float iA = 1.0f / Pf[5];
         const float rA = sqrtf(iA);
@@ -418,7 +439,6 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
         sv[i].c0 = vr.c0;
         sv[i].c1 = vr.c1;
         sv[i].c2 = vr.c2;
-        sv[i].bb = vr.bb;
         sv[i].gid = gid;
         sv[i].vs = vr.g2.w;
         const float4 bb = vr.bb;
@@ -630,24 +650,6 @@ __global__ void __launch_bounds__(256, 4) k_forward(DevGeom g, const float4 *__r
     forward_tile<GM, STATS, KER>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
 }
 
-// symmetric 3x3 (packed 00 01 02 11 12 22) back to world: G = E G' E^T
-__device__ __forceinline__ void from_frame(const float *Gf, const float *eu, const float *ev,
-                                           const float *ew, float *G)
-{
-    const float *E[3] = { eu, ev, ew };
-    const float M[3][3] = { { Gf[0], Gf[1], Gf[2] }, { Gf[1], Gf[3], Gf[4] }, { Gf[2], Gf[4], Gf[5] } };
-    const int ia[6] = { 0, 0, 0, 1, 1, 2 }, ib[6] = { 0, 1, 2, 1, 2, 2 };
-#pragma unroll
-    for (int e = 0; e < 6; e++) {
-        float s = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) s += E[i][ia[e]] * M[i][j] * E[j][ib[e]];
-        G[e] = s;
-    }
-}
-
 __device__ __forceinline__ void cross_acc(const float *a, const float *b, float s, float *o)
 {
     o[0] += s * (a[1] * b[2] - a[2] * b[1]);
@@ -677,12 +679,12 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
     const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
     const float m[3] = { r0.x, r0.y, r0.z };
     const float alpha = r0.w * Kern<KER>::FAC;
-    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
+    const AxFrame fr = ax_frame(F);
     float Sf[6];
-    to_frame(Sh, eu, ev, ew, Sf);
-    const float mu_u = m[0] * eu[0] + m[1] * eu[1] + m[2] * eu[2];
-    const float mu_v = m[0] * ev[0] + m[1] * ev[1] + m[2] * ev[2];
-    const float mu_w = m[0] * ew[0] + m[1] * ew[1] + m[2] * ew[2];
+    to_frame_ax(Sh, fr, Sf);
+    const float mu_u = m[0] * fr.a + m[1] * fr.b;
+    const float mu_v = m[2];
+    const float mu_w = m[0] * fr.p + m[1] * fr.q;
     const float SQu = alpha * s[0], SQv = alpha * s[1], SQuu = alpha * s[2], SQuv = alpha * s[3],
                 SQvv = alpha * s[4];
     float gu[3], gv[3], d0[3], GPf[6], GSf[6];
@@ -741,12 +743,12 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
         cross_acc(cv, eV, SQvv, T);
     }
     const float dmuf[3] = { -2.0f * T[0], -2.0f * T[1], -2.0f * T[2] };
-    out16[0] = dmuf[0] * eu[0] + dmuf[1] * ev[0] + dmuf[2] * ew[0];
-    out16[1] = dmuf[0] * eu[1] + dmuf[1] * ev[1] + dmuf[2] * ew[1];
-    out16[2] = dmuf[0] * eu[2] + dmuf[1] * ev[2] + dmuf[2] * ew[2];
+    out16[0] = dmuf[0] * fr.a + dmuf[2] * fr.p;
+    out16[1] = dmuf[0] * fr.b + dmuf[2] * fr.q;
+    out16[2] = dmuf[1];
     out16[3] = Kern<KER>::FAC * Sw;
-    from_frame(GPf, eu, ev, ew, out16 + 4);
-    from_frame(GSf, eu, ev, ew, out16 + 10);
+    from_frame_ax(GPf, fr, out16 + 4);
+    from_frame_ax(GSf, fr, out16 + 10);
 }
 
 // Gradient of one Gaussian from its 3-D PET view-space moments, summed over
@@ -768,10 +770,11 @@ __device__ __forceinline__ void pet3d_chain(const float *F, const float4 *rec, u
     const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
     const float P[6] = { r1.x, r1.y, r1.z, r1.w, r2.x, r2.y };
     const float Sh[6] = { r2.z, r2.w, r3.x, r3.y, r3.z, r3.w };
-    const float eu[3] = { F[0], F[1], F[2] }, ev[3] = { F[3], F[4], F[5] }, ew[3] = { F[6], F[7], F[8] };
+    const AxFrame fr = ax_frame(F);
     float Sf[6];
-    to_frame(Sh, eu, ev, ew, Sf);
-    const float ipw = 1.0f / quad_form(P, ew, ew);
+    to_frame_ax(Sh, fr, Sf);
+    const float Pww = (P[0] * fr.p + P[1] * fr.q) * fr.p + (P[1] * fr.p + P[3] * fr.q) * fr.q;
+    const float ipw = 1.0f / Pww;
     const float aw = sqrtf(ipw);
     const float ah = r0.w * Kern<KER>::FAC * aw * ipw;
     float GSf[6], GPf[6];
@@ -796,12 +799,12 @@ __device__ __forceinline__ void pet3d_chain(const float *F, const float4 *rec, u
     T[1] = -M0 * (-cu[0]) + M2 * (-cv[0]) + M3 * cw[0];
     T[2] = -M1 * cu[0] + M3 * cv[0] - M4 * cw[0];
     const float dmuf[3] = { 2.0f * ah * T[0], 2.0f * ah * T[1], 2.0f * ah * T[2] };
-    out16[0] = dmuf[0] * eu[0] + dmuf[1] * ev[0] + dmuf[2] * ew[0];
-    out16[1] = dmuf[0] * eu[1] + dmuf[1] * ev[1] + dmuf[2] * ew[1];
-    out16[2] = dmuf[0] * eu[2] + dmuf[1] * ev[2] + dmuf[2] * ew[2];
+    out16[0] = dmuf[0] * fr.a + dmuf[2] * fr.p;
+    out16[1] = dmuf[0] * fr.b + dmuf[2] * fr.q;
+    out16[2] = dmuf[1];
     out16[3] = Kern<KER>::FAC * aw * s[14];
-    from_frame(GPf, eu, ev, ew, out16 + 4);
-    from_frame(GSf, eu, ev, ew, out16 + 10);
+    from_frame_ax(GPf, fr, out16 + 4);
+    from_frame_ax(GSf, fr, out16 + 10);
 }
 
 // Adjoint, one Gaussian per thread.  A CTA takes a tile: it stages the
