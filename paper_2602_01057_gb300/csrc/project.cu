@@ -1000,60 +1000,71 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             }
         }
         if (P3 && __any_sync(0xffffffffu, active && vs)) {
+            // columns outer: the LOR slope kappa is fixed along a column, so
+            // the column's kappa terms are taken once and its rows need only
+            // five kappa-free sums (h, h v~, h v~^2, gA, w), folded into the 15
+            // moments with the column's du and kappa powers afterwards
             const float4 c0 = r.c0, c1 = r.c1, c2 = r.c2;
             float s[15];
 #pragma unroll
             for (int q = 0; q < 15; q++) s[q] = 0.0f;
-            for (int j = 0; j < TH; j++) {
-                const bool rowin = active && vs && j >= jlo && j <= jhi;
-                const uint32_t need = __reduce_or_sync(0xffffffffu, rowin ? groups : 0u);
-                if (need == 0u || !rowin) continue;
-                const float dv = svr[j] - c0.y;
-                const float *gl_row = sgl + j * TW;
-#pragma unroll
-                for (int c8 = 0; c8 < TW / 8; c8++) {
-                if (!((need >> c8) & 1u)) continue;
-#pragma unroll
-                for (int i = 8 * c8; i < 8 * c8 + 8; i++) {
-                    const float du = su[i] - c0.x, kap = skap[i];
-                    const float vt = fmaf(kap, c0.z, dv);
-                    const float muu = fmaf(fmaf(c1.z, kap, c1.y), kap, c1.x);
-                    const float muv2 = fmaf(c2.x, kap, c1.w);
-                    const float qv = du * (muu * du + muv2 * vt) + c0.w * vt * vt;
-                    const float rA = rsqrt_approx(fmaf(fmaf(c2.z, kap, c2.y), kap, 1.0f));
-                    const float iA = rA * rA;
+#pragma unroll 1
+            for (int i = 0; i < TW; i++) {
+                const bool colin = active && vs && i >= ilo && i <= ihi;
+                if (!__any_sync(0xffffffffu, colin)) continue;
+                // rows that any lane's box holds in this column
+                const int rlo = __reduce_min_sync(0xffffffffu, colin ? jlo : TH);
+                const int rhi = __reduce_max_sync(0xffffffffu, colin ? jhi : -1);
+                if (!colin) continue;
+                const float du = su[i] - c0.x, kap = skap[i];
+                const float muu = fmaf(fmaf(c1.z, kap, c1.y), kap, c1.x);
+                const float muv2 = fmaf(c2.x, kap, c1.w);
+                const float rA = rsqrt_approx(fmaf(fmaf(c2.z, kap, c2.y), kap, 1.0f));
+                const float iA = rA * rA;
+                const float Kq = muu * du * du, Lq = muv2 * du;
+                const float vt0 = fmaf(kap, c0.z, -c0.y);     // v~ = v + vt0
+                float H0 = 0.0f, Hv = 0.0f, Hvv = 0.0f, G0 = 0.0f, W = 0.0f;
+                for (int j = rlo; j <= rhi; j++) {
+                    const float vt = svr[j] + vt0;
+                    const float qv = fmaf(fmaf(c0.w, vt, Lq), vt, Kq);   // du (muu du + muv2 v~) + S_uu v~^2
                     const float arg = qv * iA;
+                    const float gl = sgl[j * TW + i];
                     float wv, h, gA;
                     if (KER == 1) {
                         const float c = 1.0f + arg;
                         const float sc = c > 0.0f ? sqrt_approx(c) : 0.0f;
-                        const float t = gl_row[i] * rA * sc;
+                        const float t = gl * rA * sc;
                         wv = t * c;
                         h = (1.5f / Kern<1>::KAPPA2) * t * iA;
                         gA = t * iA * (1.5f - 2.0f * c);
                     } else {
-                        wv = arg >= CUT_ARG ? gl_row[i] * rA * ex2_approx(arg) : 0.0f;
+                        wv = arg >= CUT_ARG ? gl * rA * ex2_approx(arg) : 0.0f;
                         h = 0.5f * wv * iA;
                         gA = h * (arg * M_PER_ARG - 1.0f);
                     }
-                    const float hd = h * du, hv = h * vt, hdk = hd * kap, hdkk = hdk * kap, gk = gA * kap;
-                    s[0] = fmaf(hv, vt, s[0]);
-                    s[1] = fmaf(hv, du, s[1]);
-                    s[2] = fmaf(hdk, vt, s[2]);
-                    s[3] = fmaf(hd, du, s[3]);
-                    s[4] = fmaf(hdk, du, s[4]);
-                    s[5] = fmaf(hdkk, du, s[5]);
-                    s[6] += hv;
-                    s[7] = fmaf(hv, kap, s[7]);
-                    s[8] += hd;
-                    s[9] += hdk;
-                    s[10] += hdkk;
-                    s[11] += gA;
-                    s[12] += gk;
-                    s[13] = fmaf(gk, kap, s[13]);
-                    s[14] += wv;
+                    const float hv = h * vt;
+                    H0 += h;
+                    Hv += hv;
+                    Hvv = fmaf(hv, vt, Hvv);
+                    G0 += gA;
+                    W += wv;
                 }
-                }
+                const float hd = H0 * du, hvd = Hv * du, kk = kap * kap;
+                s[0] += Hvv;
+                s[1] += hvd;
+                s[2] = fmaf(kap, hvd, s[2]);
+                s[3] = fmaf(hd, du, s[3]);
+                s[4] = fmaf(kap * hd, du, s[4]);
+                s[5] = fmaf(kk * hd, du, s[5]);
+                s[6] += Hv;
+                s[7] = fmaf(kap, Hv, s[7]);
+                s[8] += hd;
+                s[9] = fmaf(kap, hd, s[9]);
+                s[10] = fmaf(kk, hd, s[10]);
+                s[11] += G0;
+                s[12] = fmaf(kap, G0, s[12]);
+                s[13] = fmaf(kk, G0, s[13]);
+                s[14] += W;
             }
             if (active && vs) {
 #pragma unroll
