@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(EMIT_BS) k_emit(DevGeom g, int nv, int64_t n,
 }
 
 constexpr int SORT_BS = 256;     // one thread per digit value
-constexpr int SORT_ITEMS = 8;    // keys per thread
+constexpr int SORT_ITEMS = 16;   // keys per thread
 constexpr int SORT_TILE = SORT_BS * SORT_ITEMS;
 constexpr int SORT_WARPS = SORT_BS / 32;
 constexpr int SORT_WSEG = 32 * SORT_ITEMS;   // keys of one warp's segment
