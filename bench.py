@@ -69,6 +69,9 @@ WORKLOADS = {
              "rings of 576 crystals (radius 400 mm, ring pitch 4 mm), ring differences up to 5 (11 segments), "
              "288 angles x 329 arc-corrected radial bins (30.5M LORs; 33.4M sinogram bins with the rows "
              "past each segment's last ring pair)",
+    "c3-tof": "time-of-flight PET fwd+bwd (Poisson NLL + Adam): the C3 workload (200,000 Gaussians, 288 x 329 "
+              "x 63 arc-corrected sinogram) with 13 TOF bins per LOR (47 mm apart, Gaussian TOF kernel of "
+              "31.85 mm, 500 ps FWHM): 77.6M outputs",
     "pet3d-rays": "the LORs of pet3d as explicit rays (geometry_set_rays, no detector structure), fwd+bwd "
                   "(Poisson NLL + Adam)",
     "helical": "helical cone-beam CT as explicit rays (geometry_set_rays): the 50,000 Gaussians of the "
@@ -139,6 +142,10 @@ def _workload(name, seed):
         G, _ = synth.workload_c3(seed)
         true = synth.perturbed(G, seed + 101, pos_std=1.0)
         return G, true, synth.geom_c3_3d(), "poisson"
+    if name == "c3-tof":
+        G, gd = synth.workload_c3(seed)
+        true = synth.perturbed(G, seed + 101, pos_std=1.0)
+        return G, true, synth.with_tof_bins(gd, *TOF_BINS), "poisson"
     if name == "c1":
         G, gd = synth.workload_c1(seed)
         true = synth.perturbed(G, seed + 101, pos_std=0.01)
@@ -533,7 +540,7 @@ def measure_step(args, name, rgrt, ctx, dev, seed, world, rank, local, cpu=True,
         sm_mhz = peaks["sm_max_mhz"] or 2070.0
         note = "no clock samples: the maximum SM clock"
     STEPS_TIMED[0] = args.steps
-    n_views = synth.num_rays(gd) // (int(gd["n_rows"]) * int(gd["n_cols"]))
+    n_views = synth.num_rays(gd) // (int(gd["n_rows"]) * int(gd["n_cols"]) * max(1, int(gd.get("n_tof", 0))))
     tiles = n_views * geom.tiles_per_view
     roof = roofline(kernels, pairs, st["keys"], int(G["mu"].shape[0]), n_views, tiles, n_sm, sm_mhz, note,
                     peaks, name, TRAFFIC)
@@ -557,6 +564,8 @@ def measure_step(args, name, rgrt, ctx, dev, seed, world, rank, local, cpu=True,
     # end to end: host parameters in, step, host loss + parameters out
     if not args.no_e2e:
         line["e2e"] = e2e(args, rgrt, ctx, geom, G, y, lkind, hp, R, world)
+    if name == "c3-tof":
+        line["vs_explicit_rays"] = tof_vs_explicit(rgrt, G, dev)
     if name in ("c2", "c3") and not args.no_fitted:
         line["fitted"] = fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world)
     if cpu and rank == 0 and not args.no_cpu_baseline:
@@ -566,6 +575,53 @@ def measure_step(args, name, rgrt, ctx, dev, seed, world, rank, local, cpu=True,
     geom.close()
     del flush
     return line
+
+
+def tof_vs_explicit(rgrt, G, dev, n_angles=32, reps=3):
+    """Forward and adjoint of the TOF sinogram against the same LORs and TOF
+    kernels as explicit rays (geometry_set_rays_tof), on the first n_angles
+    angles of the sinogram: ms per pass of each and the ratio."""
+    import torch
+    ctx = rgrt.Context(dev.index or 0)
+    sub = synth.geom_pet(288, 329, 63, 400.0, 576, 2.0)
+    sub["angles"] = (math.pi * np.arange(n_angles) / 288.0).astype(np.float64)
+    sub["n_views"] = n_angles
+    gd = synth.with_tof_bins(sub, *TOF_BINS)
+    nl = synth.num_rays(sub)
+    o, d, ta, tb = synth.pet_lors(sub)
+    nb, h, sig = TOF_BINS
+    centres = (np.arange(nb) - 0.5 * (nb - 1)) * h
+    R = dict(kind="rays", o=np.tile(o, (nb, 1)).astype(np.float32), d=np.tile(d, (nb, 1)).astype(np.float32),
+             t=np.tile(np.stack([ta, tb], 1), (nb, 1)).astype(np.float32),
+             tof=np.stack([np.repeat(centres, nl) + np.tile(0.5 * (ta + tb), nb), np.full(nb * nl, sig)],
+                          1).astype(np.float32))
+    gs = rgrt.Gaussians(ctx, *[torch.from_numpy(G[k]).to(dev) for k in ("mu", "ls", "q", "rho")])
+    out = {}
+    for name, desc in (("sinogram", gd), ("explicit_rays", R)):
+        geom = rgrt.Geometry(ctx, desc)
+        I = torch.empty(geom.n_rays, device=dev)
+        w = torch.ones(geom.n_rays, device=dev)
+        grads = [torch.empty(sz, device=dev) for sz in ((gs.n, 3), (gs.n, 3), (gs.n, 4), (gs.n,))]
+        rgrt.project_forward(ctx, gs, geom, I)
+        rgrt.project_backward(ctx, gs, geom, w, *grads)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        for _ in range(reps):
+            rgrt.project_forward(ctx, gs, geom, I)
+        e[1].record()
+        for _ in range(reps):
+            rgrt.project_backward(ctx, gs, geom, w, *grads)
+        e[2].record()
+        torch.cuda.synchronize()
+        out[name] = dict(forward_ms=e[0].elapsed_time(e[1]) / reps, backward_ms=e[1].elapsed_time(e[2]) / reps)
+        geom.close()
+    gs.close()
+    ctx.close()
+    s, x = out["sinogram"], out["explicit_rays"]
+    return dict(angles=n_angles, outputs=nb * nl, sinogram=s, explicit_rays=x,
+                speedup=(x["forward_ms"] + x["backward_ms"]) / (s["forward_ms"] + s["backward_ms"]),
+                note="forward + adjoint of the same LORs and TOF kernels (first angles of the sinogram)")
 
 
 def run_ours(args):
@@ -608,6 +664,8 @@ def run_ours(args):
 
 
 EXTRA_STEPS, EXTRA_WARMUP = 3, 2
+# time of flight of the TOF PET workload: bins, spacing (mm), kernel width (mm)
+TOF_BINS = (13, 47.0, 31.85)
 
 
 def fitted(args, rgrt, ctx, geom, gs, y, lkind, hp, step, R, world):

@@ -205,6 +205,26 @@ int geometry_set_rays(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const floa
  * RGRT_E_INVAL).  RGRT_E_INVAL also for a NaN width or centre. */
 int geometry_set_rays_tof(rgrt_ctx *ctx, int64_t n_rays, const float *o3, const float *d3,
                           const float *t2, const float *tof2, rgrt_geom **out);
+
+/* Largest number of time-of-flight bins per LOR of a sinogram geometry. */
+#define RGRT_TOF_MAX_BINS 16
+
+/* Time of flight on a PET ring sinogram (RGRT_GEOM_PET_RING; the paper's
+ * future-work section plans TOF PET): every LOR is measured in n_tof bins
+ * (1..RGRT_TOF_MAX_BINS), bin k weighting the line by the Gaussian kernel
+ * N(t; t_k, sigma^2) with t measured along the LOR from its midpoint (the
+ * transaxial plane's chord centre) and t_k = (k - (n_tof - 1)/2) spacing
+ * (same length unit as the geometry).  The outputs become n_tof per LOR,
+ * bin outermost: I[bin][plane][angle][radial] (geometry_num_rays = n_tof x
+ * sinogram size), as do the losses' measurements and the measurement model's
+ * arrays (set those after this call).  Tile lists are those of the sinogram
+ * (one binning serves every bin).  A pair still counts by its spatial
+ * m <= 9.  Gaussian kernel only (projections of an Epanechnikov set return
+ * RGRT_E_INVAL).  RGRT_E_INVAL for another geometry kind, a bin count out
+ * of range, or a spacing or width that is not positive and finite. */
+int geometry_set_tof(rgrt_geom *g, int n_tof, float spacing, float sigma);
+
+/* Outputs of a geometry: rays, or (time-of-flight bin, LOR) pairs. */
 int64_t geometry_num_rays(const rgrt_geom *g);
 
 /* Measurement model of the losses (the attenuation, scatter and randoms that

@@ -60,6 +60,10 @@
  *   Pixel coordinates: u_i = (i - (n_cols-1)/2) pitch_u, v_j likewise.
  *   Output layout: CT [view][row][col]; PET [plane][angle][radial];
  *   3-D PET [segment][angle][ring pair][radial].
+ *   Time of flight (PET kinds, n_tof > 0): every LOR carries n_tof outputs,
+ *   TOF bin k weighting the line by N(t; t_k, sigma_T^2) with t measured
+ *   along the LOR from its midpoint and t_k = (k - (n_tof - 1)/2) spacing;
+ *   output [k][the layout above].
  *
  * It also holds an FP32 replica of the culling predicate (records and
  * detector bounding boxes) used only to check that the GPU tile lists are
@@ -79,6 +83,11 @@ typedef struct {
     const double *angles;
     double pitch_u, pitch_v, t_a, t_b, dso, dsd, radius;
     int32_t n_crystals, arc_mode, max_ring_diff;
+    /* time of flight on PET LORs (n_tof = 0: none): n_tof bins centred at
+     * t_k = (k - (n_tof - 1)/2) tof_spacing along the LOR from its midpoint,
+     * each weighting the line by N(t; t_k, tof_sigma^2) */
+    int32_t n_tof;
+    double tof_spacing, tof_sigma;
 } og_geom;
 
 #define OG_PARALLEL 0
@@ -90,6 +99,24 @@ typedef struct {
 static int og_nviews(const og_geom *g)
 {
     return g->kind == OG_PET3D ? g->n_views * (2 * g->max_ring_diff + 1) : g->n_views;
+}
+
+/* outputs per LOR: its time-of-flight bins (1 without time of flight) */
+static int og_tof_bins(const og_geom *g)
+{
+    return g->n_tof > 0 ? g->n_tof : 1;
+}
+
+/* centre (along the LOR from its midpoint) and 1/sigma^2 of TOF bin k (0, 0
+ * without time of flight) */
+static void og_tof(const og_geom *g, int k, double *tc, double *tau)
+{
+    *tc = 0.0;
+    *tau = 0.0;
+    if (g->n_tof > 0) {
+        *tc = ((double)k - 0.5 * (double)(g->n_tof - 1)) * g->tof_spacing;
+        *tau = 1.0 / (g->tof_sigma * g->tof_sigma);
+    }
 }
 
 /* 3-D PET: ring difference of view v */
@@ -637,17 +664,25 @@ void or_cov(int64_t n, const float *ls, const float *q, double *sig9, double *p9
     }
 }
 
-int64_t or_num_rays(const og_geom *g)
+/* LORs / detector rays of the geometry (one per pixel of every view) */
+static int64_t og_num_lors(const og_geom *g)
 {
     return (int64_t)og_nviews(g) * g->n_rows * g->n_cols;
 }
 
-/* rays for flat output indices */
+/* outputs: with time of flight, TOF bin k of LOR x is output k * lors + x */
+int64_t or_num_rays(const og_geom *g)
+{
+    return og_num_lors(g) * og_tof_bins(g);
+}
+
+/* rays for flat output indices (the LOR of a time-of-flight output) */
 void or_rays(const og_geom *g, int64_t n, const int64_t *idx, double *o, double *d, double *ta, double *tb)
 {
+    const int64_t nl = og_num_lors(g);
     for (int64_t r = 0; r < n; r++) {
         int v, j, i;
-        og_unflatten(g, idx[r], &v, &j, &i);
+        og_unflatten(g, idx[r] % nl, &v, &j, &i);
         og_ray(g, v, j, i, o + 3 * r, d + 3 * r, ta + r, tb + r);
     }
 }
@@ -696,11 +731,15 @@ void or_forward(const og_geom *g, int64_t n, const float *mu, const float *ls, c
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
                     if (!og_ray(g, v, j, i, o, d, &ta, &tb)) continue;
-                    og_pairval r;
-                    og_eval(o, d, ta, tb, m3, P[k], rho[k], 0.0, 0.0, &r);
-                    int64_t x = og_index(g, v, j, i);
-                    og_accum(r.f, r.m, cut2, band, I + x, Ilo + x, Ihi + x);
-                    if (r.m <= cut2) npair++;
+                    for (int b = 0; b < og_tof_bins(g); b++) {
+                        double tc, tau;
+                        og_tof(g, b, &tc, &tau);
+                        og_pairval r;
+                        og_eval(o, d, ta, tb, m3, P[k], rho[k], tc, tau, &r);
+                        int64_t x = og_index(g, v, j, i) + b * og_num_lors(g);
+                        og_accum(r.f, r.m, cut2, band, I + x, Ilo + x, Ihi + x);
+                        if (b == 0 && r.m <= cut2) npair++;
+                    }
                 }
         }
     }
@@ -719,7 +758,9 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t r = 0; r < nr; r++) {
         int v, j, i;
-        og_unflatten(g, idx[r], &v, &j, &i);
+        og_unflatten(g, idx[r] % og_num_lors(g), &v, &j, &i);
+        double tc, tau;
+        og_tof(g, (int)(idx[r] / og_num_lors(g)), &tc, &tau);
         double o[3], d[3], ta, tb;
         const int has = og_ray(g, v, j, i, o, d, &ta, &tb);
         double s = 0.0, slo = 0.0, shi = 0.0;
@@ -727,7 +768,7 @@ void or_forward_rays(const og_geom *g, int64_t n, const float *mu, const float *
         for (int64_t k = 0; k < n; k++) {
             double m3[3] = { mu[3 * k], mu[3 * k + 1], mu[3 * k + 2] };
             og_pairval pv;
-            og_eval(o, d, ta, tb, m3, P[k], rho[k], 0.0, 0.0, &pv);
+            og_eval(o, d, ta, tb, m3, P[k], rho[k], tc, tau, &pv);
             og_accum(pv.f, pv.m, cut2, band, &s, &slo, &shi);
         }
         I[r] = s; Ilo[r] = slo; Ihi[r] = shi;
@@ -822,8 +863,13 @@ void or_backward(const og_geom *g, int64_t n, const float *mu, const float *ls, 
                 for (int i = i0; i <= i1; i++) {
                     double o[3], d[3], ta, tb;
                     if (!og_ray(g, v, j, i, o, d, &ta, &tb)) continue;
-                    og_grad_pair(&acc, o, d, ta, tb, 0.0, 0.0, m3, P, rho[k], dLdI[og_index(g, v, j, i)], cut2,
-                                 band, ls + 3 * k, q + 4 * k);
+                    for (int b = 0; b < og_tof_bins(g); b++) {
+                        double tc, tau;
+                        og_tof(g, b, &tc, &tau);
+                        og_grad_pair(&acc, o, d, ta, tb, tc, tau, m3, P, rho[k],
+                                     dLdI[og_index(g, v, j, i) + b * og_num_lors(g)], cut2, band, ls + 3 * k,
+                                     q + 4 * k);
+                    }
                 }
         }
         og_grad_finish(&acc, k, ls + 3 * k, q + 4 * k, g_mu, g_ls, g_q, g_rho, lohi);

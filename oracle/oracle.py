@@ -47,6 +47,7 @@ class _Geom(ctypes.Structure):
         ("dso", ctypes.c_double), ("dsd", ctypes.c_double), ("radius", ctypes.c_double),
         ("n_crystals", ctypes.c_int32), ("arc_mode", ctypes.c_int32),
         ("max_ring_diff", ctypes.c_int32),
+        ("n_tof", ctypes.c_int32), ("tof_spacing", ctypes.c_double), ("tof_sigma", ctypes.c_double),
     ]
 
 
@@ -94,10 +95,13 @@ class Geometry:
             float(desc.get("t_a", 0.0)), float(desc.get("t_b", 0.0)),
             float(desc.get("dso", 0.0)), float(desc.get("dsd", 0.0)),
             float(desc.get("radius", 0.0)), int(desc.get("n_crystals", 0)),
-            int(desc.get("arc_mode", 0)), int(desc.get("max_ring_diff", 0)))
+            int(desc.get("arc_mode", 0)), int(desc.get("max_ring_diff", 0)),
+            int(desc.get("n_tof", 0)), float(desc.get("tof_spacing", 0.0)), float(desc.get("tof_sigma", 0.0)))
         self.n_views = int(desc["n_views"]) * (2 * int(desc.get("max_ring_diff", 0)) + 1
                                                if desc["kind"] == "pet3d" else 1)
-        self.n_rays = self.n_views * int(desc["n_rows"]) * int(desc["n_cols"])
+        # outputs: with time of flight, n_tof per LOR (TOF bin outermost)
+        self.n_lors = self.n_views * int(desc["n_rows"]) * int(desc["n_cols"])
+        self.n_rays = self.n_lors * max(1, int(desc.get("n_tof", 0)))
 
     @property
     def ref(self):

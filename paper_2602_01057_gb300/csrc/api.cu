@@ -464,6 +464,8 @@ int run_forward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, float
         }
         return run_forward_rays(ctx, g, geom, out, s);
     }
+    if (geom->dg.n_tof && g->kernel != RGRT_KERNEL_GAUSSIAN)
+        return fail(RGRT_E_INVAL, "time of flight takes the Gaussian kernel");
     if (g->n == 0) {
         CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)geom->n_rays, s));
         return RGRT_OK;
@@ -513,6 +515,8 @@ int run_backward(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, cons
         CK(launch_param_chain(g->mu, g->ls, g->q, g->rho, N, (float4 *)ctx->grad.p, gm, gl, gq, gr, s));
         return RGRT_OK;
     }
+    if (geom->dg.n_tof && g->kernel != RGRT_KERNEL_GAUSSIAN)
+        return fail(RGRT_E_INVAL, "time of flight takes the Gaussian kernel");
     TRY(for_chunks(ctx, g, geom, s, reuse, [&](int v0, int nv, uint32_t K) -> int {
         (void)K;
         DevGeom dg = geom->dg;
@@ -976,6 +980,29 @@ static int set_ray_array(rgrt_ctx *ctx, float **dst, const float *src, int64_t n
     }
     if (!*dst) TRY(dev_alloc(ctx, (void **)dst, bytes));
     CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyDefault));
+    return RGRT_OK;
+}
+
+int geometry_set_tof(rgrt_geom *g, int n_tof, float spacing, float sigma)
+{
+    if (!g) return fail(RGRT_E_INVAL, "null geometry");
+    TRY(check_ctx(g->ctx));
+    if (g->rays || g->desc.kind != RGRT_GEOM_PET_RING)
+        return fail(RGRT_E_INVAL, "time-of-flight bins apply to PET ring sinograms");
+    if (n_tof < 1 || n_tof > RGRT_TOF_MAX_BINS)
+        return fail(RGRT_E_INVAL, "%d time-of-flight bins (1..%d)", n_tof, RGRT_TOF_MAX_BINS);
+    if (!(spacing > 0.0f) || !std::isfinite(spacing) || !(sigma > 0.0f) || !std::isfinite(sigma))
+        return fail(RGRT_E_INVAL, "time-of-flight spacing and width must be positive and finite");
+    if (g->d_mult || g->d_add)
+        return fail(RGRT_E_INVAL, "set the measurement model after the time-of-flight bins");
+    const int64_t lors = desc_rays(&g->desc);
+    g->dg.n_tof = n_tof;
+    g->dg.tof_h = spacing;
+    g->dg.tof_t0 = -0.5f * (float)(n_tof - 1) * spacing;
+    g->dg.tof_s2 = sigma * sigma;
+    g->dg.tof_tau = 1.0f / (sigma * sigma);
+    g->dg.stride_tof = lors;
+    g->n_rays = lors * n_tof;
     return RGRT_OK;
 }
 

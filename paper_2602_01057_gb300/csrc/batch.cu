@@ -403,9 +403,9 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g, const rg
             delete b;
             return report_error(RGRT_E_INVAL, "batch scan with a null handle or one of another context");
         }
-        if (geom[i]->rays || geom[i]->dg.kind == GM_PET3D) {
+        if (geom[i]->rays || geom[i]->dg.kind == GM_PET3D || geom[i]->dg.n_tof) {
             delete b;
-            return report_error(RGRT_E_INVAL, "explicit-ray and 3-D PET geometries are not batched");
+            return report_error(RGRT_E_INVAL, "explicit-ray, 3-D PET and time-of-flight geometries are not batched");
         }
         if (g[i]->kernel != RGRT_KERNEL_GAUSSIAN) {
             delete b;

@@ -61,6 +61,7 @@ struct VRec {
     float4 g0;  // mu, rho                      (general path)
     float4 g1;  // P00 P01 P02 P11              (general path)
     float4 g2;  // P12 P22, gid bits, 1 = view-space path / 0 = general path
+    float4 t4;  // parallel rays: the closest approach along the ray, t* = x + y du + z dv, and 1/A (w)
 };
 
 // the forward's shared-memory copy of a VRec: the view-space coefficients
@@ -182,6 +183,7 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
     constexpr bool CONE = GM == GM_CONE;
     const float4 *r = rec + REC_F4 * (size_t)gid;
     float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
+    out.t4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 k1 = __ldg(crec + CREC_F4 * (size_t)gid + 1), k2 = __ldg(crec + CREC_F4 * (size_t)gid + 2);
     const float Sg[6] = { k1.x, k1.y, k1.z, k1.w, k2.x, k2.y };
     const float P[6] = { r1.x, r1.y, r1.z, r1.w, r2.x, r2.y };
@@ -269,6 +271,9 @@ __device__ __forceinline__ void prep_record(const DevGeom &g, const float *F, ui
         out.c0 = make_float4(mu_u, mu_v, k * Sf[3], -2.0f * k * Sf[1]);
         out.c1 = make_float4(k * Sf[0], iA, rA, 0.0f);
         out.c2 = make_float4(0.0f, 0.0f, 0.0f, rho * Kern<KER>::FAC * rA);
+        // along the ray (direction e_w) the exponent is smallest at
+        // t* = mu_w - (P'_uw du + P'_vw dv) / P'_ww
+        out.t4 = make_float4(mu_w, -Pf[2] * iA, -Pf[4] * iA, iA);
 
         if (g.pet) {
             float rxy = sqrtf(m[0] * m[0] + m[1] * m[1]);
@@ -425,7 +430,7 @@ struct ChunkLists {
     uint8_t gen[8][CH];
 };
 
-template <int GM, int KER>
+template <int GM, int KER, bool TOF>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
                                            uint32_t base, uint32_t stride, int cnt,
                                            const float4 *rec, const float4 *crec, SRec *sv,
@@ -436,6 +441,19 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
         const uint32_t gid = __ldg(gids + base + (uint32_t)i * stride);
         VRec vr;
         prep_record<GM, KER>(g, F, gid, rec, crec, vr, kap0, kap1);
+        if (TOF) {
+            // time of flight (parallel rays): the pair's value times the
+            // kernel of width s^2 = 1/A + sigma_T^2 at t* - t_k (the
+            // convolution of the Gaussian's profile along the ray with the
+            // TOF kernel): c1.y = -log2(e) / (2 s^2), c1.z = 1/sqrt(2 pi s^2),
+            // c2.xyz = the coefficients of t*
+            const float s2 = vr.t4.w + g.tof_s2;
+            vr.c1.y = Kern<0>::QSCALE / s2;
+            vr.c1.z = rsqrtf(2.0f * 3.14159265358979324f * s2);
+            vr.c2.x = vr.t4.x;
+            vr.c2.y = vr.t4.y;
+            vr.c2.z = vr.t4.z;
+        }
         sv[i].c0 = vr.c0;
         sv[i].c1 = vr.c1;
         sv[i].c2 = vr.c2;
@@ -550,7 +568,7 @@ __device__ __forceinline__ bool vs_keep(float arg)
 }
 
 // forward integration of tile `tile` of geometry g (one ray per thread)
-template <int GM, bool STATS, int KER>
+template <int GM, bool STATS, int KER, bool TOF = false>
 __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -579,6 +597,10 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                   : GM == GM_PET3D ? sqrtf(1.0f + kap * kap) : 1.0f;
     const uint2 rg = ranges[tile];
     float acc_vs = 0.0f, acc_gen = 0.0f;
+    // time of flight (parallel rays, Gaussian kernel): one sum per bin
+    float acc_t[TOF ? TOF_MAX : 1];
+#pragma unroll
+    for (int q = 0; q < (TOF ? TOF_MAX : 1); q++) acc_t[q] = 0.0f;
     unsigned n_eval = 0, n_kept = 0;
     // chunk c takes list entries c, c + nch, c + 2 nch, ...: the lists are
     // ordered by footprint position, and interleaving spreads every chunk
@@ -589,13 +611,30 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
         SRec *sv = sv_buf[ch % NBUF];
         uint32_t *msk = msk_buf[ch % NBUF];
-        prep_chunk<GM, KER>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk, c.kap0, c.kap1);
+        prep_chunk<GM, KER, TOF>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk, c.kap0, c.kap1);
         // every thread has prepared this chunk and (with two buffers) left the
         // previous one, whose buffer the next chunk's preparation reuses
         __syncthreads();
         int nvs, ngen;
         build_lists(cnt, msk, lists, w, lane, nvs, ngen);
         int k = 0;
+        if (TOF) {
+            for (; k < nvs; k++) {
+                const SRec &r = sv[lists.vs[w][k]];
+                float a0;
+                const float v0 = vs_value<GM, KER>(r, u, v, kap, a0);
+                if (STATS) n_kept += vs_keep<KER>(a0);
+                if (!vs_keep<KER>(a0)) continue;
+                const float ts = r.c2.x + r.c2.y * (u - r.c0.x) + r.c2.z * (v - r.c0.y) - g.tof_t0;
+                const float vn = v0 * r.c1.z;
+#pragma unroll
+                for (int b = 0; b < TOF_MAX; b++) {
+                    if (b >= g.n_tof) break;
+                    const float x = ts - (float)b * g.tof_h;
+                    acc_t[b] = fmaf(vn, ex2_approx(r.c1.y * x * x), acc_t[b]);
+                }
+            }
+        }
         for (; k + 1 < nvs; k += 2) {
             const int j0 = lists.vs[w][k], j1 = lists.vs[w][k + 1];
             float a0, a1;
@@ -617,15 +656,35 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                 const GRec r = load_grec(rec, sv[lists.gen[w][k2]].gid);
                 PairGeo q;
                 pair_geo(ray, r, q);
+                if (STATS) n_kept += q.m <= PAIR_CUT2;
+                if (TOF) {
+                    if (q.m <= PAIR_CUT2) {
+#pragma unroll
+                        for (int b = 0; b < TOF_MAX; b++) {
+                            if (b >= g.n_tof) break;
+                            acc_t[b] += general_value<KER>(q, r.g0.w, g.tof_t0 + (float)b * g.tof_h, g.tof_tau);
+                        }
+                    }
+                    continue;
+                }
                 const float val = general_value<KER>(q, r.g0.w);
                 acc_gen += q.m <= PAIR_CUT2 ? val : 0.0f;
-                if (STATS) n_kept += q.m <= PAIR_CUT2;
             }
         }
         if (STATS) n_eval += nvs + ngen;
         if (NBUF == 1) __syncthreads();
     }
-    if (c.valid) out[c.out_idx] = c.live ? acc_gen + L * acc_vs : 0.0f;
+    if (TOF) {
+        if (c.valid) {
+#pragma unroll
+            for (int b = 0; b < TOF_MAX; b++) {
+                if (b >= g.n_tof) break;
+                out[c.out_idx + (long long)b * g.stride_tof] = c.live ? acc_t[b] : 0.0f;
+            }
+        }
+    } else if (c.valid) {
+        out[c.out_idx] = c.live ? acc_gen + L * acc_vs : 0.0f;
+    }
     if (STATS) {
         unsigned long long e = c.live ? n_eval : 0, kk = c.live ? n_kept : 0;
 #pragma unroll
@@ -648,6 +707,17 @@ __global__ void __launch_bounds__(256, 4) k_forward(DevGeom g, const float4 *__r
                                                     float *__restrict__ out, Stats *stats)
 {
     forward_tile<GM, STATS, KER>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
+}
+
+// time-of-flight sinograms (PET ring, Gaussian kernel): one sum per bin per ray
+template <bool STATS>
+__global__ void __launch_bounds__(256, 2) k_forward_tof(DevGeom g, const float4 *__restrict__ rec,
+                                                        const float4 *__restrict__ crec,
+                                                        const uint32_t *__restrict__ gids,
+                                                        const uint2 *__restrict__ ranges,
+                                                        float *__restrict__ out, Stats *stats)
+{
+    forward_tile<GM_PARALLEL, STATS, 0, true>(g, blockIdx.x, rec, crec, gids, ranges, out, stats);
 }
 
 __device__ __forceinline__ void cross_acc(const float *a, const float *b, float s, float *o)
@@ -819,7 +889,7 @@ __device__ __forceinline__ void pet3d_chain(const float *F, const float4 *rec, u
 // the Q and A quadratics are evaluated in Horner form in du with the dv terms
 // hoisted.  For 3-D PET the LOR slope kappa varies from column to column:
 // the moments carry its powers (pet3d_chain).
-template <int GM, int TW, int KER>
+template <int GM, int TW, int KER, bool TOF = false>
 __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
                                              const float4 *__restrict__ crec,
@@ -829,7 +899,9 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              float4 *__restrict__ grad)
 {
     constexpr bool CONE = GM == GM_CONE, P3 = GM == GM_PET3D;
-    __shared__ float sgl[256];   // dL/dI |d~| of the tile's rays, row-major (0 outside the detector)
+    // dL/dI |d~| of the tile's rays, row-major (0 outside the detector); with
+    // time of flight one such tile per bin (bin b at b * 256)
+    __shared__ float sgl[TOF ? TOF_MAX * 256 : 256];
     __shared__ float su[32], svr[32];
     __shared__ float skap[P3 ? 32 : 1];   // 3-D PET: LOR slope of every column
     __shared__ float Fs[9];
@@ -854,6 +926,12 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
     if (threadIdx.x < TH) svr[threadIdx.x] = __ldg(g.vtab + min(r0 + (int)threadIdx.x, g.n_rows - 1)) + zoff;
     for (int r = threadIdx.x; r < TW * TH; r += blockDim.x) {
         const int col = c0 + r % TW, row = r0 + r / TW;
+        if (TOF) {
+            const bool in = col < g.n_cols && row < rows;
+            const long long idx = (long long)view * g.stride_view + (long long)row * g.stride_row + col;
+            for (int b = 0; b < g.n_tof; b++) sgl[b * 256 + r] = in ? __ldg(dLdI + idx + b * g.stride_tof) : 0.0f;
+            continue;
+        }
         float gl = 0.0f;
         if (col < g.n_cols && row < rows) {
             const long long idx = (long long)view * g.stride_view + (long long)row * g.stride_row + col;
@@ -890,7 +968,9 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             r.g2 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
         }
         const float4 bb = r.bb;
-        const bool vs = r.g2.w != 0.0f;
+        // with time of flight every pair takes the general path (the weight
+        // of each bin on the world-space form)
+        const bool vs = !TOF && r.g2.w != 0.0f;
         // the Gaussian's box in tile pixels (rows jlo..jhi, columns ilo..ihi)
         int jlo = TH, jhi = -1, ilo = TW, ihi = -1;
         for (int j = 0; j < TH; j++) {
@@ -1080,6 +1160,22 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 for (int j = jlo; j <= jhi; j++) {
                     const float vj = svr[j];
                     for (int i = ilo; i <= ihi; i++) {
+                        if (TOF) {
+                            const Ray ray = make_ray<GM>(g, F, su[i], vj, 0.0f);
+                            PairGeo q;
+                            pair_geo(ray, r, q);
+                            if (!(q.m <= PAIR_CUT2)) continue;
+                            for (int b = 0; b < g.n_tof; b++) {
+                                const float gw = sgl[b * 256 + j * TW + i];
+                                if (gw == 0.0f) continue;
+                                float pv[NG];
+                                general_grad<KER>(ray, q, r.g0.w, gw, pv, g.tof_t0 + (float)b * g.tof_h,
+                                                  g.tof_tau);
+#pragma unroll
+                                for (int qq = 0; qq < NG; qq++) val[qq] += pv[qq];
+                            }
+                            continue;
+                        }
                         const float gw0 = sgl[j * TW + i];
                         if (gw0 == 0.0f) continue;
                         const float u = su[i];
@@ -1124,6 +1220,18 @@ __global__ void __launch_bounds__(ADJ_BS) k_adjoint(DevGeom g, const float4 *__r
                                                  float4 *__restrict__ grad)
 {
     adjoint_tile<GM, TW, KER>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
+}
+
+// time-of-flight sinograms (PET ring, Gaussian kernel)
+template <int TW>
+__global__ void __launch_bounds__(ADJ_BS) k_adjoint_tof(DevGeom g, const float4 *__restrict__ rec,
+                                                     const float4 *__restrict__ crec,
+                                                     const uint32_t *__restrict__ gids,
+                                                     const uint2 *__restrict__ ranges,
+                                                     const float *__restrict__ dLdI,
+                                                     float4 *__restrict__ grad)
+{
+    adjoint_tile<GM_PARALLEL, TW, 0, true>(g, blockIdx.x, rec, crec, gids, ranges, dLdI, grad);
 }
 
 // Persistent forms over a batch of scans: every CTA takes (scan, tile) work
@@ -1246,7 +1354,10 @@ cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const fl
     if (g.kind == GM_CONE) RGRT_FWD_K(GM_CONE, K)      \
     else if (g.kind == GM_PET3D) RGRT_FWD_K(GM_PET3D, K) \
     else RGRT_FWD_K(GM_PARALLEL, K)
-    if (ker == 1) { RGRT_FWD_M(1) } else { RGRT_FWD_M(0) }
+    if (g.n_tof > 0) {   // PET ring, Gaussian kernel (checked by the caller)
+        if (stats) k_forward_tof<true><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+        else k_forward_tof<false><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, out, stats);
+    } else if (ker == 1) { RGRT_FWD_M(1) } else { RGRT_FWD_M(0) }
 #undef RGRT_FWD_M
 #undef RGRT_FWD_K
 #undef RGRT_FWD
@@ -1272,7 +1383,11 @@ cudaError_t launch_adjoint(const DevGeom &g, int nv, const float4 *rec, const fl
     if (g.kind == GM_CONE) RGRT_ADJ_W(GM_CONE, K)             \
     else if (g.kind == GM_PET3D) RGRT_ADJ_W(GM_PET3D, K)      \
     else RGRT_ADJ_W(GM_PARALLEL, K)
-    if (ker == 1) { RGRT_ADJ_K(1) } else { RGRT_ADJ_K(0) }
+    if (g.n_tof > 0) {   // PET ring, Gaussian kernel (checked by the caller)
+        if (g.tile_w == 8) k_adjoint_tof<8><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
+        else if (g.tile_w == 16) k_adjoint_tof<16><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
+        else k_adjoint_tof<32><<<nt, bs, 0, s>>>(g, rec, crec, gids, ranges, dLdI, grad);
+    } else if (ker == 1) { RGRT_ADJ_K(1) } else { RGRT_ADJ_K(0) }
 #undef RGRT_ADJ_K
 #undef RGRT_ADJ_W
 #undef RGRT_ADJ

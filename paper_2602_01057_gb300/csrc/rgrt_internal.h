@@ -28,7 +28,15 @@ struct DevGeom {
     const float *frames;          // n_views x 9 : e_u, e_v, e_w
     const float *utab;            // n_cols pixel u coordinates
     const float *vtab;            // n_rows pixel v coordinates (3-D PET: ring heights)
+    // time of flight (PET ring): n_tof bins (0: none) centred at
+    // tof_t0 + k tof_h along the LOR from its midpoint, 1/sigma^2 = tof_tau,
+    // sigma^2 = tof_s2; output of bin k at k stride_tof + the LOR's index
+    int n_tof;
+    float tof_t0, tof_h, tof_tau, tof_s2;
+    long long stride_tof;
 };
+
+constexpr int TOF_MAX = RGRT_TOF_MAX_BINS;
 
 // 3-D PET: ring difference of view `view`
 __host__ __device__ inline int pet3d_delta(const DevGeom &g, int view) { return view / g.n_ang - g.max_rd; }

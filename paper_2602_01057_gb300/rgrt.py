@@ -68,6 +68,7 @@ _EXPORTS = {
     "gaussians_count": ([_VP], ctypes.c_int64),
     "geometry_set": ([_VP, ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_set_corrections": ([_VP, _VP, _VP], ctypes.c_int),
+    "geometry_set_tof": ([_VP, ctypes.c_int, ctypes.c_float, ctypes.c_float], ctypes.c_int),
     "geometry_set_rays_tof": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_set_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
     "geometry_destroy": ([_VP], ctypes.c_int),
@@ -313,6 +314,12 @@ class Geometry:
         else:
             desc, angles = make_desc(d)
             _check(lib().geometry_set(ctx.h, ctypes.byref(desc), ctypes.byref(h)))
+            if int(d.get("n_tof", 0)) > 0:
+                rc = lib().geometry_set_tof(h, int(d["n_tof"]), float(d["tof_spacing"]), float(d["tof_sigma"]))
+                if rc != RGRT_OK:
+                    msg = lib().rgrt_last_error().decode()
+                    lib().geometry_destroy(h)
+                    raise RgrtError(rc, msg)
             tw, th = int(d.get("tile_w", 16)), int(d.get("tile_h", 16))
             self.tiles_per_view = ((int(d["n_cols"]) + tw - 1) // tw) * ((int(d["n_rows"]) + th - 1) // th)
         self.h = h

@@ -195,12 +195,21 @@ def geom_c3_3d(max_ring_diff: int = 5, arc_mode: int = 0, tile=(16, 16)) -> dict
 
 
 def num_rays(g: dict) -> int:
+    """Outputs of a geometry: one per ray, or per (time-of-flight bin, LOR)."""
     if g["kind"] == "rays":
         return int(np.asarray(g["o"]).shape[0])
     v = int(g["n_views"])
     if g["kind"] == "pet3d":
         v *= 2 * int(g["max_ring_diff"]) + 1
-    return v * int(g["n_rows"]) * int(g["n_cols"])
+    return v * int(g["n_rows"]) * int(g["n_cols"]) * max(1, int(g.get("n_tof", 0)))
+
+
+def with_tof_bins(g: dict, n_tof: int, spacing: float, sigma: float) -> dict:
+    """A PET sinogram geometry with time of flight: n_tof bins per LOR, bin k
+    centred at (k - (n_tof - 1)/2) spacing along the LOR from its midpoint,
+    Gaussian TOF kernel of width sigma (output [bin][sinogram])."""
+    assert g["kind"] in ("pet", "pet3d")
+    return dict(g, n_tof=int(n_tof), tof_spacing=float(spacing), tof_sigma=float(sigma))
 
 
 # ---------------------------------------------------------------------------
@@ -236,6 +245,30 @@ def detector_rays(g: dict):
     else:
         raise ValueError("detector_rays covers the CT geometries")
     return (o.reshape(-1, 3), d.reshape(-1, 3), ta.reshape(-1), tb.reshape(-1))
+
+
+def pet_lors(g: dict):
+    """(o, d, t_a, t_b) in FP64 of every LOR of a PET ring sinogram (output
+    order [plane][angle][radial]): o = s e_u + z e_v at the chord's midpoint,
+    d = e_w, t in [-h, h] with h = sqrt(R^2 - s^2); e_u = (cos phi, sin phi,
+    0), e_w = (sin phi, -cos phi, 0), phi_j = pi j / n_views (or the listed
+    angles), s_k = (k - (W-1)/2) pi R / n_crystals (arc-corrected) or
+    R sin((k - (W-1)/2) pi / n_crystals) (raw), z_p = (p - (H-1)/2) pitch."""
+    assert g["kind"] == "pet"
+    V, H, W = int(g["n_views"]), int(g["n_rows"]), int(g["n_cols"])
+    ang = np.asarray(g.get("angles", np.zeros(0)), np.float64)
+    phi = ang if ang.size else math.pi * np.arange(V) / V
+    R = float(g["radius"])
+    k = np.arange(W) - 0.5 * (W - 1)
+    s = k * math.pi * R / g["n_crystals"] if g["arc_mode"] == 0 else R * np.sin(k * math.pi / g["n_crystals"])
+    z = (np.arange(H) - 0.5 * (H - 1)) * g["pitch_v"]
+    eu = np.stack([np.cos(phi), np.sin(phi), np.zeros(V)], 1)
+    ew = np.stack([np.sin(phi), -np.cos(phi), np.zeros(V)], 1)
+    o = s[None, None, :, None] * eu[None, :, None, :] + z[:, None, None, None] * np.array([0.0, 0.0, 1.0])
+    d = np.broadcast_to(ew[None, :, None, :], o.shape)
+    h = np.sqrt(np.maximum(R * R - s * s, 0.0))
+    hb = np.broadcast_to(h[None, None, :], o.shape[:3])
+    return o.reshape(-1, 3), d.reshape(-1, 3), -hb.reshape(-1), hb.reshape(-1)
 
 
 def phantom_projection(ph: dict, o, d, ta, tb) -> np.ndarray:

@@ -104,3 +104,63 @@ def test_adjoint_matches_finite_differences(oracle):
             fd = (loss({k: v.astype(np.float32) for k, v in Gp.items()})
                   - loss({k: v.astype(np.float32) for k, v in Gm.items()})) / (hp + hm)
             assert fd == pytest.approx(want, rel=2e-3, abs=1e-6), (key, c)
+
+
+def _sinogram_lors(oracle, gd):
+    """The LORs of a PET sinogram geometry without time of flight, as
+    explicit rays (the oracle's own LOR definition)."""
+    g0 = {k: v for k, v in gd.items() if k not in ("n_tof", "tof_spacing", "tof_sigma")}
+    n = synth.num_rays(g0)
+    o, d, ta, tb = oracle.rays(g0, np.arange(n))
+    return g0, o, d, np.stack([ta, tb], 1)
+
+
+@pytest.mark.parametrize("kind", ["pet", "pet3d"])
+def test_tof_sinogram_is_the_explicit_tof_rays(oracle, kind):
+    """Structured TOF sinograms (bin k of every LOR centred at (k - (n-1)/2)
+    spacing from the LOR's midpoint) equal the same LORs traced as explicit
+    rays with time of flight, forward and adjoint."""
+    if kind == "pet":
+        gd = synth.geom_pet(6, 41, 5, 200.0, 288, 4.0)
+    else:
+        gd = synth.geom_pet3d(5, 41, 4, 200.0, 288, 4.0, 1)
+    gd = synth.with_tof_bins(gd, 5, 30.0, 25.0)
+    G = synth.gaussians_uniform(40, 31, half_box=60.0, log_sigma=math.log(6.0))
+    G["mu"][:, 2] *= 0.05
+    g0, o, d, t = _sinogram_lors(oracle, gd)
+    nl = o.shape[0]
+    nb = gd["n_tof"]
+    centres = ((np.arange(nb) - 0.5 * (nb - 1)) * gd["tof_spacing"])
+    # explicit rays, TOF-bin major like the sinogram: the LOR midpoint is t = 0
+    mid = 0.5 * (t[:, 0] + t[:, 1])
+    assert np.allclose(mid, 0.0, atol=1e-9)
+    O = np.tile(o, (nb, 1)); D = np.tile(d, (nb, 1)); T = np.tile(t, (nb, 1))
+    tof = np.stack([np.repeat(centres, nl), np.full(nb * nl, gd["tof_sigma"])], 1)
+    live = ~((T[:, 0] == 0.0) & (T[:, 1] == 0.0))     # 3-D PET rows without a ring pair
+    ref = oracle.forward_list(O[live], D[live], T[live], G, tof=tof[live])
+    got = oracle.forward(gd, G)
+    assert got["I"].size == nb * nl
+    want = np.zeros(nb * nl)
+    want[live] = ref["I"]
+    assert np.count_nonzero(want) > 100
+    np.testing.assert_allclose(got["I"], want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+    w = synth.random_weights(nb * nl, 4).astype(np.float64)
+    gb = oracle.backward(gd, G, w)
+    gl = oracle.backward_list(O[live], D[live], T[live], G, w[live], tof=tof[live])
+    for k in ("mu", "ls", "q", "rho"):
+        np.testing.assert_allclose(gb[k], gl[k], rtol=1e-9, atol=1e-12 * np.abs(gl[k]).max())
+
+
+def test_tof_bins_sum_to_the_plain_sinogram(oracle):
+    """Dense TOF bins (spacing small against the TOF width) over the whole
+    LOR sum, times the spacing, to the sinogram without time of flight (the
+    weights form a partition of unity up to the Riemann-sum error)."""
+    g0 = synth.geom_pet(4, 31, 3, 200.0, 288, 4.0)
+    G = synth.gaussians_uniform(25, 32, half_box=50.0, log_sigma=math.log(5.0))
+    G["mu"][:, 2] *= 0.05
+    plain = oracle.forward(g0, G)["I"]
+    h = 4.0
+    n = int(2 * 200.0 / h) + 41
+    gd = synth.with_tof_bins(g0, n, h, 12.0)
+    tof = oracle.forward(gd, G)["I"].reshape(n, -1)
+    np.testing.assert_allclose(h * tof.sum(axis=0), plain, rtol=1e-9, atol=1e-12 * plain.max())

@@ -78,3 +78,19 @@ def test_fwhm():
     tri = np.maximum(1.0 - np.abs(x) / 2.0, 0.0)       # triangle of half-width 2: FWHM 2, exact
     assert synth.fwhm(tri, h) == pytest.approx(2.0, rel=1e-9)
     assert math.isnan(synth.fwhm(np.ones(10), 1.0))   # no half-maximum crossing
+
+
+def test_pet_lors_are_the_oracle_lors(oracle):
+    """The explicit-ray LORs of a PET ring sinogram (input generator) are the
+    oracle's LORs of the same geometry, arc-corrected and raw, with a listed
+    angle subset."""
+    for arc in (0, 1):
+        g = synth.geom_pet(5, 21, 3, 200.0, 288, 4.0, arc_mode=arc)
+        g["angles"] = np.array([0.1, 0.7, 1.3, 2.0, 2.9])
+        o, d, ta, tb = synth.pet_lors(g)
+        n = synth.num_rays(g)
+        ro, rd, rta, rtb = oracle.rays(g, np.arange(n))
+        np.testing.assert_allclose(o, ro, atol=1e-9)
+        np.testing.assert_allclose(d, rd, atol=1e-12)
+        np.testing.assert_allclose(ta, rta, atol=1e-9)
+        np.testing.assert_allclose(tb, rtb, atol=1e-9)
