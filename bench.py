@@ -931,7 +931,10 @@ def c5_run(serve, rgrt, specs, offsets, n_slots, budget, rate_scale=1.0):
         if sel.any():
             by_kind[k] = dict(jobs=int(sel.sum()), p50_s=float(np.percentile(lat[sel], 50)),
                               p99_s=float(np.percentile(lat[sel], 99)))
+    ov = srv.device_overlap()
     return dict(slots=n_slots, jobs=len(jobs), wall_s=t1 - t0, jobs_per_s=len(jobs) / (t1 - t0),
+                device_overlap=dict(ov, note="jobs' device intervals (CUDA events on their streams): sum, "
+                                             "union, time covered by two or more, most at once"),
                 rays_per_s=rays / (t1 - t0), p50_s=float(np.percentile(lat, 50)),
                 p99_s=float(np.percentile(lat, 99)), mean_s=float(lat.mean()), by_kind=by_kind,
                 peak_running=srv.peak_running, peak_budget_gb=srv.peak_used / 1e9,

@@ -55,6 +55,7 @@ class Job:
     t_arrive: float | None = None  # arrival time (perf_counter); default: submission
     t_start: float = 0.0
     t_done: float = 0.0
+    dev_ms: tuple | None = None    # (start, end) on the device, ms after the server's reference event
     rays: int = 0                  # rays projected (forward + adjoint counted once)
     cancelled: threading.Event = dataclasses.field(default_factory=threading.Event)
 
@@ -202,6 +203,27 @@ def run_job(job: Job, device: int, budget: int, stream) -> dict:
         ctx.close()
 
 
+def overlap_stats(iv):
+    """Sum, union, time with two or more intervals, and peak concurrency of
+    (start, end) intervals."""
+    if not iv:
+        return dict(jobs=0, busy_sum_ms=0.0, union_ms=0.0, overlapped_ms=0.0, max_concurrent=0)
+    ev = sorted([(a, 1) for a, _ in iv] + [(b, -1) for _, b in iv], key=lambda x: (x[0], x[1]))
+    cur = peak = 0
+    last = ev[0][0]
+    union = multi = 0.0
+    for t, dlt in ev:
+        if cur >= 1:
+            union += t - last
+        if cur >= 2:
+            multi += t - last
+        cur += dlt
+        peak = max(peak, cur)
+        last = t
+    return dict(jobs=len(iv), busy_sum_ms=float(sum(b - a for a, b in iv)), union_ms=union,
+                overlapped_ms=multi, max_concurrent=peak)
+
+
 class Server:
     """Up to `n_slots` jobs in flight, admitted by HBM budget in arrival order.
 
@@ -226,6 +248,15 @@ class Server:
         self.stop = False
         self.done: list[Job] = []
         self.admit_order: list[object] = []
+        # device time line: CUDA events on each job's stream at its start and
+        # end, measured from a reference event recorded when the server starts
+        self.ref = None
+        if device is not None:
+            import torch
+            with torch.cuda.device(device):
+                self.ref = torch.cuda.Event(enable_timing=True)
+                self.ref.record()
+                self.ref.synchronize()
         self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(n_slots)]
         for t in self.threads:
             t.start()
@@ -263,7 +294,16 @@ class Server:
         """Seconds from arrival to completion of every finished job."""
         return np.array([j.t_done - j.t_arrive for j in self.done])
 
+    def device_overlap(self):
+        """How the finished jobs' work lay on the device: from each job's
+        device interval (first to last operation on its stream), the sum of
+        the intervals, their union, the time covered by two jobs or more and
+        the largest number at once (ms)."""
+        iv = sorted(j.dev_ms for j in self.done if j.dev_ms is not None)
+        return overlap_stats(iv)
+
     # -- worker side ---------------------------------------------------------
+
     def _take(self):
         """Block until a job can be admitted; returns (job, fut, need) or None."""
         with self.cv:
@@ -303,8 +343,13 @@ class Server:
             try:
                 if stream is not None:
                     import torch
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     with torch.cuda.stream(stream):
+                        e0.record(stream)
                         res = self.runner(job, need, stream)
+                        e1.record(stream)
+                    e1.synchronize()
+                    job.dev_ms = (self.ref.elapsed_time(e0), self.ref.elapsed_time(e1))
                 else:
                     res = self.runner(job, need, stream)
                 job.t_done = time.perf_counter()

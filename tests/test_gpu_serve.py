@@ -116,6 +116,10 @@ def test_results_same_alone_and_in_the_mix(mods, oracle):
     res = [(j, f.result(timeout=600)) for j, f in mix]
     srv.close()
     assert srv.peak_running > 1                 # jobs were in flight together
+    # and their work lay on the device together: the jobs' device intervals
+    # (CUDA events on their streams) cover some time two or more at once
+    ov = srv.device_overlap()
+    assert ov["jobs"] == len(mix) and ov["max_concurrent"] >= 2 and ov["overlapped_ms"] > 0.0
     for j, r in res:
         _compare(serve, alone[j.tag[0]], r, j.kind)
 

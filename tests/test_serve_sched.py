@@ -164,3 +164,14 @@ def test_minibatch_subsets_reproduce_the_full_scan(oracle, kind):
     parts = np.concatenate([oracle.forward(x, G)["I"] for x in geoms])
     np.testing.assert_array_equal(parts.astype(np.float32), ys)
     assert np.abs(parts).max() > 0
+
+
+def test_overlap_stats():
+    """Sum, union, multiply covered time and peak concurrency of intervals."""
+    from paper_2602_01057_gb300 import serve
+    st = serve.overlap_stats([(0.0, 4.0), (1.0, 3.0), (2.0, 6.0), (10.0, 11.0)])
+    assert st["busy_sum_ms"] == 4 + 2 + 4 + 1
+    assert st["union_ms"] == 6 + 1
+    assert st["overlapped_ms"] == 3          # [1, 4] has two or more
+    assert st["max_concurrent"] == 3
+    assert serve.overlap_stats([])["jobs"] == 0
