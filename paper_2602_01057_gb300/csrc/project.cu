@@ -739,9 +739,12 @@ __device__ __forceinline__ void cross_acc(const float *a, const float *b, float 
 //   dL/dmu' = -2 sum dL/dQ (S' c) x d~      (Q = c^T S' c, c = d~ x (S - mu'))
 //   dL/drho = sqrt(2 pi) Sw
 // out16 = (dmu[3], drho, G_P[6], G_S[6]) in world coordinates.
+// tof4 (nullable; parallel rays with time of flight): the moments of the
+// TOF weight's derivatives (see adjoint_tile), added to dL/dmu' and dL/dP'.
 template <int GM, int KER>
 __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, const float4 *rec,
-                                           uint32_t gid, const float *s, float *out16)
+                                           uint32_t gid, const float *s, float *out16,
+                                           const float *tof4 = nullptr)
 {
     constexpr bool CONE = GM == GM_CONE;
     const float4 *r = rec + REC_F4 * (size_t)gid;
@@ -812,7 +815,26 @@ __device__ __forceinline__ void view_chain(const DevGeom &g, const float *F, con
         cross_acc(cv, eU, SQuv, T);
         cross_acc(cv, eV, SQvv, T);
     }
-    const float dmuf[3] = { -2.0f * T[0], -2.0f * T[1], -2.0f * T[2] };
+    float dmuf[3] = { -2.0f * T[0], -2.0f * T[1], -2.0f * T[2] };
+    if (!CONE && tof4) {
+        // the TOF weight W(t*, s^2): t* = mu_w + k_u du + k_v dv with
+        // k_u = -P'_uw / P'_ww, k_v = -P'_vw / P'_ww, s^2 = 1/P'_ww + sigma_T^2.
+        // tof4 = alpha-free sums of val dW/dt* (1, du, dv) and val dW/ds^2.
+        const float4 r1 = __ldg(rec + REC_F4 * (size_t)gid + 1), r2 = __ldg(rec + REC_F4 * (size_t)gid + 2);
+        const float P[6] = { r1.x, r1.y, r1.z, r1.w, r2.x, r2.y };
+        float Pf[6];
+        to_frame_ax(P, fr, Pf);
+        const float ipw = 1.0f / Pf[5];
+        const float ku = -Pf[2] * ipw, kv = -Pf[4] * ipw;
+        const float T0 = alpha * tof4[0], Tu = alpha * tof4[1], Tv = alpha * tof4[2], S0 = alpha * tof4[3];
+        dmuf[0] -= ku * T0;        // du = u - mu_u: dt*/dmu_u = -k_u
+        dmuf[1] -= kv * T0;
+        dmuf[2] += T0;
+        // symmetric-entry gradients (the full matrix holds P'_uw twice)
+        GPf[2] -= 0.5f * Tu * ipw;
+        GPf[4] -= 0.5f * Tv * ipw;
+        GPf[5] -= (ku * Tu + kv * Tv) * ipw + S0 * ipw * ipw;
+    }
     out16[0] = dmuf[0] * fr.a + dmuf[2] * fr.p;
     out16[1] = dmuf[0] * fr.b + dmuf[2] * fr.q;
     out16[2] = dmuf[1];
@@ -968,9 +990,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             r.g2 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
         }
         const float4 bb = r.bb;
-        // with time of flight every pair takes the general path (the weight
-        // of each bin on the world-space form)
-        const bool vs = !TOF && r.g2.w != 0.0f;
+        const bool vs = r.g2.w != 0.0f;
         // the Gaussian's box in tile pixels (rows jlo..jhi, columns ilo..ihi)
         int jlo = TH, jhi = -1, ilo = TW, ihi = -1;
         for (int j = 0; j < TH; j++) {
@@ -998,6 +1018,20 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
             float s[NV_CONE];
 #pragma unroll
             for (int q = 0; q < NV_CONE; q++) s[q] = 0.0f;
+            // time of flight (parallel rays): a pair's value times the bin's
+            // weight W_k = N(t* - t_k; 0, s^2), s^2 = 1/A + sigma_T^2.  The
+            // value's gradient takes the view-space moments with the pair's
+            // weight G = sum_k g_k W_k in place of dL/dI; the weights'
+            // gradients take four more sums, of val dW/dt* (1, du, dv) and of
+            // val dW/ds^2 (per unit alpha), chained in view_chain.
+            float tof4[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
+            float ns = 0.0f, is2 = 0.0f;
+            if (TOF) {
+                const float s2 = r.t4.w + g.tof_s2;
+                is2 = 1.0f / s2;
+                ns = Kern<0>::QSCALE * is2;
+            }
+            const float nrm = TOF ? rsqrtf(2.0f * 3.14159265358979324f / is2) : 0.0f;
             for (int j = 0; j < TH; j++) {
                 const float vj = svr[j];
                 const bool rowin = active && vs && j >= jlo && j <= jhi;
@@ -1018,6 +1052,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                     rAc = r.c1.z;
                 }
                 float H0 = 0.0f, H1 = 0.0f, H2 = 0.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, Sw = 0.0f;
+                float T0r = 0.0f, Tur = 0.0f, S0r = 0.0f;
                 const float *gl_row = sgl + j * TW;
 #pragma unroll
                 for (int c4 = 0; c4 < TW / 4; c4++) {
@@ -1038,7 +1073,30 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                         arg = qv;
                     }
                     float wv, h, gA;
-                    if (KER == 1) {
+                    if (TOF) {
+                        // the bins' weights at this pair's t*, and their sums
+                        const float ts = r.t4.x + r.t4.y * du + r.t4.z * dv - g.tof_t0;
+                        float Ge = 0.0f, D1 = 0.0f, D2 = 0.0f;
+                        for (int b = 0; b < g.n_tof; b++) {
+                            const float x = ts - (float)b * g.tof_h, x2 = x * x;
+                            const float gw = sgl[b * 256 + j * TW + i] * ex2_approx(ns * x2);
+                            Ge += gw;
+                            D1 = fmaf(gw, x, D1);
+                            D2 = fmaf(gw, x2, D2);
+                        }
+                        Ge *= nrm;
+                        D1 *= -nrm * is2;                                   // sum g_k dW_k/dt*
+                        D2 = 0.5f * is2 * (nrm * is2 * D2 - Ge);           // sum g_k dW_k/ds^2
+                        const bool keep = arg >= CUT_ARG;
+                        const float vu = keep ? rA * ex2_approx(arg) : 0.0f;   // value per unit alpha
+                        wv = Ge * vu;
+                        h = 0.5f * wv * iA;
+                        gA = h * (arg * M_PER_ARG - 1.0f);
+                        const float v1 = vu * D1;
+                        T0r += v1;
+                        Tur = fmaf(v1, du, Tur);
+                        S0r = fmaf(vu, D2, S0r);
+                    } else if (KER == 1) {
                         // f = alpha A^-1/2 c^3/2, c = 1 - Q/(kappa^2 A): -dL/dQ / alpha =
                         // 1.5 w rA iA sqrt(c) / kappa^2, dL/dA / alpha = w rA iA sqrt(c) (1.5 - 2c)
                         const float c = 1.0f + arg;
@@ -1071,12 +1129,19 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 s[9] += G1 * dv;
                 s[10] += G0 * dv2;
                 s[11] += Sw;
+                if (TOF) {
+                    tof4[0] += T0r;
+                    tof4[1] += Tur;
+                    tof4[2] = fmaf(T0r, dv, tof4[2]);
+                    tof4[3] += S0r;
+                }
             }
             if (active && vs) {
                 if (!CONE) s[6] = s[11];   // parallel layout: [SQ.. (5), SA, Sw]
 #pragma unroll
                 for (int q = 0; q < NV_CONE; q++) any |= s[q] != 0.0f;
-                if (any) view_chain<GM, KER>(g, F, rec, gid, s, o);
+                if (TOF) any |= tof4[0] != 0.0f || tof4[1] != 0.0f || tof4[2] != 0.0f || tof4[3] != 0.0f;
+                if (any) view_chain<GM, KER>(g, F, rec, gid, s, o, TOF ? tof4 : nullptr);
             }
         }
         if (P3 && __any_sync(0xffffffffu, active && vs)) {
