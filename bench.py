@@ -43,6 +43,13 @@ UNIT = "rays/s"
 OPS_PER_PAIR_FWD = 39.0
 OPS_PER_PAIR_ADJ = 97.5
 MUFU_PER_PAIR = 3.0
+# With time of flight each kept pair adds, per bin, 4 operations and one
+# exponential to the forward (the bin's offset, its square, the scale, the
+# accumulation) and 8 operations and one exponential to the adjoint (the same
+# weight, times dL/dI, and its three sums).
+OPS_PER_BIN_FWD = 4.0
+OPS_PER_BIN_ADJ = 8.0
+MUFU_PER_BIN = 1.0
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 # DRAM bytes (read + write) of one launch of an integration kernel, from an
@@ -379,9 +386,15 @@ def sources_digest():
     return h.hexdigest()[:16]
 
 
-def sort_passes(tiles):
-    """Radix passes of the tile sort: 8-bit digits over the tile id plus an
-    8-bit position code."""
+def sort_passes(tiles, n_views=1):
+    """Radix passes of the tile sort: 8-bit digits over the tile within the
+    view plus an 8-bit position code (each view's keys are sorted on their
+    own while view << bits of the tile fits 24 bits; else over the tile id of
+    all the views)."""
+    tpv = max(1, tiles // max(1, n_views))
+    lb = math.ceil(math.log2(tpv)) if tpv > 1 else 0
+    if (n_views << lb) < (1 << 24):
+        return (lb + 8 + 7) // 8
     bits = max(1, math.ceil(math.log2(max(tiles, 2)))) + 8
     return (bits + 7) // 8
 
@@ -394,12 +407,12 @@ def binning_bytes(n_gauss, n_views, keys, tiles):
     ranges' 4-byte read; 8 B per tile range."""
     e = float(n_gauss) * n_views
     parts = dict(k_cull=60.0 * e, scan=8.0 * e, k_emit=16.0 * e + 8.0 * keys,
-                 radix_sort=16.0 * sort_passes(tiles) * keys, k_ranges=4.0 * keys + 8.0 * tiles)
+                 radix_sort=16.0 * sort_passes(tiles, n_views) * keys, k_ranges=4.0 * keys + 8.0 * tiles)
     return parts
 
 
 def roofline(kernels, pairs, keys, n_gauss, n_views, tiles, n_sm, sm_mhz, clock_note, peaks, workload,
-             traffic_table=None):
+             traffic_table=None, n_tof=0):
     """Roofline of the integration kernels (FP32 issue and MUFU against the
     SM count read from the device and the sampled clock) and of the binning
     kernels (HBM against the measured copy bandwidth).  The top-level
@@ -409,12 +422,15 @@ def roofline(kernels, pairs, keys, n_gauss, n_views, tiles, n_sm, sm_mhz, clock_
     mufu_peak = n_sm * MUFU_LANES_PER_SM * f / 1e12
     digest = sources_digest()
     out = {}
-    for name, ops in (("k_forward", OPS_PER_PAIR_FWD), ("k_adjoint", OPS_PER_PAIR_ADJ)):
+    mufu = MUFU_PER_PAIR + n_tof * MUFU_PER_BIN
+    ops_f = OPS_PER_PAIR_FWD + n_tof * OPS_PER_BIN_FWD
+    ops_a = OPS_PER_PAIR_ADJ + n_tof * OPS_PER_BIN_ADJ
+    for name, ops in (("k_forward", ops_f), ("k_adjoint", ops_a)):
         kms = kernels[name]["ms"] / max(kernels[name]["launches"], 1)
         # pairs are counted per step: work per step / the kernel's time per step
         step_ms = kernels[name]["ms"] / max(STEPS_TIMED[0], 1)
         ach = pairs * ops / (step_ms / 1e3) / 1e12 if step_ms > 0 else 0.0
-        sfu = pairs * MUFU_PER_PAIR / (step_ms / 1e3) / 1e12 if step_ms > 0 else 0.0
+        sfu = pairs * mufu / (step_ms / 1e3) / 1e12 if step_ms > 0 else 0.0
         tr = None
         if traffic_table:
             ent = traffic_table.get((workload, name))
@@ -442,8 +458,9 @@ def roofline(kernels, pairs, keys, n_gauss, n_views, tiles, n_sm, sm_mhz, clock_
                                  frac=gbs / peaks["hbm_gbs"], bytes_per_step=tot, ms_per_step=bin_ms,
                                  kernels=per, peak_source=peaks["source"]),
                 n_sm=n_sm, sm_mhz=sm_mhz, clock=clock_note, sources_digest=digest,
-                note=(f"FP32 work = {OPS_PER_PAIR_FWD:g} (forward) / {OPS_PER_PAIR_ADJ:g} (adjoint) operations "
-                      f"and {MUFU_PER_PAIR:g} MUFU per kept pair (m <= 9), per step / kernel time per step; "
+                note=(f"FP32 work = {ops_f:g} (forward) / {ops_a:g} (adjoint) operations "
+                      f"and {mufu:g} MUFU per kept pair (m <= 9"
+                      + (f"; {n_tof} TOF bins" if n_tof else "") + "), per step / kernel time per step; "
                       f"peaks = {n_sm} SMs x {FP32_LANES_PER_SM} FP32 (x {MUFU_LANES_PER_SM} MUFU) lanes x "
                       f"{sm_mhz:.0f} MHz; binning bytes as documented in binning_bytes()"))
 
@@ -543,7 +560,7 @@ def measure_step(args, name, rgrt, ctx, dev, seed, world, rank, local, cpu=True,
     n_views = synth.num_rays(gd) // (int(gd["n_rows"]) * int(gd["n_cols"]) * max(1, int(gd.get("n_tof", 0))))
     tiles = n_views * geom.tiles_per_view
     roof = roofline(kernels, pairs, st["keys"], int(G["mu"].shape[0]), n_views, tiles, n_sm, sm_mhz, note,
-                    peaks, name, TRAFFIC)
+                    peaks, name, TRAFFIC, n_tof=int(gd.get("n_tof", 0)))
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_max / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",

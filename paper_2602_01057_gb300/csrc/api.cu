@@ -245,7 +245,14 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     if (K >= 0xffffffffull)
         return fail(RGRT_E_CAPACITY, "views %d..%d produce %llu tile entries (more than 2^32)", v0,
                     v0 + nv, K);
-    size_t need = 4 * sizeof(uint32_t) * (size_t)K + sizeof(uint32_t) * sort_tmp_elems((uint32_t)K);
+    // the views' keys are sorted view by view (on the tile within the view and
+    // the position code) when the padded tile field (view << lbits | tile)
+    // fits the key's 24 bits
+    const uint32_t tpv = (uint32_t)geom->tiles_per_view;
+    const int lbits = ceil_log2(tpv);
+    const bool by_view = ((uint64_t)nv << lbits) < (1ull << 24);
+    const int nseg = by_view ? nv : 0;
+    size_t need = 4 * sizeof(uint32_t) * (size_t)K + sizeof(uint32_t) * sort_tmp_elems((uint32_t)K, nseg);
     size_t have = ctx->keys.bytes + ctx->vals.bytes + ctx->keys_alt.bytes + ctx->vals_alt.bytes +
                   ctx->sort_tmp.bytes;
     if (need > have && ctx->used - have + need + need / 8 > ctx->budget)
@@ -255,18 +262,23 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     TRY(ensure(ctx, ctx->vals, sizeof(uint32_t) * (size_t)K));
     TRY(ensure(ctx, ctx->keys_alt, sizeof(uint32_t) * (size_t)K));
     TRY(ensure(ctx, ctx->vals_alt, sizeof(uint32_t) * (size_t)K));
-    TRY(ensure(ctx, ctx->sort_tmp, sizeof(uint32_t) * sort_tmp_elems((uint32_t)K)));
+    TRY(ensure(ctx, ctx->sort_tmp, sizeof(uint32_t) * sort_tmp_elems((uint32_t)K, nseg)));
     uint32_t *keys = (uint32_t *)ctx->keys.p, *vals = (uint32_t *)ctx->vals.p;
     {
         PROF("k_emit");
         CK(launch_emit(dg, nv, N, (uint32_t *)ctx->cnt.p, (uint32_t *)ctx->off.p,
-                       (uint2 *)ctx->rect.p, keys, vals, (uint32_t)K, nullptr, s));
+                       (uint2 *)ctx->rect.p, keys, vals, (uint32_t)K, nullptr, s, by_view ? lbits : -1));
     }
     {
         PROF("radix_sort");
         bool in_alt = false;
-        CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
-                       (uint32_t)K, ceil_log2(T) + 8, (uint32_t *)ctx->sort_tmp.p, s, &in_alt));
+        if (by_view)
+            CK(launch_sort_views(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
+                                 (uint32_t)K, lbits + 8, (const uint32_t *)ctx->off.p, N, nv,
+                                 (uint32_t *)ctx->sort_tmp.p, s, &in_alt));
+        else
+            CK(launch_sort(keys, vals, (uint32_t *)ctx->keys_alt.p, (uint32_t *)ctx->vals_alt.p,
+                           (uint32_t)K, ceil_log2(T) + 8, (uint32_t *)ctx->sort_tmp.p, s, &in_alt));
         if (in_alt) {   // adopt the buffers that hold the result
             std::swap(ctx->keys, ctx->keys_alt);
             std::swap(ctx->vals, ctx->vals_alt);
@@ -277,7 +289,7 @@ int bin_views(rgrt_ctx *ctx, const rgrt_gauss *g, const rgrt_geom *geom, int v0,
     {
         PROF("k_ranges");
         CK(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * (size_t)T, s));
-        CK(launch_ranges(keys, (uint32_t)K, (uint2 *)ctx->ranges.p, T, s));
+        CK(launch_ranges(keys, (uint32_t)K, (uint2 *)ctx->ranges.p, T, s, nullptr, tpv, by_view ? lbits : -1));
     }
     *n_keys = (uint32_t)K;
     ctx->last_keys += (long long)K;

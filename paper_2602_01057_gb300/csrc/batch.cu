@@ -59,6 +59,7 @@ struct BatchScan {
     int64_t N = 0, R = 0, E = 0;
     uint32_t T = 0, cap = 0;
     int bits = 0, nblk = 1;
+    int lbits = -1;             // >= 0: keys sorted view by view (see launch_sort_views)
     bool large = false;         // projected by its own launches (not the persistent ones)
     uint32_t *vals = nullptr;   // sorted Gaussian ids [cap]
     uint2 *ranges = nullptr;    // [T]
@@ -151,6 +152,7 @@ int plan(rgrt_batch *b)
     BTRY(balloc(b, (void **)&b->stmp, sizeof(unsigned long long) * scan_tmp_elems(Emax)));
     BTRY(balloc(b, (void **)&b->total, sizeof(unsigned long long) * 2));
     uint32_t capmax = 1;
+    int vmax = 0;
     b->keys_capacity = 0;
     for (int i = 0; i < b->n; i++) {
         BatchScan &x = b->sc[i];
@@ -166,6 +168,7 @@ int plan(rgrt_batch *b)
         if (cap >= 0xffffffffull) return report_error(RGRT_E_CAPACITY, "a scan of the batch has more than 2^32 tile entries");
         x.cap = (uint32_t)cap;
         capmax = std::max(capmax, x.cap);
+        if (x.lbits >= 0) vmax = std::max(vmax, x.geom->dg.n_views);
         b->keys_capacity += cap;
         BTRY(balloc(b, (void **)&x.vals, sizeof(uint32_t) * (size_t)x.cap));
         BTRY(balloc(b, (void **)&x.ranges, sizeof(uint2) * (size_t)x.T));
@@ -179,7 +182,7 @@ int plan(rgrt_batch *b)
     BTRY(balloc(b, (void **)&b->keys, sizeof(uint32_t) * capmax));
     BTRY(balloc(b, (void **)&b->keys_alt, sizeof(uint32_t) * capmax));
     BTRY(balloc(b, (void **)&b->vals_alt, sizeof(uint32_t) * capmax));
-    BTRY(balloc(b, (void **)&b->sort_tmp, sizeof(uint32_t) * sort_tmp_elems(capmax)));
+    BTRY(balloc(b, (void **)&b->sort_tmp, sizeof(uint32_t) * sort_tmp_elems(capmax, vmax)));
     b->grid_f = persistent_grid(true, b->cone, b->tile_w, b->tile_w * b->tile_h);
     b->grid_a = persistent_grid(false, b->cone, b->tile_w, b->tile_w * b->tile_h);
     // A scan whose tiles fill the GPU for 16 waves or more gains nothing from
@@ -239,11 +242,16 @@ int enqueue_bin_scan(rgrt_batch *b, int i, cudaStream_t s)
         // capacity; an item past it writes padding keys, which sort last and
         // map to no tile, and raises the overflow flag)
         BK(launch_emit(dg, dg.n_views, x.N, b->cnt, b->off, b->rect, b->keys, x.vals, x.cap,
-                       b->d_overflow, s));
-        BK(launch_sort(b->keys, x.vals, b->keys_alt, b->vals_alt, x.cap, x.bits, b->sort_tmp, s, nullptr,
-                       b->total));
+                       b->d_overflow, s, x.lbits));
+        if (x.lbits >= 0)
+            BK(launch_sort_views(b->keys, x.vals, b->keys_alt, b->vals_alt, x.cap, x.bits, b->off, x.N,
+                                 dg.n_views, b->sort_tmp, s, nullptr, b->total));
+        else
+            BK(launch_sort(b->keys, x.vals, b->keys_alt, b->vals_alt, x.cap, x.bits, b->sort_tmp, s, nullptr,
+                           b->total));
         BK(cudaMemsetAsync(x.ranges, 0, sizeof(uint2) * (size_t)x.T, s));
-        BK(launch_ranges(b->keys, x.cap, x.ranges, x.T, s, b->total));
+        BK(launch_ranges(b->keys, x.cap, x.ranges, x.T, s, b->total, (uint32_t)x.geom->tiles_per_view,
+                         x.lbits));
     }
     return RGRT_OK;
 }
@@ -433,7 +441,9 @@ int rgrt_batch_create(rgrt_ctx *ctx, int n_scans, rgrt_gauss *const *g, const rg
             delete b;
             return report_error(RGRT_E_CAPACITY, "a batch scan has more than 2^24 tiles");
         }
-        x.bits = ceil_log2_b(x.T) + 8;
+        const int lb = ceil_log2_b((uint64_t)geom[i]->tiles_per_view);
+        x.lbits = ((uint64_t)dg.n_views << lb) < (1ull << 24) ? lb : -1;
+        x.bits = x.lbits >= 0 ? x.lbits + 8 : ceil_log2_b(x.T) + 8;
     }
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);

@@ -86,12 +86,18 @@ cudaError_t launch_records(const float *mu, const float *ls, const float *q, con
                            int64_t n, float4 *rec, float4 *crec, uint32_t *bad, cudaStream_t s);
 cudaError_t launch_cull(const DevGeom &g, int nv, const float4 *crec, int64_t n, uint32_t *cnt,
                         uint2 *rect, cudaStream_t s);
+// key = tile field << 8 | position code; lbits >= 0: the tile field is
+// (view << lbits) | tile within the view, for launch_sort_views; lbits < 0:
+// the tile id view * tiles per view + tile
 cudaError_t launch_emit(const DevGeom &g, int nv, int64_t n, const uint32_t *cnt,
                         const uint32_t *off, const uint2 *rect, uint32_t *keys, uint32_t *vals,
-                        uint32_t cap, uint32_t *overflow, cudaStream_t s);
-// n_dev (nullable): the number of sorted keys, read on the device (<= n_keys)
+                        uint32_t cap, uint32_t *overflow, cudaStream_t s, int lbits = -1);
+// n_dev (nullable): the number of sorted keys, read on the device (<= n_keys);
+// tpv, lbits: tiles per view and the emit's lbits (the tile field decoded to
+// view * tpv + tile when lbits >= 0)
 cudaError_t launch_ranges(const uint32_t *keys, uint32_t n_keys, uint2 *ranges, uint32_t n_tiles,
-                          cudaStream_t s, const unsigned long long *n_dev = nullptr);
+                          cudaStream_t s, const unsigned long long *n_dev = nullptr, uint32_t tpv = 0,
+                          int lbits = -1);
 
 // exclusive scan of n u32 values; writes out[0..n) and the 64-bit total to
 // *total (device).  tmp must hold scan_tmp_elems(n) u64.
@@ -101,8 +107,8 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, int64_t n, unsigned l
 
 // stable LSD radix sort of (keys, vals) by the low `bits` key bits; results
 // end in (keys, vals) (alt buffers are scratch).  tmp must hold
-// sort_tmp_elems(n) u32.
-size_t sort_tmp_elems(uint32_t n);
+// sort_tmp_elems(n) u32 (sort_tmp_elems(n, nv) for launch_sort_views).
+size_t sort_tmp_elems(uint32_t n, int nv = 0);
 // in_alt (nullable): set when the result is left in (keys_alt, vals_alt)
 // instead of being copied back (an odd number of passes).  n_dev (nullable):
 // sort only the first min(n, *n_dev) keys, the count read on the device
@@ -110,6 +116,15 @@ size_t sort_tmp_elems(uint32_t n);
 cudaError_t launch_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                         uint32_t n, int bits, uint32_t *tmp, cudaStream_t s, bool *in_alt = nullptr,
                         const unsigned long long *n_dev = nullptr);
+// The same sort, view by view: the emitted keys are grouped by view (view v's
+// keys start at off[v stride], the scan of the per-(view, Gaussian) counts),
+// and each view's keys are sorted on their own by their low `bits` bits --
+// the tile within the view and the position code, with keys emitted with
+// lbits = bits - 8 -- which takes fewer passes than sorting on the view too.
+cudaError_t launch_sort_views(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                              uint32_t n, int bits, const uint32_t *off, int64_t stride, int nv,
+                              uint32_t *tmp, cudaStream_t s, bool *in_alt = nullptr,
+                              const unsigned long long *n_dev = nullptr);
 
 // ker: kernel of the primitives (RGRT_KERNEL_GAUSSIAN / RGRT_KERNEL_EPANECHNIKOV)
 cudaError_t launch_forward(const DevGeom &g, int nv, const float4 *rec, const float4 *crec,
