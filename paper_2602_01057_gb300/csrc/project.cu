@@ -41,7 +41,7 @@ namespace {
 constexpr int CH = 256;             // records per chunk (one per thread in the prep)
 // chunk buffers of the forward: with two, a chunk's records are prepared into
 // one buffer while slower warps still read the other, and a single barrier
-// per chunk suffices.  The staged record (SRec, 64 B) leaves the general-path
+// per chunk suffices.  The staged records (52 B each) leave the general-path
 // fields in global memory so that two buffers still fit 4 CTAs per SM.
 constexpr int NBUF = 2;
 constexpr int ADJ_BS = 128;         // threads of an adjoint CTA (one Gaussian each)
@@ -64,14 +64,28 @@ struct VRec {
     float4 t4;  // parallel rays: the closest approach along the ray, t* = x + y du + z dv, and 1/A (w)
 };
 
-// the forward's shared-memory copy of a VRec: the view-space coefficients
-// and (gid, path); general-path records read mu, rho and P from the global
-// records by gid
+// the forward's copy of a VRec: the view-space coefficients and the gid
+// (general-path records read mu, rho and P from the global records by gid)
 struct SRec {
     float4 c0, c1, c2;
     uint32_t gid;
-    float vs;       // 1 = view-space path, 0 = general path
-    float pad0, pad1;
+};
+
+// a chunk of staged records in shared memory, one array per field: the
+// preparing threads write consecutive 16-byte (4-byte) words, free of bank
+// conflicts, and a warp reads one record at a time (broadcast)
+struct SChunk {
+    float4 c0[CH], c1[CH], c2[CH];
+    uint32_t gid[CH];
+    __device__ __forceinline__ SRec operator[](int j) const
+    {
+        SRec r;
+        r.c0 = c0[j];
+        r.c1 = c1[j];
+        r.c2 = c2[j];
+        r.gid = gid[j];
+        return r;
+    }
 };
 
 // the general-path fields of record gid (mu, rho | P00 P01 P02 P11 | P12 P22)
@@ -433,7 +447,7 @@ struct ChunkLists {
 template <int GM, int KER, bool TOF>
 __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, const uint32_t *gids,
                                            uint32_t base, uint32_t stride, int cnt,
-                                           const float4 *rec, const float4 *crec, SRec *sv,
+                                           const float4 *rec, const float4 *crec, SChunk *sv,
                                            const float4 *wbox, int nw, uint32_t *msk,
                                            float kap0, float kap1)
 {
@@ -454,11 +468,10 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
             vr.c2.y = vr.t4.y;
             vr.c2.z = vr.t4.z;
         }
-        sv[i].c0 = vr.c0;
-        sv[i].c1 = vr.c1;
-        sv[i].c2 = vr.c2;
-        sv[i].gid = gid;
-        sv[i].vs = vr.g2.w;
+        sv->c0[i] = vr.c0;
+        sv->c1[i] = vr.c1;
+        sv->c2[i] = vr.c2;
+        sv->gid[i] = gid;
         const float4 bb = vr.bb;
         // a block inside the footprint's box may still miss the footprint
         // ellipse: skip it when the tangent plane of G at the block centre
@@ -576,7 +589,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
                                              const uint2 *__restrict__ ranges,
                                              float *__restrict__ out, Stats *stats)
 {
-    __shared__ SRec sv_buf[NBUF][CH];
+    __shared__ SChunk sv_buf[NBUF];
     __shared__ ChunkLists lists;
     __shared__ uint32_t msk_buf[NBUF][CH];
     __shared__ float4 wbox[8];
@@ -609,9 +622,10 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     const uint32_t nch = (nlist + CH - 1) / CH;
     for (uint32_t ch = 0; ch < nch; ch++) {
         const int cnt = (int)((nlist - ch + nch - 1) / nch);
-        SRec *sv = sv_buf[ch % NBUF];
+        const SChunk &sv = sv_buf[ch % NBUF];
         uint32_t *msk = msk_buf[ch % NBUF];
-        prep_chunk<GM, KER, TOF>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, sv, wbox, nw, msk, c.kap0, c.kap1);
+        prep_chunk<GM, KER, TOF>(g, F, gids, rg.x + ch, nch, cnt, rec, crec, &sv_buf[ch % NBUF], wbox, nw, msk,
+                                 c.kap0, c.kap1);
         // every thread has prepared this chunk and (with two buffers) left the
         // previous one, whose buffer the next chunk's preparation reuses
         __syncthreads();
@@ -620,7 +634,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         int k = 0;
         if (TOF) {
             for (; k < nvs; k++) {
-                const SRec &r = sv[lists.vs[w][k]];
+                const SRec r = sv[lists.vs[w][k]];
                 float a0;
                 const float v0 = vs_value<GM, KER>(r, u, v, kap, a0);
                 if (STATS) n_kept += vs_keep<KER>(a0);
@@ -653,7 +667,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         if (ngen > 0) {
             const Ray ray = make_ray<GM>(g, F, u, v, kap);
             for (int k2 = 0; k2 < ngen; k2++) {
-                const GRec r = load_grec(rec, sv[lists.gen[w][k2]].gid);
+                const GRec r = load_grec(rec, sv.gid[lists.gen[w][k2]]);
                 PairGeo q;
                 pair_geo(ray, r, q);
                 if (STATS) n_kept += q.m <= PAIR_CUT2;
