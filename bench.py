@@ -53,9 +53,16 @@ MUFU_PER_BIN = 1.0
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 # DRAM bytes (read + write) of one launch of an integration kernel, from an
-# ncu capture of the workload, valid only while the kernel sources hash to
-# the recorded digest (otherwise the bench line reports null)
-TRAFFIC = {}
+# ncu capture of the workload at full size (dram__bytes.sum.per_second x
+# gpu__time_duration.sum of one timed-step launch), valid only while the
+# kernel sources hash to the recorded digest (otherwise the bench line
+# reports null)
+TRAFFIC = {
+    ("c2", "k_forward"): (262.5e6, "6774fc6bb8c68041"),
+    ("c2", "k_adjoint"): (276.8e6, "6774fc6bb8c68041"),
+    ("c3", "k_forward"): (475.3e6, "6774fc6bb8c68041"),
+    ("c3", "k_adjoint"): (478.7e6, "6774fc6bb8c68041"),
+}
 KERNEL_SOURCES = ("paper_2602_01057_gb300/csrc/project.cu", "paper_2602_01057_gb300/csrc/pair.cuh")
 WORKLOADS = {
     "c2": "cone-beam CT fwd+bwd (L2 + Adam): 50,000 Gaussians fitted to a 12-ellipsoid phantom, "
