@@ -925,6 +925,35 @@ __device__ __forceinline__ void pet3d_chain(const float *F, const float4 *rec, u
 // the Q and A quadratics are evaluated in Horner form in du with the dv terms
 // hoisted.  For 3-D PET the LOR slope kappa varies from column to column:
 // the moments carry its powers (pet3d_chain).
+// Time of flight, general path: the world-space form of every pair of the
+// Gaussian's box, once per bin, added to val.  Out of line: it is rarely
+// taken, and inlined it crowds the view-space loop out of the instruction
+// cache.
+template <int KER>
+__device__ __noinline__ void tof_general_box(const DevGeom &g, const float *F, const float *su, const float *svr,
+                                             const float *sgl, int tw, const VRec &r, int ilo, int ihi, int jlo,
+                                             int jhi, float *val)
+{
+    float Fl[9];
+    for (int q = 0; q < 9; q++) Fl[q] = F[q];
+    for (int j = jlo; j <= jhi; j++) {
+        const float vj = svr[j];
+        for (int i = ilo; i <= ihi; i++) {
+            const Ray ray = make_ray<GM_PARALLEL>(g, Fl, su[i], vj, 0.0f);
+            PairGeo q;
+            pair_geo(ray, r, q);
+            if (!(q.m <= PAIR_CUT2)) continue;
+            for (int b = 0; b < g.n_tof; b++) {
+                const float gw = sgl[b * 256 + j * tw + i];
+                if (gw == 0.0f) continue;
+                float pv[NG];
+                general_grad<KER>(ray, q, r.g0.w, gw, pv, g.tof_t0 + (float)b * g.tof_h, g.tof_tau);
+                for (int qq = 0; qq < NG; qq++) val[qq] += pv[qq];
+            }
+        }
+    }
+}
+
 template <int GM, int TW, int KER, bool TOF = false>
 __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                                              const float4 *__restrict__ rec,
@@ -1236,25 +1265,10 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
 #pragma unroll
             for (int q = 0; q < NG; q++) val[q] = 0.0f;
             if (active && !vs) {
-                for (int j = jlo; j <= jhi; j++) {
+                if (TOF) tof_general_box<KER>(g, Fs, su, svr, sgl, TW, r, ilo, ihi, jlo, jhi, val);
+                for (int j = jlo; j <= (TOF ? -1 : jhi); j++) {
                     const float vj = svr[j];
                     for (int i = ilo; i <= ihi; i++) {
-                        if (TOF) {
-                            const Ray ray = make_ray<GM>(g, F, su[i], vj, 0.0f);
-                            PairGeo q;
-                            pair_geo(ray, r, q);
-                            if (!(q.m <= PAIR_CUT2)) continue;
-                            for (int b = 0; b < g.n_tof; b++) {
-                                const float gw = sgl[b * 256 + j * TW + i];
-                                if (gw == 0.0f) continue;
-                                float pv[NG];
-                                general_grad<KER>(ray, q, r.g0.w, gw, pv, g.tof_t0 + (float)b * g.tof_h,
-                                                  g.tof_tau);
-#pragma unroll
-                                for (int qq = 0; qq < NG; qq++) val[qq] += pv[qq];
-                            }
-                            continue;
-                        }
                         const float gw0 = sgl[j * TW + i];
                         if (gw0 == 0.0f) continue;
                         const float u = su[i];
