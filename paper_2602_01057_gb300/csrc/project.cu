@@ -354,7 +354,7 @@ struct TileCtx {
     int vl, tx, ty, view, col, row;
     bool valid;                        // the thread's pixel is on the detector
     bool live;                         // ... and has a ray (3-D PET: a ring pair)
-    float wu_lo, wu_hi, wv_lo, wv_hi;  // detector box of this warp's 8 x 4 rays
+    float wu_lo, wu_hi, wv_lo, wv_hi;  // detector box of this warp's (half-warp's) rays
     float zoff, dz;                    // 3-D PET: mid-height offset of the rows, axial LOR rise
     float kap0, kap1;                  // 3-D PET: LOR slopes at the tile's extreme columns
     long long out_idx;
@@ -385,9 +385,19 @@ __device__ __forceinline__ void pet3d_slopes(const DevGeom &g, float dz, int c0,
     k1 = pet3d_slope(g, dz, amax);
 }
 
+// Half-warp blocks (4 x 4 rays per half-warp) for the parallel-ray and 3-D
+// PET geometries, whose footprints span a few bins; cone-beam footprints are
+// large enough that whole-warp 8 x 4 blocks waste little and build their
+// lists for less.
+template <int GM>
+struct HalfBlocks {
+    static constexpr bool value = GM != GM_CONE;
+};
+
 template <int GM>
 __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
 {
+    constexpr bool HALF = HalfBlocks<GM>::value;
     TileCtx c;
     int T = g.tiles_x * g.tiles_y;
     c.vl = (int)(tile / (uint32_t)T);
@@ -395,12 +405,13 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
     c.ty = tin / g.tiles_x;
     c.tx = tin - c.ty * g.tiles_x;
     c.view = g.v0 + c.vl;
+    // a warp takes an 8 x 4 block of rays (HALF: each half-warp a 4 x 4 half of it)
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int wpr = g.tile_w >> 3;  // warps per tile row
     int wx = w % wpr, wy = w / wpr;
-    int c0 = c.tx * g.tile_w + wx * 8, r0 = c.ty * g.tile_h + wy * 4;
-    c.col = c0 + (lane & 7);
-    c.row = r0 + (lane >> 3);
+    int c0 = c.tx * g.tile_w + wx * 8 + (HALF ? 4 * (lane >> 4) : 0), r0 = c.ty * g.tile_h + wy * 4;
+    c.col = c0 + (HALF ? (lane & 3) : (lane & 7));
+    c.row = r0 + (HALF ? ((lane >> 2) & 3) : (lane >> 3));
     c.valid = c.col < g.n_cols && c.row < g.n_rows;
     int rows = g.n_rows;
     c.zoff = c.dz = c.kap0 = c.kap1 = 0.0f;
@@ -411,7 +422,7 @@ __device__ __forceinline__ TileCtx tile_ctx(const DevGeom &g, uint32_t tile)
     }
     c.live = c.valid && c.row < rows;
     if (c0 < g.n_cols && r0 < rows) {
-        int c1 = min(c0 + 7, g.n_cols - 1), r1 = min(r0 + 3, rows - 1);
+        int c1 = min(c0 + (HALF ? 3 : 7), g.n_cols - 1), r1 = min(r0 + 3, rows - 1);
         c.wu_lo = __ldg(g.utab + c0); c.wu_hi = __ldg(g.utab + c1);
         c.wv_lo = __ldg(g.vtab + r0) + c.zoff; c.wv_hi = __ldg(g.vtab + r1) + c.zoff;
     } else {
@@ -436,12 +447,17 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 }
 
 // Per chunk: every thread turns one record into its view-space form and tests
-// its detector box against the 8 x 4 ray block of every warp of the tile
-// (bit w of msk); then each warp compacts, in record order, the records that
-// touch its block into a list of view-space records and a list of general ones.
+// its detector box against the ray block of every warp of the tile (bit w of
+// msk), or with half-warp blocks of every half-warp (bit 2w + h, h the half of
+// warp w); then each warp compacts, in record order, the records that touch
+// its block (each of its halves' blocks) into a list of view-space records and
+// a list of general ones.  The two halves of a warp walk their own lists side
+// by side: smaller blocks leave fewer lanes evaluating pairs outside the
+// footprint.
+constexpr uint32_t MSK_VS = 1u << 16;   // msk: the record takes the view-space path
 struct ChunkLists {
-    uint8_t vs[8][CH];
-    uint8_t gen[8][CH];
+    uint8_t vs[16][CH];
+    uint8_t gen[16][CH];
 };
 
 template <int GM, int KER, bool TOF>
@@ -489,7 +505,7 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
         }
         const float tol = 1e-3f * fabsf(cn.f);
         uint32_t m = 0;
-        for (int w = 0; w < nw; w++) {
+        for (int w = 0; w < (HalfBlocks<GM>::value ? 2 * nw : nw); w++) {
             const float4 wb = wbox[w];
             bool hit = !(bb.y < wb.x || bb.x > wb.y || bb.w < wb.z || bb.z > wb.w);
             if (GM == GM_CONE && hit && cn.ok) {
@@ -501,36 +517,67 @@ __device__ __forceinline__ void prep_chunk(const DevGeom &g, const float *F, con
             }
             m |= (uint32_t)hit << w;
         }
-        if (vr.g2.w != 0.0f) m |= 0x100u;
+        if (vr.g2.w != 0.0f) m |= MSK_VS;
         msk[i] = m;
     }
 }
 
 // warp-private compaction; returns the list lengths in nvs, ngen
+// nvs, ngen: the lengths of this lane's lists
+template <bool HALF>
 __device__ __forceinline__ void build_lists(int cnt, const uint32_t *msk, ChunkLists &L, int w,
                                             int lane, int &nvs, int &ngen)
 {
     const uint32_t lt = (1u << lane) - 1u;
-    nvs = 0;
-    ngen = 0;
+    if (!HALF) {
+        nvs = 0;
+        ngen = 0;
+        for (int b = 0; b < cnt; b += 32) {
+            const int i = b + lane;
+            const uint32_t m = i < cnt ? msk[i] : 0u;
+            const bool in = (m >> w) & 1u;
+            const bool vs = (m & MSK_VS) != 0u;
+            const uint32_t bv = __ballot_sync(0xffffffffu, in && vs);
+            const uint32_t bg = __ballot_sync(0xffffffffu, in && !vs);
+            if (in && vs) L.vs[w][nvs + __popc(bv & lt)] = (uint8_t)i;
+            if (in && !vs) L.gen[w][ngen + __popc(bg & lt)] = (uint8_t)i;
+            nvs += __popc(bv);
+            ngen += __popc(bg);
+        }
+        __syncwarp();
+        return;
+    }
+    int v0 = 0, v1 = 0, g0 = 0, g1 = 0;
     for (int b = 0; b < cnt; b += 32) {
         const int i = b + lane;
         const uint32_t m = i < cnt ? msk[i] : 0u;
-        const bool in = (m >> w) & 1u;
-        const bool vs = (m & 0x100u) != 0u;
-        const uint32_t bv = __ballot_sync(0xffffffffu, in && vs);
-        const uint32_t bg = __ballot_sync(0xffffffffu, in && !vs);
-        if (in && vs) L.vs[w][nvs + __popc(bv & lt)] = (uint8_t)i;
-        if (in && !vs) L.gen[w][ngen + __popc(bg & lt)] = (uint8_t)i;
-        nvs += __popc(bv);
-        ngen += __popc(bg);
+        const bool in0 = (m >> (2 * w)) & 1u, in1 = (m >> (2 * w + 1)) & 1u;
+        const bool vs = (m & MSK_VS) != 0u;
+        const uint32_t bv0 = __ballot_sync(0xffffffffu, in0 && vs);
+        const uint32_t bv1 = __ballot_sync(0xffffffffu, in1 && vs);
+        const uint32_t bg0 = __ballot_sync(0xffffffffu, in0 && !vs);
+        const uint32_t bg1 = __ballot_sync(0xffffffffu, in1 && !vs);
+        if (in0 && vs) L.vs[2 * w][v0 + __popc(bv0 & lt)] = (uint8_t)i;
+        if (in1 && vs) L.vs[2 * w + 1][v1 + __popc(bv1 & lt)] = (uint8_t)i;
+        if (in0 && !vs) L.gen[2 * w][g0 + __popc(bg0 & lt)] = (uint8_t)i;
+        if (in1 && !vs) L.gen[2 * w + 1][g1 + __popc(bg1 & lt)] = (uint8_t)i;
+        v0 += __popc(bv0);
+        v1 += __popc(bv1);
+        g0 += __popc(bg0);
+        g1 += __popc(bg1);
     }
     __syncwarp();
+    const bool h = lane >= 16;
+    nvs = h ? v1 : v0;
+    ngen = h ? g1 : g0;
 }
 
+// the warps' detector boxes, wbox[w] (HALF: the half-warps', wbox[2w + h])
+template <bool HALF>
 __device__ __forceinline__ void warp_box(const TileCtx &c, float4 *wbox)
 {
-    if ((threadIdx.x & 31) == 0) wbox[threadIdx.x >> 5] = make_float4(c.wu_lo, c.wu_hi, c.wv_lo, c.wv_hi);
+    if ((threadIdx.x & (HALF ? 15 : 31)) == 0)
+        wbox[threadIdx.x >> (HALF ? 4 : 5)] = make_float4(c.wu_lo, c.wu_hi, c.wv_lo, c.wv_hi);
 }
 
 // view-space value of one pair (without the |d~| factor of cone beam and
@@ -592,13 +639,15 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
     __shared__ SChunk sv_buf[NBUF];
     __shared__ ChunkLists lists;
     __shared__ uint32_t msk_buf[NBUF][CH];
-    __shared__ float4 wbox[8];
+    __shared__ float4 wbox[16];
     __shared__ float Fs[9];
     constexpr bool CONE = GM == GM_CONE;
     const TileCtx c = tile_ctx<GM>(g, tile);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr bool HALF = HalfBlocks<GM>::value;
+    const int hw = HALF ? threadIdx.x >> 4 : w;   // this lane's lists
     if (threadIdx.x < 9) Fs[threadIdx.x] = __ldg(g.frames + 9 * (size_t)c.view + threadIdx.x);
-    warp_box(c, wbox);
+    warp_box<HALF>(c, wbox);
     __syncthreads();
     float F[9];
 #pragma unroll
@@ -630,11 +679,11 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         // previous one, whose buffer the next chunk's preparation reuses
         __syncthreads();
         int nvs, ngen;
-        build_lists(cnt, msk, lists, w, lane, nvs, ngen);
+        build_lists<HALF>(cnt, msk, lists, w, lane, nvs, ngen);
         int k = 0;
         if (TOF) {
             for (; k < nvs; k++) {
-                const SRec r = sv[lists.vs[w][k]];
+                const SRec r = sv[lists.vs[hw][k]];
                 float a0;
                 const float v0 = vs_value<GM, KER>(r, u, v, kap, a0);
                 if (STATS) n_kept += vs_keep<KER>(a0);
@@ -650,7 +699,7 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
             }
         }
         for (; k + 1 < nvs; k += 2) {
-            const int j0 = lists.vs[w][k], j1 = lists.vs[w][k + 1];
+            const int j0 = lists.vs[hw][k], j1 = lists.vs[hw][k + 1];
             float a0, a1;
             const float v0 = vs_value<GM, KER>(sv[j0], u, v, kap, a0);
             const float v1 = vs_value<GM, KER>(sv[j1], u, v, kap, a1);
@@ -660,14 +709,14 @@ __device__ __forceinline__ void forward_tile(const DevGeom &g, uint32_t tile,
         }
         if (k < nvs) {
             float a0;
-            const float v0 = vs_value<GM, KER>(sv[lists.vs[w][k]], u, v, kap, a0);
+            const float v0 = vs_value<GM, KER>(sv[lists.vs[hw][k]], u, v, kap, a0);
             acc_vs += vs_keep<KER>(a0) ? v0 : 0.0f;
             if (STATS) n_kept += vs_keep<KER>(a0);
         }
         if (ngen > 0) {
             const Ray ray = make_ray<GM>(g, F, u, v, kap);
             for (int k2 = 0; k2 < ngen; k2++) {
-                const GRec r = load_grec(rec, sv.gid[lists.gen[w][k2]]);
+                const GRec r = load_grec(rec, sv.gid[lists.gen[hw][k2]]);
                 PairGeo q;
                 pair_geo(ray, r, q);
                 if (STATS) n_kept += q.m <= PAIR_CUT2;
