@@ -1146,11 +1146,7 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                 float H0 = 0.0f, H1 = 0.0f, H2 = 0.0f, G0 = 0.0f, G1 = 0.0f, G2 = 0.0f, Sw = 0.0f;
                 float T0r = 0.0f, Tur = 0.0f, S0r = 0.0f;
                 const float *gl_row = sgl + j * TW;
-#pragma unroll
-                for (int c4 = 0; c4 < TW / 4; c4++) {
-                if (!((need >> c4) & 1u)) continue;
-#pragma unroll
-                for (int i = 4 * c4; i < 4 * c4 + 4; i++) {
+                auto pixel = [&](int i) {
                     const float du = su[i] - u0;
                     const float qv = (kMuu * du + a1) * du + a0;
                     float rA, iA, arg;
@@ -1206,7 +1202,41 @@ __device__ __forceinline__ void adjoint_tile(const DevGeom &g, uint32_t tile,
                     H0 += h; H1 += hd; H2 += hd * du;
                     G0 += gA; G1 += gd; G2 += gd * du;
                     Sw += wv;
-                }
+                };
+                if (!TOF) {
+                    // 4-column groups that some Gaussian of the warp needs
+#pragma unroll
+                    for (int c4 = 0; c4 < TW / 4; c4++) {
+                        if (!((need >> c4) & 1u)) continue;
+#pragma unroll
+                        for (int i = 4 * c4; i < 4 * c4 + 4; i++) pixel(i);
+                    }
+                } else {
+                    // time of flight (parallel rays): a pixel costs a loop over
+                    // the bins, so each lane visits only its row's chord of the
+                    // footprint, arg(du) = kMuu du^2 + a1 du + a0 >= the cut
+                    // (kMuu < 0), widened to whole columns on either side (each
+                    // pixel is still tested); uniformly spaced columns only,
+                    // else the box.  (Without time of flight the lanes' uneven
+                    // chords cost more in divergence than they save.)
+                    int ia = ilo, ib = ihi;
+                    const float thr = KER == 1 ? -1.0f : CUT_ARG;
+                    if (g.uinv != 0.0f && kMuu < 0.0f && ia <= ib) {
+                        const float cc = a0 - thr;
+                        const float D = a1 * a1 - 4.0f * kMuu * cc;
+                        if (D < 0.0f) {
+                            ib = ia - 1;
+                        } else {
+                            const float sq = sqrtf(D), i2a = 0.5f / kMuu;
+                            const float d1 = (-a1 + sq) * i2a, d2 = (-a1 - sq) * i2a;   // d1 <= d2
+                            const float x1 = (u0 + d1 - su[0]) * g.uinv, x2 = (u0 + d2 - su[0]) * g.uinv;
+                            const int ja = (int)floorf(fminf(fmaxf(x1, (float)ia), (float)ib + 1.0f));
+                            const int jb = (int)ceilf(fmaxf(fminf(x2, (float)ib), (float)ia - 1.0f));
+                            ia = max(ia, ja);
+                            ib = min(ib, jb);
+                        }
+                    }
+                    for (int i = ia; i <= ib; i++) pixel(i);
                 }
                 // dL/dQ = -h:  SQ_x = -sum h x ;  SA_x = sum gA x
                 s[0] -= H1;
